@@ -1,0 +1,388 @@
+"""Pins for the FP64 oracle against facts the paper and the mathematics fix.
+
+None of these tests touches the GPU.  Each pin is chosen so that a plausible
+mistake in the oracle (a dropped term, a wrong sign or index, a transposed
+operand, a missing factor 2) makes one of them fail; test_planted_mistakes
+checks exactly that for a few such mistakes.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import gw_oracle as O
+from paper_2404_08970_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def load_golden(name):
+    return np.loadtxt(os.path.join(GOLDEN, name), comments="#")
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# ---------------------------------------------------------------------------
+# Printed matrices (golden fixtures typed from the paper)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k,name", [(1, "L_N5_k1.txt"), (2, "L_N5_k2.txt")])
+def test_golden_L(k, name):
+    assert np.array_equal(O.lower_toeplitz(5, k), load_golden(name))
+
+
+def test_golden_D1_and_dtilde():
+    D1 = load_golden("D1_n4.txt")
+    assert np.array_equal(O.grid_dist_1d(4, 1.0, 1), D1)
+    L = O.lower_toeplitz(4, 1)
+    assert np.array_equal(L + L.T, D1)  # D-tilde = L + L^T (Sec. 3)
+
+
+@pytest.mark.parametrize("n,k,name", [(2, 1, "Dhat_n2_k1.txt"), (3, 2, "Dhat_n3_k2.txt")])
+def test_golden_Dhat(n, k, name):
+    assert np.array_equal(O.grid_dist_2d(n, 1.0, "manhattan", k), load_golden(name))
+
+
+# ---------------------------------------------------------------------------
+# The paper's recursion for y = L x (Sec. 3)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("N", [1, 2, 3, 7, 40])
+def test_recursion_exact_integers(k, N):
+    rng = np.random.default_rng(100 * k + N)
+    x = rng.integers(-50, 50, size=N).astype(object)
+    L = [[(i - j) ** k if i > j else 0 for j in range(N)] for i in range(N)]
+    want = [sum(L[i][j] * x[j] for j in range(N)) for i in range(N)]
+    got = O.fgc_lower(x, k)
+    assert [int(v) for v in got] == [int(v) for v in want]
+
+
+def stirling2(k, r):
+    return sum((-1) ** (r - j) * math.comb(r, j) * j ** k for j in range(r + 1)) // math.factorial(r)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_recursion_vs_stirling_form(k):
+    """Independent derivation: t^k = sum_r S2(k,r) r! C(t,r), and
+    sum_{j<i} C(i-j, r) x_j is the r-fold shifted (r+1)-fold prefix sum.
+    So L x = sum_r S2(k,r) r! shift_r(S^{r+1} x), in exact integers."""
+    N = 33
+    rng = np.random.default_rng(k)
+    x = rng.integers(0, 1000, size=N).astype(np.int64)
+    total = np.zeros(N, dtype=np.int64)
+    for r in range(1, k + 1):
+        s = x.copy()
+        for _ in range(r + 1):
+            s = np.cumsum(s)
+        shifted = np.zeros(N, dtype=np.int64)
+        shifted[r:] = s[:N - r]
+        total += stirling2(k, r) * math.factorial(r) * shifted
+    assert np.array_equal(O.fgc_lower(x, k).astype(np.int64), total)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("N", [2, 10, 57])
+def test_recursion_operation_counts(k, N):
+    """Sec. 3: (N-1) k(k+1)/2 multiplications and (N-1)(k+1)(k+2)/2 additions."""
+    _, (mults, adds) = O.fgc_lower(np.ones(N), k, count_ops=True)
+    assert mults == (N - 1) * k * (k + 1) // 2
+    assert adds == (N - 1) * (k + 1) * (k + 2) // 2
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_fast_equals_dense_gradient(k):
+    """The paper's claim that FGC reproduces the original gradient: the fast
+    route (eq. "Dx" with the recursion) equals the dense decomposition."""
+    rng = np.random.default_rng(7 + k)
+    n, m = 37, 23
+    u = I.dirichlet(n, 1.0, rng)
+    v = I.dirichlet(m, 1.0, rng)
+    T = I.random_coupling(u, v, rng)
+    hx, hy = 1.0 / n, 1.0 / m
+    DX, DY = O.grid_dist_1d(n, hx, k), O.grid_dist_1d(m, hy, k)
+    G_dense = O.grad(DX, DY, T, u, v)
+    G_fast = O.fgc_grad_1d(T, hx, hy, k, u, v)
+    assert relerr(G_fast, G_dense) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Gradient: brute force, closed forms, invariances
+# ---------------------------------------------------------------------------
+
+def _tiny_cases():
+    cases = []
+    for k in (1, 2, 3):
+        cases.append(("1d", k, O.grid_dist_1d(5, 0.3, k), O.grid_dist_1d(4, 0.7, k)))
+    cases.append(("2d-man1", 1, O.grid_dist_2d(2, 0.5, "manhattan", 1), O.grid_dist_2d(3, 0.5, "manhattan", 1)))
+    cases.append(("2d-man2", 2, O.grid_dist_2d(3, 0.5, "manhattan", 2), O.grid_dist_2d(2, 1.0, "manhattan", 2)))
+    cases.append(("2d-sq", 2, O.grid_dist_2d(3, 0.5, "sqeuclid"), O.grid_dist_2d(2, 0.25, "sqeuclid")))
+    return cases
+
+
+@pytest.mark.parametrize("case", _tiny_cases(), ids=lambda c: c[0] + f"-k{c[1]}")
+def test_grad_matches_brute_force(case):
+    _, _, DX, DY = case
+    rng = np.random.default_rng(3)
+    T = rng.uniform(0.1, 1.0, size=(DX.shape[0], DY.shape[0]))
+    assert relerr(O.grad_exact(DX, DY, T), O.grad_brute(DX, DY, T)) < 1e-13
+
+
+@pytest.mark.parametrize("case", _tiny_cases()[:4], ids=lambda c: c[0] + f"-k{c[1]}")
+def test_value_matches_objective(case):
+    _, _, DX, DY = case
+    rng = np.random.default_rng(4)
+    T = rng.uniform(0.0, 1.0, size=(DX.shape[0], DY.shape[0]))
+    T /= T.sum()
+    E = O.objective(DX, DY, T)
+    assert E >= 0
+    assert abs(O.value(DX, DY, T) - E) <= 1e-13 * E
+
+
+def closed_form_dtilde_ones(N, k):
+    """(D-tilde 1)_i = sum_{t=1}^{i-1} t^k + sum_{t=1}^{N-i} t^k (1-based i),
+    with Faulhaber's sums for k = 1, 2."""
+    i = np.arange(1, N + 1, dtype=np.float64)
+    if k == 1:
+        return (i - 1) * i / 2 + (N - i) * (N - i + 1) / 2
+    if k == 2:
+        s = lambda t: t * (t + 1) * (2 * t + 1) / 6
+        return s(i - 1) + s(N - i)
+    raise ValueError(k)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_product_coupling_closed_form(k):
+    """T = u v^T with uniform u, v: D_X T D_Y = (D_X u)(D_Y v)^T in closed form,
+    and the constant term c_x = (D_X o D_X) u in closed form (k = 1)."""
+    n, m = 31, 19
+    hx, hy = 1.0 / n, 1.0 / m
+    u, v = np.full(n, 1.0 / n), np.full(m, 1.0 / m)
+    DX, DY = O.grid_dist_1d(n, hx, k), O.grid_dist_1d(m, hy, k)
+    G = O.grad(DX, DY, np.outer(u, v), u, v)
+    a = hx ** k * closed_form_dtilde_ones(n, k) / n
+    b = hy ** k * closed_form_dtilde_ones(m, k) / m
+    cx = hx ** (2 * k) * closed_form_dtilde_ones(n, 2 * k) / n if 2 * k <= 2 else (DX * DX) @ u
+    cy = hy ** (2 * k) * closed_form_dtilde_ones(m, 2 * k) / m if 2 * k <= 2 else (DY * DY) @ v
+    want = cx[:, None] + cy[None, :] - 2.0 * np.outer(a, b)
+    assert relerr(G, want) < 1e-13
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_reflection_equivariance(dim):
+    """Reflecting a uniform grid maps D to J D J = D (Sec. 4.3 invariance), so
+    G(J T J') = J G(T) J' exactly."""
+    rng = np.random.default_rng(11)
+    if dim == 1:
+        DX, DY = O.grid_dist_1d(9, 0.1, 1), O.grid_dist_1d(7, 0.2, 1)
+    else:
+        DX, DY = O.grid_dist_2d(3, 0.5, "manhattan", 1), O.grid_dist_2d(4, 0.3, "sqeuclid")
+    n, m = DX.shape[0], DY.shape[0]
+    T = rng.uniform(size=(n, m))
+    r, c = rng.uniform(size=n), rng.uniform(size=m)
+    G = O.grad(DX, DY, T, r, c)
+    Gr = O.grad(DX, DY, T[::-1, ::-1], r[::-1], c[::-1])
+    assert relerr(Gr[::-1, ::-1], G) < 1e-13
+    Gc = O.grad(DX, DY, T[:, ::-1], r, c[::-1])
+    assert relerr(Gc[:, ::-1], G) < 1e-13
+
+
+def test_transpose_and_symmetry():
+    rng = np.random.default_rng(12)
+    DX, DY = O.grid_dist_1d(8, 0.2, 2), O.grid_dist_1d(6, 0.3, 2)
+    T = rng.uniform(size=(8, 6))
+    r, c = rng.uniform(size=8), rng.uniform(size=6)
+    assert relerr(O.grad(DY, DX, T.T, c, r), O.grad(DX, DY, T, r, c).T) < 1e-13
+    D = O.grid_dist_1d(7, 0.1, 1)
+    S = rng.uniform(size=(7, 7))
+    S = S + S.T
+    w = rng.uniform(size=7)
+    G = O.grad(D, D, S, w, w)
+    assert relerr(G, G.T) < 1e-13
+
+
+def test_linearity():
+    rng = np.random.default_rng(13)
+    DX, DY = O.grid_dist_1d(6, 0.2, 1), O.grid_dist_1d(5, 0.3, 1)
+    A, B = rng.uniform(size=(6, 5)), rng.uniform(size=(6, 5))
+    zx, zy = np.zeros(6), np.zeros(5)
+    lhs = O.grad(DX, DY, 2.0 * A - 3.0 * B, zx, zy)
+    rhs = 2.0 * O.grad(DX, DY, A, zx, zy) - 3.0 * O.grad(DX, DY, B, zx, zy)
+    assert relerr(lhs, rhs) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# 2D structure (Sec. 3.1)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_kronecker_expansion(k):
+    """eq. "2D kronecker": D-hat = sum_r C(k,r) D1^{odot r} (x) D1^{odot k-r}
+    with D1^{odot 0} = J (0^0 = 1), and D-hat x = sum_r C(k,r)
+    vec(D1^{odot k-r} mat(x) D1^{odot r}) with the row-major vec."""
+    n = 4
+    D1 = O.grid_dist_1d(n, 1.0, 1)
+    pw = lambda e: np.ones((n, n)) if e == 0 else D1 ** e
+    Dhat = O.grid_dist_2d(n, 1.0, "manhattan", k)
+    K = sum(math.comb(k, r) * np.kron(pw(r), pw(k - r)) for r in range(k + 1))
+    assert np.array_equal(K, Dhat)
+    x = np.random.default_rng(k).uniform(size=n * n)
+    y = sum(math.comb(k, r) * (pw(k - r) @ x.reshape(n, n) @ pw(r)).reshape(-1) for r in range(k + 1))
+    # With row-major vec, D1^{odot r} (x) D1^{odot k-r} acts as
+    # mat(x) -> D1^{odot r} mat(x) D1^{odot k-r}; summing over r symmetrically
+    # gives the same total because C(k,r) = C(k,k-r).
+    assert relerr(y, Dhat @ x) < 1e-13
+
+
+@pytest.mark.parametrize("cost", ["sqeuclid", "manhattan"])
+def test_2d_four_marginal_identity(cost):
+    """For a separable 2D cost d = phi(da) + phi(db) (squared Euclidean, or
+    Manhattan with k = 1), D_X T D_Y[(a,b),(c,d)] =
+    Z1[a,c] + Z2[a,d] + Z3[b,c] + Z4[b,d], Zt = Phi_X Mt Phi_Y, where the Mt
+    are T's sums over the other two grid axes."""
+    sx, sy = 3, 4
+    hx, hy = 0.5, 0.25
+    DX = O.grid_dist_2d(sx, hx, cost, 1)
+    DY = O.grid_dist_2d(sy, hy, cost, 1)
+    kk = 2 if cost == "sqeuclid" else 1
+    PX = O.grid_dist_1d(sx, hx, kk)
+    PY = O.grid_dist_1d(sy, hy, kk)
+    T = np.random.default_rng(5).uniform(size=(sx * sx, sy * sy))
+    T4 = T.reshape(sx, sx, sy, sy)  # [a, b, c, d]
+    M1 = T4.sum(axis=(1, 3))  # [a, c]
+    M2 = T4.sum(axis=(1, 2))  # [a, d]
+    M3 = T4.sum(axis=(0, 3))  # [b, c]
+    M4 = T4.sum(axis=(0, 2))  # [b, d]
+    Z1, Z2, Z3, Z4 = (PX @ M @ PY for M in (M1, M2, M3, M4))
+    Z = (Z1[:, None, :, None] + Z2[:, None, None, :] + Z3[None, :, :, None] + Z4[None, :, None, :])
+    assert relerr(Z.reshape(sx * sx, sy * sy), DX @ T @ DY) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Sinkhorn and mirror descent
+# ---------------------------------------------------------------------------
+
+def _small_problem(n=12, m=9, seed=0):
+    rng = np.random.default_rng(seed)
+    u, v = I.dirichlet(n, 1.0, rng), I.dirichlet(m, 1.0, rng)
+    Pi = rng.uniform(0.0, 1.0, size=(n, m))
+    return u, v, Pi
+
+
+def test_sinkhorn_column_marginals_exact_and_rows_converge():
+    u, v, Pi = _small_problem()
+    f, g = O.sinkhorn_log(Pi, u, v, 0.1, 200)
+    T = O.plan(Pi, f, g, 0.1)
+    assert np.max(np.abs(T.sum(axis=0) - v)) < 1e-13
+    assert np.max(np.abs(T.sum(axis=1) - u)) < 1e-10
+    f1, g1 = O.sinkhorn_log(Pi, u, v, 0.1, 1)
+    T1 = O.plan(Pi, f1, g1, 0.1)
+    assert np.max(np.abs(T1.sum(axis=0) - v)) < 1e-13
+
+
+def test_sinkhorn_matches_scaling_form():
+    """The log-domain iteration and the textbook scaling iteration are the
+    same sequence: T = diag(a) K diag(b), K = exp(-Pi/eps), a = exp(f/eps),
+    b = exp(g/eps)."""
+    u, v, Pi = _small_problem(seed=1)
+    eps = 0.2
+    f, g = O.sinkhorn_log(Pi, u, v, eps, 37)
+    a, b = O.sinkhorn_scaling(np.exp(-Pi / eps), u, v, 37)
+    assert relerr(np.exp(f / eps), a) < 1e-12
+    assert relerr(np.exp(g / eps), b) < 1e-12
+
+
+def test_sinkhorn_large_eps_gives_product_coupling():
+    u, v, Pi = _small_problem(seed=2)
+    f, g = O.sinkhorn_log(Pi, u, v, 1e7, 5)
+    assert relerr(O.plan(Pi, f, g, 1e7), np.outer(u, v)) < 1e-6
+
+
+def test_mirror_descent_reflection():
+    """Reversing v's grid reverses the plan's columns (exact symmetry of the
+    uniform grid; the paper's reflection invariance, Sec. 4.3)."""
+    n, m = 10, 8
+    rng = np.random.default_rng(21)
+    u, v = I.dirichlet(n, 1.0, rng), I.dirichlet(m, 1.0, rng)
+    DX, DY = O.grid_dist_1d(n, 1.0 / n, 1), O.grid_dist_1d(m, 1.0 / m, 1)
+    T, _, _ = O.mirror_descent(DX, DY, u, v, 0.05, 5, 30)
+    Tr, _, _ = O.mirror_descent(DX, DY, u, v[::-1].copy(), 0.05, 5, 30)
+    assert relerr(Tr[:, ::-1], T) < 1e-11
+
+
+def test_mirror_descent_single_point():
+    """n = 1: the only coupling is T = v^T."""
+    rng = np.random.default_rng(22)
+    v = I.dirichlet(6, 1.0, rng)
+    DX, DY = O.grid_dist_1d(1, 1.0, 1), O.grid_dist_1d(6, 1.0 / 6, 1)
+    T, _, _ = O.mirror_descent(DX, DY, np.ones(1), v, 0.05, 3, 10)
+    assert relerr(T[0], v) < 1e-13
+
+
+def test_fgw_limits():
+    n, m = 7, 6
+    rng = np.random.default_rng(23)
+    u, v = I.dirichlet(n, 1.0, rng), I.dirichlet(m, 1.0, rng)
+    DX, DY = O.grid_dist_1d(n, 1.0 / n, 1), O.grid_dist_1d(m, 1.0 / m, 1)
+    CC = O.fgw_feature_cost(I.features(n, 4, rng), I.features(m, 4, rng))
+    Tg, _, _ = O.mirror_descent(DX, DY, u, v, 0.1, 3, 20)
+    T1, _, _ = O.mirror_descent(DX, DY, u, v, 0.1, 3, 20, theta=1.0, CC=CC)
+    assert relerr(T1, Tg) < 1e-14
+    T0, _, _ = O.mirror_descent(DX, DY, u, v, 0.1, 3, 20, theta=0.0, CC=CC)
+    f, g = O.sinkhorn_log(CC, u, v, 0.1, 20)
+    assert relerr(T0, O.plan(CC, f, g, 0.1)) < 1e-13
+
+
+def test_feature_cost_definition():
+    rng = np.random.default_rng(24)
+    phi, psi = I.features(5, 3, rng), I.features(4, 3, rng)
+    CC = O.fgw_feature_cost(phi, psi)
+    for i in range(5):
+        for p in range(4):
+            assert abs(CC[i, p] - sum((phi[i, t] - psi[p, t]) ** 2 for t in range(3))) < 1e-13
+
+
+def test_random_coupling_marginals():
+    rng = np.random.default_rng(25)
+    u, v = I.dirichlet(50, 0.5, rng), I.dirichlet(40, 0.5, rng)
+    T = I.random_coupling(u, v, rng)
+    assert np.all(T > 0)
+    assert np.max(np.abs(T.sum(axis=1) - u)) < 1e-15
+    assert np.max(np.abs(T.sum(axis=0) - v)) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# Planted mistakes: each must be caught by one of the pins above
+# ---------------------------------------------------------------------------
+
+def test_planted_mistakes():
+    rng = np.random.default_rng(31)
+    DX, DY = O.grid_dist_1d(5, 0.3, 1), O.grid_dist_1d(4, 0.7, 1)
+    T = rng.uniform(0.1, 1.0, size=(5, 4))
+    brute = O.grad_brute(DX, DY, T)
+    r, c = T.sum(axis=1), T.sum(axis=0)
+    cx, cy = (DX * DX) @ r, (DY * DY) @ c
+    wrong = {
+        "factor 4 (the paper's grad E scale)": cx[:, None] + cy[None, :] - 4.0 * DX @ T @ DY,
+        "dropped c_y": cx[:, None] - 2.0 * DX @ T @ DY,
+        "c_y from the wrong marginal": cx[:, None] + ((DY * DY) @ T[:4, :].sum(axis=1))[None, :] - 2.0 * DX @ T @ DY,
+        "sign of the bilinear term": cx[:, None] + cy[None, :] + 2.0 * DX @ T @ DY,
+        "D_Y built with exponent k + 1": cx[:, None] + cy[None, :] - 2.0 * DX @ T @ O.grid_dist_1d(4, 0.7, 2),
+    }
+    for name, G in wrong.items():
+        assert relerr(G, brute) > 1e-3, name
+    # A recursion with the wrong binomial row fails the exact-integer pin.
+    x = np.arange(1, 9).astype(object)
+    L2 = [[(i - j) ** 2 if i > j else 0 for j in range(8)] for i in range(8)]
+    want = [sum(L2[i][j] * x[j] for j in range(8)) for i in range(8)]
+    a1 = [0] * 9
+    a2 = [0] * 9
+    a3 = [0] * 9
+    for i in range(1, 8):  # mistake: a3 update uses C(2,1) = 1 instead of 2
+        a1[i + 1] = x[i - 1] + a1[i]
+        a2[i + 1] = x[i - 1] + a1[i] + a2[i]
+        a3[i + 1] = x[i - 1] + a1[i] + 1 * a2[i] + a3[i]
+    assert [int(a3[i]) for i in range(1, 9)] != [int(w) for w in want]
