@@ -1,0 +1,323 @@
+"""Benchmark of the structured GW gradient on GB300.
+
+Default workload: 1D uniform grids n = m = 8192, k = 1, uniform marginals, a
+random positive coupling T with those marginals (float32 on the device),
+spacing h = 1/n.  One step = one gradient evaluation G = L(C_X,C_Y) (x) T
+through the C ABI (gw_grad, target marginals).  T and G are 268 MB each,
+larger than the 129 MB L2, so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  Under torchrun every rank runs the same workload on
+its own GPU (independent replicas, weak scaling); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GW grad evals/s fast vs dense (%roofline); served solves/s + p50/p99"
+UNIT = "grad evals/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(n, k):
+    from paper_2404_08970_gb300 import inputs as I
+    return I.workload_1d_grad(n, k, "uniform", seed=0)
+
+
+def config(n, k, extra=None):
+    c = {"workload": f"1D uniform grids n=m={n}, k={k}, uniform marginals, random positive coupling, h=1/n; "
+                     f"one structured gradient evaluation per step",
+         "n": n, "m": n, "k": k, "marginals": "target (uniform)", "l2": "inputs larger than L2 (268 MB T, 268 MB G)",
+         "global_batch": 1, "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_rows_time(T64, u, v, k, h, rows):
+    """Times the FP64 oracle's gradient rows (definition: c_x + c_y - 2 D_X T D_Y)."""
+    import numpy as np
+    from oracle import gw_oracle as O
+    n, m = T64.shape
+    idx = np.arange(n, dtype=np.float64)
+    t0 = time.perf_counter()
+    sel = np.arange(rows)
+    DXr = (h ** k) * np.abs(idx[sel][:, None] - idx[None, :]) ** k
+    DY = O.grid_dist_1d(m, h, k)
+    cy = (DY * DY) @ v
+    O.grad_rows(DXr, DY, T64, (DXr * DXr) @ u, cy)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_rate(w, budget_s=15.0):
+    """Gradient evals/s of the oracle on the host, from a timed sample of rows
+    (the full dense gradient at n = 8192 takes minutes in FP64)."""
+    import numpy as np
+    T64 = w["T"]
+    n = T64.shape[0]
+    rows = 16
+    t = oracle_rows_time(T64, w["u"], w["v"], w["k"], w["hx"], rows)
+    # Grow the sample until it costs about budget_s/2.
+    while t < budget_s / 4 and rows < n:
+        rows = min(n, rows * 4)
+        t = oracle_rows_time(T64, w["u"], w["v"], w["k"], w["hx"], rows)
+    rate = (rows / n) / t
+    return rate, rows, t
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs"), d.get("bf16_tflops"), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Arms
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = workload(args.n, args.k)
+    import numpy as np
+    n = args.n
+    # Each step: one bounded row sample of the oracle gradient.
+    rate0, rows, t = cpu_oracle_rate(w, budget_s=8.0)
+    for _ in range(args.warmup):
+        oracle_rows_time(w["T"], w["u"], w["v"], w["k"], w["hx"], rows)
+    times = [oracle_rows_time(w["T"], w["u"], w["v"], w["k"], w["hx"], rows) for _ in range(args.steps)]
+    tot = sum(times)
+    value = args.steps * (rows / n) / tot
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps / (rows / n),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config(n, args.k),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{rows} of {n} gradient rows per step (dense FP64 definition, numpy)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2404_08970_gb300 import _lib as L
+
+    n, k = args.n, args.k
+    w = workload(n, k)
+    ctx = L.Context(local)
+    dev = torch.device("cuda", local)
+    T32 = torch.from_numpy(w["T"].astype(np.float32))
+    dT = T32.to(dev)
+    dG = torch.empty_like(dT)
+    du = torch.from_numpy(w["u"]).to(dev)
+    dv = torch.from_numpy(w["v"]).to(dev)
+    prob = L.problem(dim=1, nx=n, ny=n, hx=w["hx"], hy=w["hy"], k=k, dtype=L.GW_F32)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ctx.gw_grad(prob, du, dv, dT, dG, L.GW_MARG_TARGET, stream)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    ctx.gw_ctx_check(stream)
+    barrier()
+
+    clocks = Clocks(local)
+    clocks.start()
+    ctx.gw_ctx_profile(True)
+    ctx.gw_ctx_profile_report(reset=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ctx.gw_ctx_profile_report(reset=True)
+    ctx.gw_ctx_profile(False)
+    clk = clocks.stop()
+    ctx.gw_ctx_check(stream)
+
+    ms_max = ms
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    per_step = ms_max / args.steps
+    value = world * args.steps / (ms_max / 1e3)
+
+    # Roofline of the dominant kernel (largest total time).
+    hbm_peak, bf16_peak, peak_kind = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
+    launches = sum(v["launches"] for v in prof.values()) if prof else 0
+    nm = n * n
+    roof = None
+    if dom[0]:
+        avg_ms = dom[1]["ms"] / max(1, dom[1]["launches"])
+        alg_bytes = 8.0 * nm  # read T + write G, 4 B each (k1c) -- the gradient's algorithmic bytes
+        achieved = alg_bytes / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "peak_kind": f"hbm_gbs of {peak_kind}", "traffic": None,
+                "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms}
+    whole_gbs = 8.0 * nm / (per_step / 1e3) / 1e9
+
+    # End to end: pinned host T -> device, gradient, G -> pinned host, every step.
+    hT = T32.pin_memory()
+    hG = torch.empty_like(hT).pin_memory()
+    e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        dT.copy_(hT, non_blocking=True)
+        step()
+        hG.copy_(dG, non_blocking=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(e_steps):
+        dT.copy_(hT, non_blocking=True)
+        step()
+        hG.copy_(dG, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e_ms = float(t.item())
+    e2e = {"value": world * e_steps / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 4 * nm,
+           "d2h_bytes_per_step": 4 * nm}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, rows, t = cpu_oracle_rate(w)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{rows} of {n} rows of the FP64 dense-definition gradient (numpy), {t:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(n, k),
+                "roofline": roof, "whole_gradient_gbs": whole_gbs, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clk, "gpu_launches": launches, "kernels": prof}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,140 @@
+/*
+ * gw.h - C ABI of the GB300 fast Gromov-Wasserstein gradient library.
+ *
+ * The library computes, on one GPU, the gradient of the discrete
+ * Gromov-Wasserstein objective for distributions on uniform grids and runs
+ * the entropic mirror-descent solver built on it, following
+ * "Fast Gradient Computation for Gromov-Wasserstein Distance"
+ * (Zhang, Wang, Fan, Wu, Zhang; arXiv 2404.08970).
+ *
+ * Notation (Sec. 2 of the paper): X has n points (the paper's M), Y has m
+ * points (the paper's N).  Distances on a uniform 1D grid are
+ * d_ij = h^k |i - j|^k (eq. "1d distance matrices"); on an s x s 2D grid a
+ * point (a, b) has index a*s + b.  A coupling T is an n x m row-major array,
+ * T[i*m + p].
+ *
+ * The gradient returned by gw_grad is
+ *     G = L(C_X, C_Y) (x) T = c_x 1^T + 1 c_y^T - 2 D_X T D_Y,
+ *     c_x = (D_X o D_X) r,  c_y = (D_Y o D_Y) c,
+ * which is half the paper's grad E = C1 - 4 D_X Gamma D_Y (Sec. 2.1,
+ * gradient decomposition).  r, c are either the target marginals (u, v), as
+ * in the paper's C1, or T's own marginals (T 1, T^T 1), which makes G exact
+ * for any T.
+ *
+ * Conventions shared by every entry point:
+ *  - Device pointers (prefix d_) are caller-owned device memory; the library
+ *    never frees or keeps them beyond the call's stream work.
+ *  - Host pointers (prefix h_) are caller-owned host memory.
+ *  - stream is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    enqueue work and return without synchronising unless stated.
+ *  - Each call returns a gw_status.  On an error the call enqueues nothing
+ *    and gw_last_error(ctx) describes the cause.
+ *  - Calls that share a context share its device workspace: order them on
+ *    one stream (or use one context per stream).  Host-side state of a
+ *    context is protected by a mutex.
+ */
+#ifndef GW_FGC_H
+#define GW_FGC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GW_OK = 0,
+  GW_NOT_READY = 1,
+  GW_ERR_INVALID = -1,   /* bad argument or descriptor */
+  GW_ERR_OOM = -2,       /* device allocation failed */
+  GW_ERR_CUDA = -3,      /* a CUDA call failed */
+  GW_ERR_TIMEOUT = -4,   /* a bounded device wait gave up */
+  GW_ERR_NONFINITE = -5, /* a non-finite value reached an output */
+  GW_ERR_SHUTDOWN = -6   /* the server is shutting down */
+} gw_status;
+
+typedef enum { GW_F32 = 0, GW_F64 = 1 } gw_dtype;
+
+/* Distance on 2D grids.  GW_COST_POW: Manhattan distance to the power k,
+ * h^k (|a-a'| + |b-b'|)^k (Sec. 3.1, eq. "2d Dx"); on 1D grids it is the
+ * only cost, h^k |i-j|^k.  GW_COST_SQEUCLID: h^2 ((a-a')^2 + (b-b')^2). */
+typedef enum { GW_COST_POW = 0, GW_COST_SQEUCLID = 1 } gw_cost;
+
+/* Which marginals build the constant term c_x, c_y of the gradient. */
+typedef enum { GW_MARG_TARGET = 0, GW_MARG_EXACT = 1 } gw_marginals;
+
+/* Problem descriptor, following the paper's problem statement (Sec. 2). */
+typedef struct gw_problem {
+  int dim;       /* 1 or 2 */
+  int nx, ny;    /* 1D: points of X and Y; 2D: grid sides (points = side^2) */
+  double hx, hy; /* grid spacings h_X, h_Y (> 0) */
+  int k;         /* distance exponent, integer >= 1 (k_X = k_Y = k) */
+  int cost;      /* gw_cost (2D only; 1D uses GW_COST_POW) */
+  double eps;    /* entropic regularisation (> 0), solver only */
+  int n_outer;   /* mirror-descent iterations, solver only */
+  int n_inner;   /* Sinkhorn iterations per mirror-descent step, solver only */
+  double theta;  /* fused-GW weight of the GW term, in [0, 1]; 1 = plain GW */
+  int feat_dim;  /* fused-GW feature dimension (0 = none) */
+  int dtype;     /* gw_dtype of T, G (and of the solver's arithmetic) */
+} gw_problem;
+
+typedef struct gw_ctx gw_ctx;
+
+/* Creates a context on CUDA device `device` (made current for the calls of
+ * this context).  *ctx receives the handle.  GW_ERR_CUDA if the device is
+ * unusable. */
+gw_status gw_ctx_create(gw_ctx** ctx, int device);
+
+/* Frees the context and its device workspace (synchronises the device). */
+void gw_ctx_destroy(gw_ctx* ctx);
+
+/* Text of the last error on this context ("" if none).  The string stays
+ * valid until the next call on the context. */
+const char* gw_last_error(const gw_ctx* ctx);
+
+/* Synchronises `stream`, then reads and clears the context's device status
+ * word.  GW_ERR_TIMEOUT if a bounded device wait gave up since the last
+ * check, GW_ERR_NONFINITE if a kernel flagged a non-finite output, GW_OK
+ * otherwise. */
+gw_status gw_ctx_check(gw_ctx* ctx, void* stream);
+
+/* Switches per-kernel timing on (enable = 1) or off (0).  While on, every
+ * kernel the library launches for this context is bracketed by CUDA events
+ * recorded on the call's stream (a small cost per launch). */
+gw_status gw_ctx_profile(gw_ctx* ctx, int enable);
+
+/* Waits for the recorded events, folds them into per-kernel totals and
+ * writes the totals to buf as JSON text:
+ *   {"kernel": {"launches": L, "ms": T}, ...}
+ * reset = 1 clears the totals afterwards.  GW_ERR_INVALID if buf (len bytes)
+ * is too small or NULL. */
+gw_status gw_ctx_profile_report(gw_ctx* ctx, char* buf, size_t len, int reset);
+
+/*
+ * gw_grad - the structured gradient G = L(C_X, C_Y) (x) T (Sec. 3, eqs. "Dx",
+ * "1d y", "1d recursive relation"; Sec. 3.1, eqs. "2d gradient" and
+ * "2D kronecker").
+ *
+ *   prob       dim 1: any k >= 1 up to 3, nx, ny >= 1, ny <= 16384.
+ *              dim 2 is not available through this call yet (GW_ERR_INVALID).
+ *              Only dim, nx, ny, hx, hy, k, dtype are read.
+ *   d_u, d_v   target marginals, double, lengths n and m; read only with
+ *              marginals == GW_MARG_TARGET (may be NULL otherwise).
+ *   d_T        the coupling, n x m row-major, prob->dtype.
+ *   d_G        output, n x m row-major, prob->dtype; must not overlap d_T.
+ *   marginals  GW_MARG_TARGET or GW_MARG_EXACT.
+ *
+ * Cost O(n m): the DP recursion along columns and rows replaces the dense
+ * products.  With dtype GW_F32 the arithmetic is float with compensated band
+ * carries; GW_F64 computes in double throughout.
+ * Errors: GW_ERR_INVALID for a bad descriptor or a NULL required pointer.
+ */
+gw_status gw_grad(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const double* d_v,
+                  const void* d_T, void* d_G, int marginals, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GW_FGC_H */

@@ -1,0 +1,172 @@
+"""ctypes binding of libgw_fgc.so (argument marshalling only).
+
+The functions here carry the C entry points' names and arguments; every step
+of the computation runs inside the CUDA library.  Loading fails loudly when
+the library has not been built: there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+LIB_PATH = os.path.join(PKG, "libgw_fgc.so")
+HEADER = os.path.join(ROOT, "include", "gw.h")
+
+# gw_status
+GW_OK = 0
+GW_NOT_READY = 1
+GW_ERR_INVALID = -1
+GW_ERR_OOM = -2
+GW_ERR_CUDA = -3
+GW_ERR_TIMEOUT = -4
+GW_ERR_NONFINITE = -5
+GW_ERR_SHUTDOWN = -6
+STATUS_NAMES = {0: "GW_OK", 1: "GW_NOT_READY", -1: "GW_ERR_INVALID", -2: "GW_ERR_OOM", -3: "GW_ERR_CUDA",
+                -4: "GW_ERR_TIMEOUT", -5: "GW_ERR_NONFINITE", -6: "GW_ERR_SHUTDOWN"}
+# gw_dtype
+GW_F32 = 0
+GW_F64 = 1
+# gw_cost
+GW_COST_POW = 0
+GW_COST_SQEUCLID = 1
+# gw_marginals
+GW_MARG_TARGET = 0
+GW_MARG_EXACT = 1
+
+
+class gw_problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int),
+        ("hx", ctypes.c_double),
+        ("hy", ctypes.c_double),
+        ("k", ctypes.c_int),
+        ("cost", ctypes.c_int),
+        ("eps", ctypes.c_double),
+        ("n_outer", ctypes.c_int),
+        ("n_inner", ctypes.c_int),
+        ("theta", ctypes.c_double),
+        ("feat_dim", ctypes.c_int),
+        ("dtype", ctypes.c_int),
+    ]
+
+
+class GWError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Loads libgw_fgc.so (build it with paper_2404_08970_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -m paper_2404_08970_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I = ctypes.c_int
+    S = ctypes.c_int  # gw_status
+    prob = ctypes.POINTER(gw_problem)
+    sigs = {
+        "gw_ctx_create": (S, [ctypes.POINTER(P), I]),
+        "gw_ctx_destroy": (None, [P]),
+        "gw_last_error": (ctypes.c_char_p, [P]),
+        "gw_ctx_check": (S, [P, P]),
+        "gw_ctx_profile": (S, [P, I]),
+        "gw_ctx_profile_report": (S, [P, ctypes.c_char_p, ctypes.c_size_t, I]),
+        "gw_grad": (S, [P, prob, P, P, P, P, I, P]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/gw.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gw_[a-z0-9_]+)\s*\(", text)))
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def problem(dim=1, nx=1, ny=1, hx=1.0, hy=1.0, k=1, cost=GW_COST_POW, eps=1e-2, n_outer=1, n_inner=1,
+            theta=1.0, feat_dim=0, dtype=GW_F32) -> gw_problem:
+    return gw_problem(dim, nx, ny, hx, hy, k, cost, eps, n_outer, n_inner, theta, feat_dim, dtype)
+
+
+class Context:
+    """Owns a gw_ctx*.  Methods mirror the C entry points."""
+
+    def __init__(self, device: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        st = lib.gw_ctx_create(ctypes.byref(h), device)
+        if st != GW_OK:
+            raise GWError(st, f"gw_ctx_create(device={device}) failed")
+        self.h = h
+        self.lib = lib
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gw_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return self.lib.gw_last_error(self.h).decode()
+
+    def _check(self, st: int, what: str) -> int:
+        if st < 0:
+            raise GWError(st, f"{what}: {self.last_error()}")
+        return st
+
+    def gw_ctx_check(self, stream=None) -> int:
+        return self._check(self.lib.gw_ctx_check(self.h, _stream(stream)), "gw_ctx_check")
+
+    def gw_ctx_profile(self, enable: bool) -> int:
+        return self._check(self.lib.gw_ctx_profile(self.h, int(enable)), "gw_ctx_profile")
+
+    def gw_ctx_profile_report(self, reset: bool = True) -> dict:
+        import json
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(self.lib.gw_ctx_profile_report(self.h, buf, len(buf), int(reset)), "gw_ctx_profile_report")
+        return json.loads(buf.value.decode())
+
+    def gw_grad(self, prob: gw_problem, u, v, T, G, marginals=GW_MARG_TARGET, stream=None) -> int:
+        st = self.lib.gw_grad(self.h, ctypes.byref(prob), _ptr(u), _ptr(v), _ptr(T), _ptr(G), marginals,
+                              _stream(stream))
+        return self._check(st, "gw_grad")

@@ -1,0 +1,273 @@
+// C ABI entry points: context, validation, workspace, dispatch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "gw_internal.h"
+
+// Records a pair of CUDA events around every traced launch; totals are folded
+// in when the report is read.
+struct EventTracer : gw::Tracer {
+  struct Rec {
+    std::string name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<std::string, cudaEvent_t>> open;
+  std::map<std::string, std::pair<long, double>> totals;  // name -> (launches, ms)
+
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void begin(const char* name, cudaStream_t st) override {
+    cudaEvent_t e = get();
+    cudaEventRecord(e, st);
+    open.push_back({name, e});
+  }
+  void end(cudaStream_t st) override {
+    if (open.empty()) return;
+    auto o = open.back();
+    open.pop_back();
+    cudaEvent_t e = get();
+    cudaEventRecord(e, st);
+    pending.push_back({o.first, o.second, e});
+  }
+  void collect() {
+    for (auto& r : pending) {
+      cudaEventSynchronize(r.b);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, r.a, r.b);
+      auto& t = totals[r.name];
+      t.first += 1;
+      t.second += ms;
+      pool.push_back(r.a);
+      pool.push_back(r.b);
+    }
+    pending.clear();
+  }
+  ~EventTracer() override {
+    for (auto& r : pending) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+struct gw_ctx {
+  int device = 0;
+  int num_sms = 0;
+  std::mutex mu;
+  std::string err;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  unsigned* status = nullptr;  // device status word
+  EventTracer* tracer = nullptr;  // non-null while profiling is on
+  gw::Tracer* tr() { return tracer; }
+};
+
+namespace {
+
+gw_status fail(gw_ctx* c, gw_status s, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+gw_status fail(gw_ctx* c, gw_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+
+gw_status cuda_fail(gw_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, GW_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Grows the context workspace to at least `bytes` (synchronises the device
+// when it has to reallocate).
+gw_status ensure_ws(gw_ctx* c, size_t bytes) {
+  if (bytes <= c->ws_bytes) return GW_OK;
+  if (c->ws) {
+    cudaDeviceSynchronize();
+    cudaFree(c->ws);
+    c->ws = nullptr;
+    c->ws_bytes = 0;
+  }
+  size_t want = bytes + bytes / 8;
+  cudaError_t e = cudaMalloc(&c->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, GW_ERR_OOM, "workspace allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+  }
+  c->ws_bytes = want;
+  return GW_OK;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+gw_status check_grid(gw_ctx* c, const gw_problem* p) {
+  if (!p) return fail(c, GW_ERR_INVALID, "problem descriptor is NULL");
+  if (p->dim != 1 && p->dim != 2) return fail(c, GW_ERR_INVALID, "dim must be 1 or 2 (got %d)", p->dim);
+  if (p->nx < 1 || p->ny < 1) return fail(c, GW_ERR_INVALID, "grid sizes must be >= 1 (got %d, %d)", p->nx, p->ny);
+  if (!finite_pos(p->hx) || !finite_pos(p->hy)) return fail(c, GW_ERR_INVALID, "grid spacings must be finite and > 0");
+  if (p->k < 1) return fail(c, GW_ERR_INVALID, "distance exponent k must be >= 1 (got %d)", p->k);
+  if (p->dtype != GW_F32 && p->dtype != GW_F64) return fail(c, GW_ERR_INVALID, "dtype must be GW_F32 or GW_F64");
+  return GW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gw_status gw_ctx_create(gw_ctx** out, int device) {
+  if (!out) return GW_ERR_INVALID;
+  *out = nullptr;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return GW_ERR_CUDA;
+  }
+  gw_ctx* c = new gw_ctx();
+  c->device = device;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  e = cudaMalloc(&c->status, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return GW_ERR_OOM;
+  }
+  cudaMemset(c->status, 0, sizeof(unsigned));
+  *out = c;
+  return GW_OK;
+}
+
+void gw_ctx_destroy(gw_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  if (c->ws) cudaFree(c->ws);
+  if (c->status) cudaFree(c->status);
+  delete c->tracer;
+  delete c;
+}
+
+gw_status gw_ctx_profile(gw_ctx* c, int enable) {
+  if (!c) return GW_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  if (enable && !c->tracer) c->tracer = new EventTracer();
+  if (!enable && c->tracer) {
+    cudaDeviceSynchronize();
+    delete c->tracer;
+    c->tracer = nullptr;
+  }
+  return GW_OK;
+}
+
+gw_status gw_ctx_profile_report(gw_ctx* c, char* buf, size_t len, int reset) {
+  if (!c || !buf || len == 0) return GW_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  std::string out = "{";
+  if (c->tracer) {
+    c->tracer->collect();
+    bool first = true;
+    for (auto& kv : c->tracer->totals) {
+      char item[256];
+      snprintf(item, sizeof item, "%s\"%s\": {\"launches\": %ld, \"ms\": %.6f}", first ? "" : ", ",
+               kv.first.c_str(), kv.second.first, kv.second.second);
+      out += item;
+      first = false;
+    }
+    if (reset) c->tracer->totals.clear();
+  }
+  out += "}";
+  if (out.size() + 1 > len) return fail(c, GW_ERR_INVALID, "profile report needs %zu bytes", out.size() + 1);
+  memcpy(buf, out.c_str(), out.size() + 1);
+  return GW_OK;
+}
+
+const char* gw_last_error(const gw_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+gw_status gw_ctx_check(gw_ctx* c, void* stream) {
+  if (!c) return GW_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  unsigned word = 0;
+  e = cudaMemcpy(&word, c->status, sizeof word, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+  cudaMemset(c->status, 0, sizeof(unsigned));
+  if (word & 1u) return fail(c, GW_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (word & 2u) return fail(c, GW_ERR_NONFINITE, "a non-finite value reached an output");
+  c->err.clear();
+  return GW_OK;
+}
+
+gw_status gw_grad(gw_ctx* c, const gw_problem* p, const double* d_u, const double* d_v, const void* d_T, void* d_G,
+                  int marginals, void* stream) {
+  if (!c) return GW_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  gw_status s = check_grid(c, p);
+  if (s != GW_OK) return s;
+  if (p->dim != 1) return fail(c, GW_ERR_INVALID, "gw_grad: 2D grids are not available in this call");
+  if (p->k > 3) return fail(c, GW_ERR_INVALID, "gw_grad: k must be <= 3 (got %d)", p->k);
+  if (p->ny > 16384) return fail(c, GW_ERR_INVALID, "gw_grad: ny must be <= 16384 (got %d)", p->ny);
+  if (marginals != GW_MARG_TARGET && marginals != GW_MARG_EXACT)
+    return fail(c, GW_ERR_INVALID, "marginals must be GW_MARG_TARGET or GW_MARG_EXACT");
+  if (!d_T || !d_G) return fail(c, GW_ERR_INVALID, "d_T and d_G must not be NULL");
+  if (marginals == GW_MARG_TARGET && (!d_u || !d_v))
+    return fail(c, GW_ERR_INVALID, "target marginals requested but d_u or d_v is NULL");
+  const size_t esz = p->dtype == GW_F32 ? 4 : 8;
+  const size_t nm = (size_t)p->nx * (size_t)p->ny;
+  const char* t0 = (const char*)d_T;
+  const char* g0 = (const char*)d_G;
+  if (t0 < g0 + nm * esz && g0 < t0 + nm * esz) return fail(c, GW_ERR_INVALID, "d_T and d_G overlap");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
+
+  gw::Grad1DArgs a{};
+  a.n = p->nx;
+  a.m = p->ny;
+  a.k = p->k;
+  a.hx = p->hx;
+  a.hy = p->hy;
+  a.dtype = p->dtype;
+  a.T = d_T;
+  a.G = d_G;
+  a.u = d_u;
+  a.v = d_v;
+  a.exact = marginals == GW_MARG_EXACT;
+  a.out_scale = 1.0;
+  a.stream = (cudaStream_t)stream;
+  a.status = c->status;
+  a.num_sms = c->num_sms;
+  a.tracer = c->tr();
+  s = ensure_ws(c, gw::grad1d_workspace_bytes(a.n, a.m, a.k, a.dtype, a.num_sms));
+  if (s != GW_OK) return s;
+  int rc = gw::grad1d_launch(a, c->ws, c->ws_bytes);
+  if (rc != GW_OK) {
+    cudaError_t e = cudaGetLastError();
+    return fail(c, (gw_status)rc, "gw_grad launch failed: %s", cudaGetErrorString(e));
+  }
+  c->err.clear();
+  return GW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,93 @@
+// Internal host-side declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/gw.h"
+
+namespace gw {
+
+// Device workspace of one context: a single growing allocation carved into
+// regions by each call.  Calls on one context are ordered on their stream.
+struct Workspace {
+  void* base = nullptr;
+  size_t bytes = 0;
+};
+
+struct Carve {
+  char* p;
+  size_t left;
+  void* take(size_t n, size_t align = 256) {
+    uintptr_t a = ((uintptr_t)p + align - 1) & ~(uintptr_t)(align - 1);
+    size_t used = (size_t)(a - (uintptr_t)p) + n;
+    if (used > left) return nullptr;
+    p += used;
+    left -= used;
+    return (void*)a;
+  }
+};
+
+// Optional per-kernel timing: when a context has profiling switched on, each
+// launch site brackets its kernel with begin()/end(), which record CUDA
+// events on the launch stream.
+struct Tracer {
+  virtual void begin(const char* name, cudaStream_t st) = 0;
+  virtual void end(cudaStream_t st) = 0;
+  virtual ~Tracer() {}
+};
+
+struct TraceScope {
+  Tracer* t;
+  cudaStream_t st;
+  TraceScope(Tracer* tr, const char* name, cudaStream_t s) : t(tr), st(s) {
+    if (t) t->begin(name, st);
+  }
+  ~TraceScope() {
+    if (t) t->end(st);
+  }
+};
+
+// Layout of the 1D row bands used by the structured gradient.
+struct Bands {
+  int B;  // number of bands
+  int R;  // rows per band (the last band may be shorter)
+};
+
+Bands choose_bands(int n, int target);
+
+struct Grad1DArgs {
+  int n, m, k;
+  double hx, hy;
+  int dtype;            // GW_F32 or GW_F64
+  const void* T;        // n x m row-major, dtype
+  void* G;              // n x m row-major, dtype
+  const double* u;      // target marginals (device) or nullptr with exact
+  const double* v;
+  int exact;            // 1: constant term from T's own marginals
+  double out_scale;     // G := out_scale * (c_x + c_y - 2 D_X T D_Y)
+  cudaStream_t stream;
+  unsigned* status;     // device status word
+  int num_sms;
+  Tracer* tracer;       // nullable
+};
+
+// Bytes of workspace the structured 1D gradient needs.
+size_t grad1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms);
+// Launches the structured 1D gradient.  Returns GW_OK or an error.
+int grad1d_launch(const Grad1DArgs& a, void* ws, size_t ws_bytes);
+
+// Per-exponent entry points (one translation unit each).
+int grad1d_launch_k1(const Grad1DArgs& a, void* ws, size_t ws_bytes);
+int grad1d_launch_k2(const Grad1DArgs& a, void* ws, size_t ws_bytes);
+int grad1d_launch_k3(const Grad1DArgs& a, void* ws, size_t ws_bytes);
+
+// c[i] = h^{2k} sum_j |i - j|^{2k} w_j for i < len (the constant term of the
+// gradient), from a double vector w on the device.  part must hold
+// marg_part_doubles(len, k) doubles.
+size_t marg_part_doubles(int len, int k);
+int marg_const_launch(const double* w, int len, int k, double h, void* out, int dtype,
+                      double* part, cudaStream_t stream, Tracer* tracer = nullptr);
+
+}  // namespace gw

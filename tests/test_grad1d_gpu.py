@@ -1,0 +1,98 @@
+"""Parity of the structured 1D gradient (CUDA, through the C ABI) with the FP64
+oracle.  Tolerances: relative error max|G - G*| / max|G*| <= 1e-6 for float
+arithmetic, <= 1e-12 for double."""
+import numpy as np
+import pytest
+
+from paper_2404_08970_gb300 import inputs as I
+from tests import gwtest_util as U
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-6, "f64": 1e-12}
+
+SHAPES = [(1, 1), (1, 7), (5, 1), (3, 5), (17, 33), (64, 64), (100, 257), (200, 200), (513, 300), (1000, 1023),
+          (257, 2049), (300, 4100)]
+
+
+def _case(n, m, seed, alpha=1.0):
+    rng = np.random.default_rng(seed)
+    u = I.dirichlet(n, alpha, rng)
+    v = I.dirichlet(m, alpha, rng)
+    T = I.random_coupling(u, v, rng)
+    return u, v, T
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("k", [1, 2, 3])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: f"{s[0]}x{s[1]}")
+def test_grad1d_parity(shape, k, dtype):
+    n, m = shape
+    u, v, T = _case(n, m, 1000 * k + n + m)
+    hx, hy = 1.0 / n, 1.0 / m
+    Tc = T.astype(np.float32) if dtype == "f32" else T
+    for marg in ("target", "exact"):
+        G = U.gpu_grad_1d(Tc, u, v, k, hx, hy, dtype, marg)
+        Gs = U.oracle_grad_1d(Tc.astype(np.float64), u, v, k, hx, hy, marg)
+        err = U.relerr(G, Gs)
+        assert err <= TOL[dtype], f"{marg} rel err {err:.3e}"
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_grad1d_wide_rows(k):
+    """m above 8192 uses the 1024-thread row layout."""
+    n, m = 40, 9001
+    u, v, T = _case(n, m, 77 + k)
+    Tc = T.astype(np.float32)
+    G = U.gpu_grad_1d(Tc, u, v, k, 1.0 / n, 1.0 / m, "f32", "target")
+    Gs = U.oracle_grad_1d(Tc.astype(np.float64), u, v, k, 1.0 / n, 1.0 / m, "target")
+    assert U.relerr(G, Gs) <= TOL["f32"]
+
+
+def test_grad1d_nonuniform_spacing_and_mass():
+    """Unnormalised positive T, different spacings: G is linear in T, so the
+    kernel must not assume a probability coupling."""
+    rng = np.random.default_rng(5)
+    n, m = 150, 97
+    T = I.random_positive(n, m, rng) * 3.7
+    for k in (1, 2):
+        G = U.gpu_grad_1d(T.astype(np.float32), None, None, k, 0.37, 2.1, "f32", "exact")
+        Gs = U.oracle_grad_1d(T.astype(np.float32).astype(np.float64), None, None, k, 0.37, 2.1, "exact")
+        assert U.relerr(G, Gs) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("marg_kind", ["uniform", "dirichlet"])
+@pytest.mark.parametrize("k", [1, 2])
+def test_grad1d_full_size_sampled(k, marg_kind):
+    """n = m = 8192 (the benchmark workload, same launch path): sampled rows
+    against the oracle, including band boundaries and both ends."""
+    w = I.workload_1d_grad(8192, k, marg_kind, seed=0)
+    T32 = w["T"].astype(np.float32)
+    G = U.gpu_grad_1d(T32, w["u"], w["v"], k, w["hx"], w["hy"], "f32", "target")
+    rows = [0, 1, 53, 54, 55, 4095, 4096, 8190, 8191]
+    Gs = U.oracle_grad_rows_1d(T32.astype(np.float64), rows, w["u"], w["v"], k, w["hx"], w["hy"])
+    err = U.relerr(G[rows], Gs)
+    assert err <= TOL["f32"], f"sampled rel err {err:.3e}"
+    # Property at full size: reflecting T reflects G (exact symmetry of the grid).
+    Gr = U.gpu_grad_1d(np.ascontiguousarray(T32[::-1, ::-1]), w["u"][::-1].copy(), w["v"][::-1].copy(), k,
+                       w["hx"], w["hy"], "f32", "target")
+    assert U.relerr(Gr[::-1, ::-1], G) <= 2 * TOL["f32"]
+
+
+def test_grad1d_invalid_arguments():
+    from paper_2404_08970_gb300 import _lib as L
+    import torch
+    c = U.ctx()
+    T = torch.ones(4, 4, device="cuda")
+    G = torch.empty_like(T)
+    bad = [L.problem(dim=1, nx=0, ny=4), L.problem(dim=1, nx=4, ny=4, k=0), L.problem(dim=1, nx=4, ny=4, hx=-1.0),
+           L.problem(dim=3, nx=4, ny=4), L.problem(dim=1, nx=4, ny=4, dtype=7)]
+    for p in bad:
+        with pytest.raises(L.GWError) as e:
+            c.gw_grad(p, None, None, T, G, L.GW_MARG_EXACT)
+        assert e.value.status == L.GW_ERR_INVALID
+    p = L.problem(dim=1, nx=4, ny=4)
+    with pytest.raises(L.GWError):
+        c.gw_grad(p, None, None, T, T, L.GW_MARG_EXACT)  # overlap
+    with pytest.raises(L.GWError):
+        c.gw_grad(p, None, None, T, G, L.GW_MARG_TARGET)  # missing marginals
