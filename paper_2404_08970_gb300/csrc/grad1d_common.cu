@@ -2,6 +2,10 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cuda.h>
+
+#include <mutex>
+
 #include "grad1d_impl.cuh"
 
 namespace gw {
@@ -38,25 +42,43 @@ __global__ void rowsum_finish(const void* rowpart, int nchunks, int n, int is_f3
 // Constant term c[i] = factor * sum_j (i - j)^P w_j, P = 2k (even), written as
 // a polynomial in (i - ctr) whose coefficients are the centred moments
 // M_t = sum_j (j - ctr)^t w_j (binomial expansion of ((i-ctr) - (j-ctr))^P).
-// FP64 throughout; the work is spread over ceil(len/256) blocks.
+// FP64 throughout.  Both vectors (X and Y) go through the same two launches;
+// the work is spread over many blocks because FP64 throughput per SM is low.
 constexpr int kMargBlock = 256;
 
-__global__ void marg_moments(const double* __restrict__ w, int len, int P, double ctr, double* __restrict__ part) {
-  __shared__ double sm[kMargBlock];
-  const int j = blockIdx.x * kMargBlock + threadIdx.x;
+struct MargVec {
+  const double* w;
+  int len;
+  double factor;
+  void* out;
+};
+
+__device__ __forceinline__ double warp_sum_d(double x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+__global__ void marg_moments2(MargVec X, MargVec Y, int nbx, int P, double* __restrict__ part) {
+  __shared__ double sm[kMargBlock / 32][16];
+  const bool isx = (int)blockIdx.x < nbx;
+  const MargVec V = isx ? X : Y;
+  const int blk = isx ? blockIdx.x : blockIdx.x - nbx;
+  const int j = blk * kMargBlock + threadIdx.x;
+  const double ctr = (double)(V.len / 2);
   const double d = (double)j - ctr;
-  const double wj = (j < len) ? w[j] : 0.0;
-  double pw = wj;
+  double pw = (j < V.len) ? V.w[j] : 0.0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int t = 0; t <= P; ++t) {
-    sm[threadIdx.x] = pw;
-    __syncthreads();
-    for (int o = kMargBlock / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) sm[threadIdx.x] += sm[threadIdx.x + o];
-      __syncthreads();
-    }
-    if (threadIdx.x == 0) part[(size_t)blockIdx.x * (P + 1) + t] = sm[0];
-    __syncthreads();
+    const double s = warp_sum_d(pw);
+    if (lane == 0) sm[warp][t] = s;
     pw *= d;
+  }
+  __syncthreads();
+  if (threadIdx.x <= P) {
+    double acc = 0.0;
+    for (int w = 0; w < kMargBlock / 32; ++w) acc += sm[w][threadIdx.x];
+    part[(size_t)blockIdx.x * (P + 1) + threadIdx.x] = acc;
   }
 }
 
@@ -64,28 +86,34 @@ __global__ void marg_moments(const double* __restrict__ w, int len, int P, doubl
 // (lo = 0 for double output), so that float consumers keep the constant term
 // to float-float accuracy.
 template <typename Real>
-__global__ void marg_eval(const double* __restrict__ part, int nblk, int len, int P, double ctr, double factor,
-                          Real* __restrict__ out) {
+__global__ void marg_eval2(MargVec X, MargVec Y, int nbx, int nby, int nex, int P, const double* __restrict__ part) {
   __shared__ double M[16];
-  if (threadIdx.x <= P) {
+  const bool isx = (int)blockIdx.x < nex;
+  const MargVec V = isx ? X : Y;
+  const int blk = isx ? blockIdx.x : blockIdx.x - nex;
+  const int p0 = isx ? 0 : nbx, np = isx ? nbx : nby;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = warp; t <= P; t += kMargBlock / 32) {
     double acc = 0.0;
-    for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * (P + 1) + threadIdx.x];
-    M[threadIdx.x] = acc;
+    for (int b = lane; b < np; b += 32) acc += part[(size_t)(p0 + b) * (P + 1) + t];
+    acc = warp_sum_d(acc);
+    if (lane == 0) M[t] = acc;
   }
   __syncthreads();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= len) return;
-  const double x = (double)i - ctr;
+  const int i = blk * kMargBlock + threadIdx.x;
+  if (i >= V.len) return;
+  const double x = (double)i - (double)(V.len / 2);
   // sum_t C(P,t) x^{P-t} (-1)^t M_t, Horner in x.
   double acc = 0.0;
   for (int t = 0; t <= P; ++t) {
-    double c = (double)binom(P, t) * ((t & 1) ? -M[t] : M[t]);
+    const double c = (double)binom(P, t) * ((t & 1) ? -M[t] : M[t]);
     acc = acc * x + c;
   }
-  const double val = factor * acc;
+  const double val = V.factor * acc;
   const Real hi = (Real)val;
+  Real* out = (Real*)V.out;
   out[i] = hi;
-  out[len + i] = (Real)(val - (double)hi);
+  out[V.len + i] = (Real)(val - (double)hi);
 }
 
 size_t marg_part_doubles(int len, int k) {
@@ -93,18 +121,54 @@ size_t marg_part_doubles(int len, int k) {
   return (size_t)nblk * (2 * k + 1);
 }
 
-int marg_const_launch(const double* w, int len, int k, double factor, void* out, int dtype, double* part,
-                      cudaStream_t stream, Tracer* tracer) {
+int marg_const2_launch(const double* wx, int n, double fx, void* outx, const double* wy, int m, double fy,
+                       void* outy, int k, int dtype, double* part, cudaStream_t stream, Tracer* tracer) {
   TraceScope ts(tracer, "marg_const", stream);
   const int P = 2 * k;
-  const int nblk = (len + kMargBlock - 1) / kMargBlock;
-  const double ctr = (double)(len / 2);
-  marg_moments<<<nblk, kMargBlock, 0, stream>>>(w, len, P, ctr, part);
+  const int nbx = (n + kMargBlock - 1) / kMargBlock, nby = (m + kMargBlock - 1) / kMargBlock;
+  MargVec X{wx, n, fx, outx}, Y{wy, m, fy, outy};
+  marg_moments2<<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, P, part);
   if (dtype == GW_F32)
-    marg_eval<float><<<nblk, kMargBlock, 0, stream>>>(part, nblk, len, P, ctr, factor, (float*)out);
+    marg_eval2<float><<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, nby, nbx, P, part);
   else
-    marg_eval<double><<<nblk, kMargBlock, 0, stream>>>(part, nblk, len, P, ctr, factor, (double*)out);
+    marg_eval2<double><<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, nby, nbx, P, part);
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+}
+
+int marg_const_launch(const double* w, int len, int k, double factor, void* out, int dtype, double* part,
+                      cudaStream_t stream, Tracer* tracer) {
+  return marg_const2_launch(w, len, factor, out, w, 0, 0.0, nullptr, k, dtype, part, stream, tracer);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_rows_tmap(void* tmap, const void* base, int n, int m, int elem_bytes, int* box_cols) {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) == cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  });
+  if (!fn) return false;
+  const int E = 128 / elem_bytes;
+  if (m % E != 0 || n < 1) return false;
+  const int bc = std::min(256, m / E);
+  cuuint64_t dims[3] = {(cuuint64_t)E, (cuuint64_t)(m / E), (cuuint64_t)n};
+  cuuint64_t strides[2] = {128, (cuuint64_t)m * (cuuint64_t)elem_bytes};
+  cuuint32_t box[3] = {(cuuint32_t)E, (cuuint32_t)bc, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn((CUtensorMap*)tmap, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                  3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  *box_cols = bc;
+  return r == CUDA_SUCCESS;
 }
 
 size_t grad1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms) {

@@ -1,0 +1,417 @@
+// Warp-specialised row kernel of the structured 1D gradient (k = 1, 2; up to
+// 8192 columns).  Same arithmetic as k1c_grad_rows; the work of a row is split
+// between NW compute warps and one scan warp, and consecutive rows overlap:
+//
+//   compute warps, row t (phase A): wait for the row in the shared-memory ring,
+//     column recursion, in-chunk forward walk, float lane scan, post the warp
+//     total -> named barrier "totals(t)";
+//   scan warp: waits on totals(t), refills the ring slot freed by row t-1
+//     (TMA), scans the NW warp totals in float-float (forward prefixes and
+//     backward suffixes) and posts, per warp, the polynomial ZW(o) of z over
+//     the warp's segment -> named barrier "poly(t)";
+//   compute warps, row t-1 (phase B, after phase A of row t): wait on
+//     poly(t-1), add the in-warp terms, add the constant term, store G.
+//
+// Barriers are double-buffered by row parity, so neither side can run more
+// than one row ahead of the other.  Rows are stored in shared memory with the
+// 128-byte swizzle (16-byte chunk index XOR 128-byte row index mod 8), which
+// makes the per-thread 16-byte reads conflict-free; TMA tensor copies write
+// that layout directly.
+#pragma once
+
+#include <cuda.h>
+
+namespace gw {
+
+__device__ __forceinline__ uint32_t swz128(uint32_t b) { return b ^ (((b >> 7) & 7u) << 4); }
+
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst_smem, const CUtensorMap* tm, int c0, int c1, int c2,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst_smem)),
+      "l"(tm), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
+}
+
+template <typename Real, int VPT>
+__device__ __forceinline__ void lds_swz(const unsigned char* base, int c0, Real (&out)[VPT]) {
+  constexpr int PER = 16 / sizeof(Real);
+#pragma unroll
+  for (int j = 0; j < VPT / PER; ++j) {
+    const uint32_t b = (uint32_t)((c0 + j * PER) * sizeof(Real));
+    const float4 f = *reinterpret_cast<const float4*>(base + swz128(b));
+    if constexpr (sizeof(Real) == 4) {
+      out[j * 4 + 0] = f.x;
+      out[j * 4 + 1] = f.y;
+      out[j * 4 + 2] = f.z;
+      out[j * 4 + 3] = f.w;
+    } else {
+      const double2 d = *reinterpret_cast<const double2*>(&f);
+      out[j * 2 + 0] = d.x;
+      out[j * 2 + 1] = d.y;
+    }
+  }
+}
+
+template <typename Real>
+__device__ __forceinline__ void sts_swz(unsigned char* base, int idx, Real v) {
+  *reinterpret_cast<Real*>(base + swz128((uint32_t)(idx * sizeof(Real)))) = v;
+}
+
+struct FastGeom {
+  int slot_bytes;  // ring slot size (multiple of 1024)
+  int vec_bytes;   // one swizzled vector of m_pad reals (multiple of 1024)
+};
+
+template <int K, int NW, int VPT, typename Real>
+struct FastSmem {
+  static constexpr int NT = 32 * NW;
+  static size_t bytes(int slot_bytes, int vec_bytes, int stages) {
+    size_t b = 1024;  // alignment slack
+    b += (size_t)stages * slot_bytes;
+    b += 2 * (size_t)vec_bytes;                     // cy hi, lo
+    b += 8 * (size_t)stages;                        // mbarriers
+    b += sizeof(Real) * 2 * NW * 2 * (K + 1);       // warp totals [2][NW][2][K+1]
+    b += sizeof(Real) * 2 * NW * (K + 2) + 64;      // polynomials [2][NW][K+2]
+    return b;
+  }
+};
+
+template <int K, int NW, int VPT, typename Real>
+__global__ void __launch_bounds__(32 * (NW + 1), 1)
+    k1c_fast_rows(const __grid_constant__ CUtensorMap tmT, const Real* __restrict__ T, Real* __restrict__ G, int n,
+                  int m, int R, const Real* __restrict__ q, const Real* __restrict__ cxh,
+                  const Real* __restrict__ cxl, const Real* __restrict__ cyh, const Real* __restrict__ cyl, Real scale,
+                  int use_tma, int stages, int slot_bytes, int vec_bytes, int box_cols, int ncopies,
+                  unsigned* status) {
+  using A = typename AccT<Real>::type;
+  constexpr int NT = 32 * NW;        // compute threads
+  constexpr int ALL = NT + 32;       // + scan warp
+  constexpr int SEG = 32 * VPT;      // columns per compute warp
+  constexpr Real CK = (K & 1) ? (Real)2 : (Real)0;
+  static_assert(K == 1 || K == 2, "fast row kernel handles k = 1, 2");
+
+  extern __shared__ unsigned char smem_dyn[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
+  unsigned char* ring = sm;
+  unsigned char* cyH = ring + (size_t)stages * slot_bytes;
+  unsigned char* cyL = cyH + vec_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(cyL + vec_bytes);
+  Real* wtot = reinterpret_cast<Real*>(bars + stages);             // [2][NW][2][K+1]
+  Real* zw = wtot + 2 * NW * 2 * (K + 1);                          // [2][NW][K+2]
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int a = blockIdx.x;
+  const int s = a * R;
+  const int Ra = min(R, n - s);
+  const int m_pad = vec_bytes / (int)sizeof(Real);
+
+  // Set-up: barriers, constant term of the columns into swizzled smem.
+  if (tid == 0 && use_tma) {
+    for (int st = 0; st < stages; ++st) mbar_init(&bars[st], 1);
+    fence_mbar_init();
+  }
+  for (int p = tid; p < m_pad; p += ALL) {
+    sts_swz<Real>(cyH, p, p < m ? cyh[p] : (Real)0);
+    sts_swz<Real>(cyL, p, p < m ? cyl[p] : (Real)0);
+  }
+  __syncthreads();
+
+  if (warp == NW) {
+    // ---------------- scan warp ----------------
+    auto issue = [&](int row, int slot) {
+      mbar_arrive_expect_tx(&bars[slot], (unsigned)(m * sizeof(Real)));
+      for (int c = 0; c < ncopies; ++c)
+        tma_load_3d(ring + (size_t)slot * slot_bytes + (size_t)c * box_cols * 128, &tmT, 0, c * box_cols, row, &bars[slot]);
+    };
+    if (use_tma && lane == 0) {
+      for (int st = 0; st < stages - 1 && st < Ra; ++st) issue(s + st, st);
+    }
+    for (int t = 0; t < Ra; ++t) {
+      named_sync(1 + (t & 1), ALL);  // totals(t) posted
+      if (use_tma && lane == 0) {
+        const int nt = t + stages - 1;
+        if (nt < Ra) issue(s + nt, nt % stages);
+      }
+      const Real* wt = wtot + (t & 1) * NW * 2 * (K + 1);
+      A W[K + 1], V[K + 1];
+      // Warp `lane`'s moments about its end (W) and about its start (V).
+#pragma unroll
+      for (int r = 0; r <= K; ++r) {
+        W[r] = (lane < NW) ? acc_of(wt[lane * 2 * (K + 1) + r]) : acc_zero((A*)nullptr);
+        V[r] = (lane < NW) ? acc_of(wt[lane * 2 * (K + 1) + K + 1 + r]) : acc_zero((A*)nullptr);
+      }
+#pragma unroll
+      for (int d = 1; d < NW; d <<= 1) {
+        A o[K + 1], ob[K + 1];
+#pragma unroll
+        for (int r = 0; r <= K; ++r) {
+          o[r] = acc_shfl_up(W[r], d);
+          ob[r] = acc_shfl_down(V[r], d);
+        }
+        shift_acc_pow2<K>(o, (Real)(d * SEG));
+        shift_acc_pow2<K>(ob, (Real)(d * SEG));
+        if (lane >= d) {
+#pragma unroll
+          for (int r = 0; r <= K; ++r) W[r] = acc_add(W[r], o[r]);
+        }
+        if (lane + d < NW) {
+#pragma unroll
+          for (int r = 0; r <= K; ++r) V[r] = acc_add(V[r], ob[r]);
+        }
+      }
+      // Exclusive forward prefix (about the warp start); V is already the
+      // inclusive suffix about the warp start.
+      A P[K + 1];
+#pragma unroll
+      for (int r = 0; r <= K; ++r) {
+        P[r] = acc_shfl_up(W[r], 1);
+        if (lane == 0) P[r] = acc_zero((A*)nullptr);
+      }
+      if (lane < NW) {
+        Real* z = zw + ((t & 1) * NW + lane) * (K + 2);
+        // ZW_e = C(K, K-e) [P_{K-e} + (-1)^e V_{K-e}]
+        const A z0 = acc_add(P[K], V[K]);
+        z[0] = (Real)acc_hi(z0);
+        z[1] = (Real)acc_lo(z0);
+#pragma unroll
+        for (int e = 1; e <= K; ++e) {
+          const int u = K - e;
+          A t2 = (e & 1) ? acc_sub(P[u], V[u]) : acc_add(P[u], V[u]);
+          z[1 + e] = (Real)binom(K, u) * (Real)acc_round(t2);
+        }
+      }
+      named_arrive(3 + (t & 1), ALL);  // poly(t) posted
+    }
+    return;
+  }
+
+  // ---------------- compute warps ----------------
+  const int c0 = tid * VPT;
+  const int o0 = lane * VPT;  // offset inside the warp segment
+  // Column state: K = 1 difference form (y_t, b_t); K = 2 Horner (q0, q1, q2).
+  Real cst[VPT][K + 1];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    const int p = c0 + v;
+#pragma unroll
+    for (int e = 0; e <= K; ++e) cst[v][e] = (p < m) ? q[((size_t)a * (K + 1) + e) * m + p] : (Real)0;
+  }
+  Real fl_prev[VPT];  // in-chunk forward states of the pending row (odd K)
+  Real ex_prev[K + 1];
+  Real cxh_prev = 0, cxl_prev = 0;
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) fl_prev[v] = 0;
+#pragma unroll
+  for (int r = 0; r <= K; ++r) ex_prev[r] = 0;
+
+  for (int t = 0; t <= Ra; ++t) {
+    Real fl_new[VPT];
+    Real ex_new[K + 1];
+    Real cxh_new = 0, cxl_new = 0;
+    if (t < Ra) {
+      // ---- phase A(t)
+      const int i = s + t;
+      const unsigned char* xr;
+      if (use_tma) {
+        const int slot = t % stages;
+        mbar_wait_bounded(&bars[slot], (unsigned)((t / stages) & 1), status);
+        xr = ring + (size_t)slot * slot_bytes;
+      } else {
+        unsigned char* dst = ring + (size_t)(t & 1) * slot_bytes;
+        const Real* src = T + (size_t)i * m;
+        for (int p = tid; p < m_pad; p += NT) sts_swz<Real>(dst, p, p < m ? src[p] : (Real)0);
+        named_sync(5, NT);
+        xr = dst;
+      }
+      cxh_new = cxh[i];
+      cxl_new = cxl[i];
+      Real x[VPT];
+      lds_swz<Real, VPT>(xr, c0, x);
+      Real y[VPT];
+      const Real tr = (Real)t;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        if constexpr (K == 1) {
+          y[v] = cst[v][0];
+          cst[v][1] = fma((Real)2, x[v], cst[v][1]);
+          cst[v][0] += cst[v][1];
+        } else {
+          y[v] = fma(fma(cst[v][2], tr, cst[v][1]), tr, cst[v][0]);
+        }
+        if (c0 + v >= m) y[v] = 0;
+      }
+      // In-chunk forward walk (odd K), the chunk's moments about its end
+      // (agg, forward convention) and about its start (bag).
+      Real agg[K + 1], bag[K + 1];
+#pragma unroll
+      for (int r = 0; r <= K; ++r) {
+        agg[r] = 0;
+        bag[r] = 0;
+      }
+      if constexpr (K & 1) {
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          fl_new[v] = agg[K];
+          pascal_step<K>(agg, y[v]);
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) {
+          const Real w = (Real)(VPT - v);
+          agg[0] += y[v];
+          agg[1] = fma(w, y[v], agg[1]);
+          agg[2] = fma(w * w, y[v], agg[2]);
+          fl_new[v] = 0;
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        const Real w = (Real)v;
+        bag[0] += y[v];
+        bag[1] = fma(w, y[v], bag[1]);
+        if constexpr (K >= 2) bag[2] = fma(w * w, y[v], bag[2]);
+      }
+      // Butterfly over the lanes: the warp's moments about its start.
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        Real o[K + 1];
+#pragma unroll
+        for (int r = 0; r <= K; ++r) o[r] = __shfl_xor_sync(0xffffffffu, bag[r], d);
+        // The right block's moments move to the left block's start.
+        if (lane & d) {
+#pragma unroll
+          for (int r = 0; r <= K; ++r) {
+            const Real tmp = o[r];
+            o[r] = bag[r];
+            bag[r] = tmp;
+          }
+        }
+        shift_real<K>(o, (Real)(d * VPT));
+#pragma unroll
+        for (int r = 0; r <= K; ++r) bag[r] += o[r];
+      }
+      // Lane scan (float), inclusive, about my chunk end.
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        Real o[K + 1];
+#pragma unroll
+        for (int r = 0; r <= K; ++r) o[r] = __shfl_up_sync(0xffffffffu, agg[r], d);
+        shift_real<K>(o, (Real)(d * VPT));
+        if (lane >= d) {
+#pragma unroll
+          for (int r = 0; r <= K; ++r) agg[r] += o[r];
+        }
+      }
+#pragma unroll
+      for (int r = 0; r <= K; ++r) {
+        ex_new[r] = __shfl_up_sync(0xffffffffu, agg[r], 1);
+        if (lane == 0) ex_new[r] = 0;
+      }
+      if (lane == 31) {
+        Real* wt = wtot + ((t & 1) * NW + warp) * 2 * (K + 1);
+#pragma unroll
+        for (int r = 0; r <= K; ++r) wt[r] = agg[r];
+      }
+      if (lane == 0) {
+        Real* wt = wtot + ((t & 1) * NW + warp) * 2 * (K + 1) + (K + 1);
+#pragma unroll
+        for (int r = 0; r <= K; ++r) wt[r] = bag[r];
+      }
+      named_arrive(1 + (t & 1), ALL);
+    }
+    if (t >= 1) {
+      // ---- phase B(t-1)
+      const int tp = t - 1;
+      const int i = s + tp;
+      named_sync(3 + (tp & 1), ALL);
+      const Real* z = zw + ((tp & 1) * NW + warp) * (K + 2);
+      Real ZW[K + 2];
+#pragma unroll
+      for (int e = 0; e < K + 2; ++e) ZW[e] = z[e];
+      // Coefficients in v of z at offset o0 + v:
+      //   ZT_e = sum_{e' >= e} C(e', e) ZW_{e'} o0^{e'-e} + c_K C(K, K-e) ex_{K-e}
+      // (ZW_{0} in two parts; ZW[1] is its low part, ZW[1+e] the others).
+      Real ZT[K + 1];
+      const Real of = (Real)o0;
+#pragma unroll
+      for (int e = 1; e <= K; ++e) {
+        Real acc = 0;
+        Real op = 1;
+#pragma unroll
+        for (int e2 = e; e2 <= K; ++e2) {
+          acc = fma((Real)binom(e2, e) * op, ZW[1 + e2], acc);
+          op *= of;
+        }
+        if constexpr (K & 1) acc = fma(CK * (Real)binom(K, K - e), ex_prev[K - e], acc);
+        ZT[e] = acc;
+      }
+      Real small0 = ZW[1];
+      {
+        Real op = of;
+#pragma unroll
+        for (int e2 = 1; e2 <= K; ++e2) {
+          small0 = fma(op, ZW[1 + e2], small0);
+          op *= of;
+        }
+        if constexpr (K & 1) small0 = fma(CK, ex_prev[K], small0);
+      }
+      const Real big0 = fma(-scale, ZW[0], cxh_prev);
+      Real* grow = G + (size_t)i * m + c0;
+      const bool vec_store = (c0 + VPT <= m) && ((((uintptr_t)grow) & 15) == 0);
+      constexpr int PER = 16 / sizeof(Real);
+      // Four (float) or two (double) columns at a time: their constant term
+      // from swizzled shared memory, the outputs straight to global memory.
+#pragma unroll
+      for (int j = 0; j < VPT / PER; ++j) {
+        const uint32_t b = (uint32_t)((c0 + j * PER) * sizeof(Real));
+        const float4 hv = *reinterpret_cast<const float4*>(cyH + swz128(b));
+        const float4 lv = *reinterpret_cast<const float4*>(cyL + swz128(b));
+        const Real* ch = reinterpret_cast<const Real*>(&hv);
+        const Real* cl = reinterpret_cast<const Real*>(&lv);
+        Real out[PER];
+#pragma unroll
+        for (int w = 0; w < PER; ++w) {
+          const int v = j * PER + w;
+          const Real vv = (Real)v;
+          Real sm2 = ZT[K];
+#pragma unroll
+          for (int e = K - 1; e >= 1; --e) sm2 = fma(sm2, vv, ZT[e]);
+          sm2 = fma(sm2, vv, small0);
+          if constexpr (K & 1) sm2 = fma(CK, fl_prev[v], sm2);
+          out[w] = (big0 + ch[w]) + fma(-scale, sm2, cxl_prev + cl[w]);
+        }
+        if (vec_store) {
+          if constexpr (sizeof(Real) == 4)
+            *reinterpret_cast<float4*>(grow + j * PER) = make_float4(out[0], out[1], out[2], out[3]);
+          else
+            *reinterpret_cast<double2*>(grow + j * PER) = make_double2(out[0], out[1]);
+        } else {
+#pragma unroll
+          for (int w = 0; w < PER; ++w)
+            if (c0 + j * PER + w < m) grow[j * PER + w] = out[w];
+        }
+      }
+    }
+    if (t < Ra) {
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) fl_prev[v] = fl_new[v];
+#pragma unroll
+      for (int r = 0; r <= K; ++r) ex_prev[r] = ex_new[r];
+      cxh_prev = cxh_new;
+      cxl_prev = cxl_new;
+    }
+  }
+}
+
+}  // namespace gw

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "gw_common.cuh"
 #include "gw_internal.h"
@@ -711,6 +712,12 @@ __global__ void __launch_bounds__(NT, 1)
   }
 }
 
+}  // namespace gw
+
+#include "grad1d_fast.cuh"
+
+namespace gw {
+
 // ---------------------------------------------------------------------------
 // Host launcher for one exponent K.
 // ---------------------------------------------------------------------------
@@ -771,6 +778,31 @@ int launch_k1c(const Grad1DArgs& g, const K1Layout& L, char* ws, int use_tma, cu
   kern<<<L.bands.B, NT, smem, st>>>((const Real*)g.T, (Real*)g.G, g.n, g.m, L.bands.R,
                                      (const Real*)(ws + L.q_off), cx, cx + g.n, cy, cy + g.m, scale, use_tma,
                                      stages, m_pad, g.status);
+  return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+}
+
+template <int K, int NW, int VPT, typename Real>
+int launch_k1c_fast(const Grad1DArgs& g, const K1Layout& L, char* ws, cudaStream_t st) {
+  CUtensorMap tm;
+  memset(&tm, 0, sizeof tm);
+  int box_cols = 0;
+  const int use_tma = ((((uintptr_t)g.T) & 15) == 0) && encode_rows_tmap(&tm, g.T, g.n, g.m, sizeof(Real), &box_cols);
+  const int cover = 32 * NW * VPT;
+  const int vec_bytes = (int)align_up((size_t)cover * sizeof(Real), 1024);
+  const int slot_bytes = vec_bytes;
+  int stages = 2;
+  if (use_tma) stages = std::max(2, std::min(4, (200 * 1024 - 2 * vec_bytes) / slot_bytes));
+  const size_t smem = FastSmem<K, NW, VPT, Real>::bytes(slot_bytes, vec_bytes, stages);
+  auto kern = k1c_fast_rows<K, NW, VPT, Real>;
+  TraceScope ts(g.tracer, "k1c_fast_rows", st);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return GW_ERR_CUDA;
+  const Real scale = (Real)(2.0 * g.out_scale * std::pow(g.hx, g.k) * std::pow(g.hy, g.k));
+  const Real* cx = (const Real*)(ws + L.cx_off);
+  const Real* cy = (const Real*)(ws + L.cy_off);
+  kern<<<L.bands.B, 32 * (NW + 1), smem, st>>>(tm, (const Real*)g.T, (Real*)g.G, g.n, g.m, L.bands.R,
+                                                (const Real*)(ws + L.q_off), cx, cx + g.n, cy, cy + g.m, scale,
+                                                use_tma, stages, slot_bytes, vec_bytes, box_cols, 1, g.status);
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }
 
@@ -850,14 +882,26 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
     wy = c;
   }
   const int dt = sizeof(Real) == 4 ? GW_F32 : GW_F64;
-  int rc = marg_const_launch(wx, n, K, std::pow(g.hx, 2 * K) * g.out_scale, ws + L.cx_off, dt,
-                             (double*)(ws + L.partx_off), st, g.tracer);
-  if (rc != GW_OK) return rc;
-  rc = marg_const_launch(wy, m, K, std::pow(g.hy, 2 * K) * g.out_scale, ws + L.cy_off, dt,
-                         (double*)(ws + L.party_off), st, g.tracer);
+  int rc = marg_const2_launch(wx, n, std::pow(g.hx, 2 * K) * g.out_scale, ws + L.cx_off, wy, m,
+                              std::pow(g.hy, 2 * K) * g.out_scale, ws + L.cy_off, K, dt,
+                              (double*)(ws + L.partx_off), st, g.tracer);
   if (rc != GW_OK) return rc;
 
   // k1c
+  if constexpr (K <= 2) {
+    if (!g.force_generic) {
+      if constexpr (sizeof(Real) == 4) {
+        if (m <= 512) return launch_k1c_fast<K, 4, 4, Real>(g, L, ws, st);
+        if (m <= 1024) return launch_k1c_fast<K, 8, 4, Real>(g, L, ws, st);
+        if (m <= 2048) return launch_k1c_fast<K, 8, 8, Real>(g, L, ws, st);
+        if (m <= 4096) return launch_k1c_fast<K, 16, 8, Real>(g, L, ws, st);
+        if (m <= 8192) return launch_k1c_fast<K, 16, 16, Real>(g, L, ws, st);
+      } else {
+        if (m <= 1024) return launch_k1c_fast<K, 8, 4, Real>(g, L, ws, st);
+        if (m <= 4096) return launch_k1c_fast<K, 16, 8, Real>(g, L, ws, st);
+      }
+    }
+  }
   const int use_tma = ((m * sizeof(Real)) % 16 == 0) && ((((uintptr_t)g.T) & 15) == 0);
   if constexpr (sizeof(Real) == 4) {
     if (m <= 512) return launch_k1c<K, 128, 4, Real>(g, L, ws, use_tma, st);

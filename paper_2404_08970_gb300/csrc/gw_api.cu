@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -78,6 +79,7 @@ struct gw_ctx {
   size_t ws_bytes = 0;
   unsigned* status = nullptr;  // device status word
   EventTracer* tracer = nullptr;  // non-null while profiling is on
+  int force_generic = 0;          // GW_FORCE_GENERIC set at creation: block-scan row kernel only
   gw::Tracer* tr() { return tracer; }
 };
 
@@ -144,6 +146,8 @@ gw_status gw_ctx_create(gw_ctx** out, int device) {
   }
   gw_ctx* c = new gw_ctx();
   c->device = device;
+  const char* fg = getenv("GW_FORCE_GENERIC");
+  c->force_generic = (fg && fg[0] && fg[0] != '0') ? 1 : 0;
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   e = cudaMalloc(&c->status, sizeof(unsigned));
   if (e != cudaSuccess) {
@@ -259,6 +263,7 @@ gw_status gw_grad(gw_ctx* c, const gw_problem* p, const double* d_u, const doubl
   a.status = c->status;
   a.num_sms = c->num_sms;
   a.tracer = c->tr();
+  a.force_generic = c->force_generic;
   s = ensure_ws(c, gw::grad1d_workspace_bytes(a.n, a.m, a.k, a.dtype, a.num_sms));
   if (s != GW_OK) return s;
   int rc = gw::grad1d_launch(a, c->ws, c->ws_bytes);

@@ -71,7 +71,14 @@ struct Grad1DArgs {
   unsigned* status;     // device status word
   int num_sms;
   Tracer* tracer;       // nullable
+  int force_generic;    // 1: use the block-scan row kernel even where the warp-specialised one applies
 };
+
+// Encodes a TMA tensor map over the rows of an n x m row-major array of
+// elem_bytes-sized reals, viewed as [n][m / E][E] with E*elem_bytes = 128,
+// 128-byte swizzle, box {E, box_cols, 1}.  False if m is not a multiple of E
+// or the driver rejects the map.
+bool encode_rows_tmap(void* tmap, const void* base, int n, int m, int elem_bytes, int* box_cols);
 
 // Bytes of workspace the structured 1D gradient needs.
 size_t grad1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms);
@@ -89,5 +96,9 @@ int grad1d_launch_k3(const Grad1DArgs& a, void* ws, size_t ws_bytes);
 size_t marg_part_doubles(int len, int k);
 int marg_const_launch(const double* w, int len, int k, double h, void* out, int dtype,
                       double* part, cudaStream_t stream, Tracer* tracer = nullptr);
+// Both constant terms in one pair of launches; part must hold
+// marg_part_doubles(n, k) + marg_part_doubles(m, k) doubles.
+int marg_const2_launch(const double* wx, int n, double fx, void* outx, const double* wy, int m, double fy,
+                       void* outy, int k, int dtype, double* part, cudaStream_t stream, Tracer* tracer);
 
 }  // namespace gw

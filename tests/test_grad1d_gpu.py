@@ -96,3 +96,27 @@ def test_grad1d_invalid_arguments():
         c.gw_grad(p, None, None, T, T, L.GW_MARG_EXACT)  # overlap
     with pytest.raises(L.GWError):
         c.gw_grad(p, None, None, T, G, L.GW_MARG_TARGET)  # missing marginals
+
+
+def test_grad1d_generic_row_kernel():
+    """The block-scan row kernel (used for k = 3 and rows above 8192) on the
+    k = 1, 2 cases the warp-specialised kernel normally takes."""
+    import os
+    from paper_2404_08970_gb300 import _lib as L
+    import torch
+    os.environ["GW_FORCE_GENERIC"] = "1"
+    try:
+        c = L.Context(0)
+    finally:
+        del os.environ["GW_FORCE_GENERIC"]
+    for (n, m, k) in [(100, 257, 1), (64, 1024, 2), (300, 4096, 1), (129, 8192, 2)]:
+        u, v, T = _case(n, m, 31 * n + k)
+        Tc = T.astype(np.float32)
+        dT = torch.from_numpy(Tc).cuda()
+        dG = torch.empty_like(dT)
+        prob = L.problem(dim=1, nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=k, dtype=L.GW_F32)
+        c.gw_grad(prob, torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), dT, dG, L.GW_MARG_TARGET)
+        c.gw_ctx_check()
+        Gs = U.oracle_grad_1d(Tc.astype(np.float64), u, v, k, 1.0 / n, 1.0 / m, "target")
+        assert U.relerr(dG.double().cpu().numpy(), Gs) <= TOL["f32"], (n, m, k)
+    c.close()
