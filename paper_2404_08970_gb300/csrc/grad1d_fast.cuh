@@ -81,6 +81,7 @@ struct FastSmem {
     b += 8 * (size_t)stages;                        // mbarriers
     b += sizeof(Real) * 2 * NW * 2 * (K + 1);       // warp totals [2][NW][2][K+1]
     b += sizeof(Real) * 2 * NW * (K + 2) + 64;      // polynomials [2][NW][K+2]
+    b += (K & 1) ? sizeof(Real) * (size_t)VPT * NT + 16 : 0;  // pending in-chunk forward states
     return b;
   }
 };
@@ -107,6 +108,8 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(cyL + vec_bytes);
   Real* wtot = reinterpret_cast<Real*>(bars + stages);             // [2][NW][2][K+1]
   Real* zw = wtot + 2 * NW * 2 * (K + 1);                          // [2][NW][K+2]
+  // In-chunk forward states of the pending row, [VPT/PER][NT] 16-byte chunks.
+  float4* flbuf = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(zw + 2 * NW * (K + 2)) + 15) & ~(uintptr_t)15);
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -125,6 +128,10 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
     sts_swz<Real>(cyH, p, p < m ? cyh[p] : (Real)0);
     sts_swz<Real>(cyL, p, p < m ? cyl[p] : (Real)0);
   }
+  // Columns m .. m_pad of every ring slot stay zero (TMA writes only the
+  // first m), so padded columns contribute nothing without per-element masks.
+  for (int st = 0; st < stages; ++st)
+    for (int p = m + tid; p < m_pad; p += ALL) sts_swz<Real>(ring + (size_t)st * slot_bytes, p, (Real)0);
   __syncthreads();
 
   if (warp == NW) {
@@ -207,11 +214,9 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
 #pragma unroll
     for (int e = 0; e <= K; ++e) cst[v][e] = (p < m) ? q[((size_t)a * (K + 1) + e) * m + p] : (Real)0;
   }
-  Real fl_prev[VPT];  // in-chunk forward states of the pending row (odd K)
+  constexpr int PER = 16 / sizeof(Real);
   Real ex_prev[K + 1];
   Real cxh_prev = 0, cxl_prev = 0;
-#pragma unroll
-  for (int v = 0; v < VPT; ++v) fl_prev[v] = 0;
 #pragma unroll
   for (int r = 0; r <= K; ++r) ex_prev[r] = 0;
 
@@ -236,51 +241,44 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
       }
       cxh_new = cxh[i];
       cxl_new = cxl[i];
-      Real x[VPT];
-      lds_swz<Real, VPT>(xr, c0, x);
-      Real y[VPT];
-      const Real tr = (Real)t;
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        if constexpr (K == 1) {
-          y[v] = cst[v][0];
-          cst[v][1] = fma((Real)2, x[v], cst[v][1]);
-          cst[v][0] += cst[v][1];
-        } else {
-          y[v] = fma(fma(cst[v][2], tr, cst[v][1]), tr, cst[v][0]);
-        }
-        if (c0 + v >= m) y[v] = 0;
-      }
-      // In-chunk forward walk (odd K), the chunk's moments about its end
-      // (agg, forward convention) and about its start (bag).
+      // Column recursion and in-chunk forward walk, 16 bytes of the row at a
+      // time; also the chunk's moments about its end (agg) and start (bag).
       Real agg[K + 1], bag[K + 1];
 #pragma unroll
       for (int r = 0; r <= K; ++r) {
         agg[r] = 0;
         bag[r] = 0;
       }
-      if constexpr (K & 1) {
+      const Real tr = (Real)t;
 #pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-          fl_new[v] = agg[K];
-          pascal_step<K>(agg, y[v]);
+      for (int j = 0; j < VPT / PER; ++j) {
+        const float4 xv = *reinterpret_cast<const float4*>(xr + swz128((uint32_t)((c0 + j * PER) * sizeof(Real))));
+        const Real* x = reinterpret_cast<const Real*>(&xv);
+#pragma unroll
+        for (int w = 0; w < PER; ++w) {
+          const int v = j * PER + w;
+          Real y;
+          if constexpr (K == 1) {
+            y = cst[v][0];
+            cst[v][1] = fma((Real)2, x[w], cst[v][1]);
+            cst[v][0] += cst[v][1];
+          } else {
+            y = fma(fma(cst[v][2], tr, cst[v][1]), tr, cst[v][0]);
+          }
+          if constexpr (K & 1) {
+            fl_new[v] = agg[K];
+            pascal_step<K>(agg, y);
+          } else {
+            const Real wv = (Real)(VPT - v);
+            agg[0] += y;
+            agg[1] = fma(wv, y, agg[1]);
+            agg[2] = fma(wv * wv, y, agg[2]);
+          }
+          const Real vv = (Real)v;
+          bag[0] += y;
+          bag[1] = fma(vv, y, bag[1]);
+          if constexpr (K >= 2) bag[2] = fma(vv * vv, y, bag[2]);
         }
-      } else {
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) {
-          const Real w = (Real)(VPT - v);
-          agg[0] += y[v];
-          agg[1] = fma(w, y[v], agg[1]);
-          agg[2] = fma(w * w, y[v], agg[2]);
-          fl_new[v] = 0;
-        }
-      }
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        const Real w = (Real)v;
-        bag[0] += y[v];
-        bag[1] = fma(w, y[v], bag[1]);
-        if constexpr (K >= 2) bag[2] = fma(w * w, y[v], bag[2]);
       }
       // Butterfly over the lanes: the warp's moments about its start.
 #pragma unroll
@@ -369,7 +367,6 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
       const Real big0 = fma(-scale, ZW[0], cxh_prev);
       Real* grow = G + (size_t)i * m + c0;
       const bool vec_store = (c0 + VPT <= m) && ((((uintptr_t)grow) & 15) == 0);
-      constexpr int PER = 16 / sizeof(Real);
       // Four (float) or two (double) columns at a time: their constant term
       // from swizzled shared memory, the outputs straight to global memory.
 #pragma unroll
@@ -379,6 +376,9 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
         const float4 lv = *reinterpret_cast<const float4*>(cyL + swz128(b));
         const Real* ch = reinterpret_cast<const Real*>(&hv);
         const Real* cl = reinterpret_cast<const Real*>(&lv);
+        float4 flv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (K & 1) flv = flbuf[j * NT + tid];
+        const Real* flp = reinterpret_cast<const Real*>(&flv);
         Real out[PER];
 #pragma unroll
         for (int w = 0; w < PER; ++w) {
@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
 #pragma unroll
           for (int e = K - 1; e >= 1; --e) sm2 = fma(sm2, vv, ZT[e]);
           sm2 = fma(sm2, vv, small0);
-          if constexpr (K & 1) sm2 = fma(CK, fl_prev[v], sm2);
+          if constexpr (K & 1) sm2 = fma(CK, flp[w], sm2);
           out[w] = (big0 + ch[w]) + fma(-scale, sm2, cxl_prev + cl[w]);
         }
         if (vec_store) {
@@ -404,8 +404,16 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
       }
     }
     if (t < Ra) {
+      if constexpr (K & 1) {
 #pragma unroll
-      for (int v = 0; v < VPT; ++v) fl_prev[v] = fl_new[v];
+        for (int j = 0; j < VPT / PER; ++j) {
+          float4 f;
+          Real* fr = reinterpret_cast<Real*>(&f);
+#pragma unroll
+          for (int w = 0; w < PER; ++w) fr[w] = fl_new[j * PER + w];
+          flbuf[j * NT + tid] = f;
+        }
+      }
 #pragma unroll
       for (int r = 0; r <= K; ++r) ex_prev[r] = ex_new[r];
       cxh_prev = cxh_new;

@@ -64,19 +64,29 @@ __device__ __forceinline__ ff acc_mul_int(ff S, unsigned long long c) {
 }
 __device__ __forceinline__ double acc_mul_int(double S, unsigned long long c) { return S * (double)c; }
 
+// a * c for a float c that is exact (an integer below 2^24).
+__device__ __forceinline__ ff acc_mulf(ff a, float c) { return ff_mul(a, c); }
+__device__ __forceinline__ double acc_mulf(double a, double c) { return a * c; }
+template <typename A> struct AccReal;
+template <> struct AccReal<ff> { using type = float; };
+template <> struct AccReal<double> { using type = double; };
+
 // Shifts moments measured at a position x to position x + d (or, for moments
 // of elements to the right, from x to x - d):
-//   S_r <- sum_{u<=r} C(r,u) d^{r-u} S_u.
+//   S_r <- sum_{u<=r} C(r,u) d^{r-u} S_u,
+// evaluated by Horner in d (d < 2^24, so every multiplier is exact).
 template <int K, typename A>
 __device__ __forceinline__ void shift_acc(A (&S)[K + 1], long long d) {
+  using F = typename AccReal<A>::type;
+  const F df = (F)d;
 #pragma unroll
   for (int r = K; r >= 1; --r) {
-    A acc = S[r];
+    A acc = S[0];
 #pragma unroll
-    for (int u = 0; u < r; ++u) {
-      unsigned long long c = (unsigned long long)binom(r, u);
-      for (int e = 0; e < r - u; ++e) c *= (unsigned long long)d;
-      acc = acc_add(acc, acc_mul_int(S[u], c));
+    for (int u = 1; u <= r; ++u) {
+      acc = acc_mulf(acc, df);
+      const int c = binom(r, u);
+      acc = acc_add(acc, c == 1 ? S[u] : acc_mulf(S[u], (F)c));
     }
     S[r] = acc;
   }
@@ -139,7 +149,8 @@ __device__ __forceinline__ void shift_acc_pow2(A (&S)[K + 1], Real d) {
     Real dp = d;
 #pragma unroll
     for (int u = r - 1; u >= 0; --u) {
-      acc = acc_add(acc, acc_pow2(acc_mul_int(S[u], (unsigned long long)binom(r, u)), dp));
+      const int c = binom(r, u);
+      acc = acc_add(acc, acc_pow2(c == 1 ? S[u] : acc_mulf(S[u], (typename AccReal<A>::type)c), dp));
       dp *= d;
     }
     S[r] = acc;
@@ -286,19 +297,20 @@ struct K1bOps {
 #pragma unroll
     for (int r = 1; r <= K; ++r) M[r] = acc_of(base[(size_t)(r + 1) * m]);
   }
-  // End-relative band moments nu_r = sum_t (R_a - t)^r x = sum_u C(r,u) R^{r-u} (-1)^u mu_u.
+  // End-relative band moments nu_r = sum_t (R_a - t)^r x = sum_u C(r,u) R^{r-u} (-1)^u mu_u,
+  // by Horner in R.
   static __device__ __forceinline__ void nu_of(const A (&M)[K + 1], long long Ra, A (&N)[K + 1]) {
+    using F = typename AccReal<A>::type;
+    const F rf = (F)Ra;
     N[0] = M[0];
 #pragma unroll
     for (int r = 1; r <= K; ++r) {
-      unsigned long long c0 = 1;
-      for (int e = 0; e < r; ++e) c0 *= (unsigned long long)Ra;
-      A acc = acc_mul_int(M[0], c0);
+      A acc = M[0];
 #pragma unroll
       for (int u = 1; u <= r; ++u) {
-        unsigned long long c = (unsigned long long)binom(r, u);
-        for (int e = 0; e < r - u; ++e) c *= (unsigned long long)Ra;
-        A term = (c == 1) ? M[u] : acc_mul_int(M[u], c);
+        acc = acc_mulf(acc, rf);
+        const int c = binom(r, u);
+        const A term = c == 1 ? M[u] : acc_mulf(M[u], (F)c);
         acc = (u & 1) ? acc_sub(acc, term) : acc_add(acc, term);
       }
       N[r] = acc;
@@ -381,17 +393,19 @@ __global__ void __launch_bounds__(256) k1b_walk(const Real* __restrict__ mu, int
   }
   for (int a = a0; a < a1; ++a) {
     const long long sa = (long long)a * R;
-    const unsigned long long dn = (unsigned long long)(n - sa);
-    // Moments about s_a of the whole column, then Bk = those minus (-1)^u A.
+    using F = typename AccReal<A>::type;
+    const F dn = (F)(n - sa);
+    // Moments about s_a of the whole column (Horner in n - s_a, alternating
+    // signs), then Bk = those minus (-1)^u A.
     A Bk[K + 1];
 #pragma unroll
     for (int u = 0; u <= K; ++u) {
-      A acc = acc_zero((A*)nullptr);
+      A acc = Nt[0];
 #pragma unroll
-      for (int w = 0; w <= u; ++w) {
-        unsigned long long c = (unsigned long long)binom(u, w);
-        for (int e = 0; e < u - w; ++e) c *= dn;
-        A term = (c == 1) ? Nt[w] : acc_mul_int(Nt[w], c);
+      for (int w = 1; w <= u; ++w) {
+        acc = acc_mulf(acc, dn);
+        const int c = binom(u, w);
+        const A term = c == 1 ? Nt[w] : acc_mulf(Nt[w], (F)c);
         acc = (w & 1) ? acc_sub(acc, term) : acc_add(acc, term);
       }
       Bk[u] = (u & 1) ? acc_add(acc, Af[u]) : acc_sub(acc, Af[u]);
@@ -401,7 +415,7 @@ __global__ void __launch_bounds__(256) k1b_walk(const Real* __restrict__ mu, int
       const int r = K - e;
       A t = (e & 1) ? acc_sub(Af[r], Bk[r]) : acc_add(Af[r], Bk[r]);
       const int cb = binom(K, r);
-      if (cb != 1) t = acc_mul_int(t, (unsigned long long)cb);
+      if (cb != 1) t = acc_mulf(t, (typename AccReal<A>::type)cb);
       q[((size_t)a * (K + 1) + e) * m + p] = (Real)acc_round(t);
     }
     const long long Ra = min(R, n - a * R);
@@ -791,7 +805,8 @@ int launch_k1c_fast(const Grad1DArgs& g, const K1Layout& L, char* ws, cudaStream
   const int vec_bytes = (int)align_up((size_t)cover * sizeof(Real), 1024);
   const int slot_bytes = vec_bytes;
   int stages = 2;
-  if (use_tma) stages = std::max(2, std::min(4, (200 * 1024 - 2 * vec_bytes) / slot_bytes));
+  const int fl_bytes = (K & 1) ? (int)(sizeof(Real) * VPT * 32 * NW) : 0;
+  if (use_tma) stages = std::max(2, std::min(4, (200 * 1024 - 2 * vec_bytes - fl_bytes) / slot_bytes));
   const size_t smem = FastSmem<K, NW, VPT, Real>::bytes(slot_bytes, vec_bytes, stages);
   auto kern = k1c_fast_rows<K, NW, VPT, Real>;
   TraceScope ts(g.tracer, "k1c_fast_rows", st);
