@@ -59,6 +59,75 @@ __device__ __forceinline__ double warp_sum_d(double x) {
   return x;
 }
 
+__device__ __forceinline__ ff warp_sum_ff(ff x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    ff y{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+    x = ff_add(x, y);
+  }
+  return x;
+}
+
+// Float output: float-float arithmetic on the FP32 pipe (the constant term
+// keeps about 48 bits, ample for a float result; FP64 throughput per SM is
+// too low to be worth it here).  Partials are stored as (hi, lo) floats.
+__global__ void marg_moments2_ff(MargVec X, MargVec Y, int nbx, int P, float* __restrict__ part) {
+  __shared__ ff sm[kMargBlock / 32][16];
+  const bool isx = (int)blockIdx.x < nbx;
+  const MargVec V = isx ? X : Y;
+  const int blk = isx ? blockIdx.x : blockIdx.x - nbx;
+  const int j = blk * kMargBlock + threadIdx.x;
+  const float d = (float)(j - V.len / 2);
+  ff pw = (j < V.len) ? ff_from_double(V.w[j]) : ff{0.f, 0.f};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = 0; t <= P; ++t) {
+    const ff s = warp_sum_ff(pw);
+    if (lane == 0) sm[warp][t] = s;
+    pw = ff_mul(pw, d);
+  }
+  __syncthreads();
+  if (threadIdx.x <= P) {
+    ff acc{0.f, 0.f};
+    for (int w = 0; w < kMargBlock / 32; ++w) acc = ff_add(acc, sm[w][threadIdx.x]);
+    part[((size_t)blockIdx.x * (P + 1) + threadIdx.x) * 2 + 0] = acc.hi;
+    part[((size_t)blockIdx.x * (P + 1) + threadIdx.x) * 2 + 1] = acc.lo;
+  }
+}
+
+__global__ void marg_eval2_ff(MargVec X, MargVec Y, int nbx, int nby, int P, const float* __restrict__ part,
+                              float fxh, float fxl, float fyh, float fyl) {
+  __shared__ ff M[16];
+  const bool isx = (int)blockIdx.x < nbx;
+  const MargVec V = isx ? X : Y;
+  const int blk = isx ? blockIdx.x : blockIdx.x - nbx;
+  const int p0 = isx ? 0 : nbx, np = isx ? nbx : nby;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = warp; t <= P; t += kMargBlock / 32) {
+    ff acc{0.f, 0.f};
+    for (int b = lane; b < np; b += 32) {
+      const size_t o = ((size_t)(p0 + b) * (P + 1) + t) * 2;
+      acc = ff_add(acc, ff{part[o], part[o + 1]});
+    }
+    acc = warp_sum_ff(acc);
+    if (lane == 0) M[t] = acc;
+  }
+  __syncthreads();
+  const int i = blk * kMargBlock + threadIdx.x;
+  if (i >= V.len) return;
+  const float x = (float)(i - V.len / 2);
+  // sum_t C(P,t) x^{P-t} (-1)^t M_t, Horner in x.
+  ff acc{0.f, 0.f};
+  for (int t = 0; t <= P; ++t) {
+    ff c = ff_mul(M[t], (float)binom(P, t));
+    if (t & 1) c = ff_neg(c);
+    acc = ff_add(ff_mul(acc, x), c);
+  }
+  const ff val = ff_mul(acc, ff{isx ? fxh : fyh, isx ? fxl : fyl});
+  float* out = (float*)V.out;
+  out[i] = val.hi;
+  out[V.len + i] = val.lo;
+}
+
 __global__ void marg_moments2(MargVec X, MargVec Y, int nbx, int P, double* __restrict__ part) {
   __shared__ double sm[kMargBlock / 32][16];
   const bool isx = (int)blockIdx.x < nbx;
@@ -83,9 +152,7 @@ __global__ void marg_moments2(MargVec X, MargVec Y, int nbx, int P, double* __re
 }
 
 // Writes out[0..len) = hi part and out[len..2 len) = lo part of each value
-// (lo = 0 for double output), so that float consumers keep the constant term
-// to float-float accuracy.
-template <typename Real>
+// (lo = 0 for double output).
 __global__ void marg_eval2(MargVec X, MargVec Y, int nbx, int nby, int nex, int P, const double* __restrict__ part) {
   __shared__ double M[16];
   const bool isx = (int)blockIdx.x < nex;
@@ -103,17 +170,14 @@ __global__ void marg_eval2(MargVec X, MargVec Y, int nbx, int nby, int nex, int 
   const int i = blk * kMargBlock + threadIdx.x;
   if (i >= V.len) return;
   const double x = (double)i - (double)(V.len / 2);
-  // sum_t C(P,t) x^{P-t} (-1)^t M_t, Horner in x.
   double acc = 0.0;
   for (int t = 0; t <= P; ++t) {
     const double c = (double)binom(P, t) * ((t & 1) ? -M[t] : M[t]);
     acc = acc * x + c;
   }
-  const double val = V.factor * acc;
-  const Real hi = (Real)val;
-  Real* out = (Real*)V.out;
-  out[i] = hi;
-  out[V.len + i] = (Real)(val - (double)hi);
+  double* out = (double*)V.out;
+  out[i] = V.factor * acc;
+  out[V.len + i] = 0.0;
 }
 
 size_t marg_part_doubles(int len, int k) {
@@ -127,11 +191,15 @@ int marg_const2_launch(const double* wx, int n, double fx, void* outx, const dou
   const int P = 2 * k;
   const int nbx = (n + kMargBlock - 1) / kMargBlock, nby = (m + kMargBlock - 1) / kMargBlock;
   MargVec X{wx, n, fx, outx}, Y{wy, m, fy, outy};
-  marg_moments2<<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, P, part);
-  if (dtype == GW_F32)
-    marg_eval2<float><<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, nby, nbx, P, part);
-  else
-    marg_eval2<double><<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, nby, nbx, P, part);
+  if (dtype == GW_F32) {
+    const float fxh = (float)fx, fyh = (float)fy;
+    const float fxl = (float)(fx - (double)fxh), fyl = (float)(fy - (double)fyh);
+    marg_moments2_ff<<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, P, (float*)part);
+    marg_eval2_ff<<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, nby, P, (const float*)part, fxh, fxl, fyh, fyl);
+  } else {
+    marg_moments2<<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, P, part);
+    marg_eval2<<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, nby, nbx, P, part);
+  }
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }
 

@@ -100,8 +100,10 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
   constexpr Real CK = (K & 1) ? (Real)2 : (Real)0;
   static_assert(K == 1 || K == 2, "fast row kernel handles k = 1, 2");
 
-  extern __shared__ unsigned char smem_dyn[];
-  unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_dyn) + 1023) & ~(uintptr_t)1023);
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  // 1024-byte aligned start (the 128-byte swizzle repeats every 1 KB); the
+  // pointer stays derived from the shared array so accesses stay shared.
+  unsigned char* sm = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
   unsigned char* ring = sm;
   unsigned char* cyH = ring + (size_t)stages * slot_bytes;
   unsigned char* cyL = cyH + vec_bytes;
@@ -109,7 +111,8 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
   Real* wtot = reinterpret_cast<Real*>(bars + stages);             // [2][NW][2][K+1]
   Real* zw = wtot + 2 * NW * 2 * (K + 1);                          // [2][NW][K+2]
   // In-chunk forward states of the pending row, [VPT/PER][NT] 16-byte chunks.
-  float4* flbuf = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(zw + 2 * NW * (K + 2)) + 15) & ~(uintptr_t)15);
+  unsigned char* flraw = reinterpret_cast<unsigned char*>(zw + 2 * NW * (K + 2));
+  float4* flbuf = reinterpret_cast<float4*>(flraw + ((16u - (smem_u32(flraw) & 15u)) & 15u));
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -242,7 +245,8 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
       cxh_new = cxh[i];
       cxl_new = cxl[i];
       // Column recursion and in-chunk forward walk, 16 bytes of the row at a
-      // time; also the chunk's moments about its end (agg) and start (bag).
+      // time; also the chunk's moments about its end (agg) and about its
+      // start (bag, orders >= 1; order 0 is agg[0]).
       Real agg[K + 1], bag[K + 1];
 #pragma unroll
       for (int r = 0; r <= K; ++r) {
@@ -250,10 +254,13 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
         bag[r] = 0;
       }
       const Real tr = (Real)t;
+      float4 xv[VPT / PER];
+#pragma unroll
+      for (int j = 0; j < VPT / PER; ++j)
+        xv[j] = *reinterpret_cast<const float4*>(xr + swz128((uint32_t)((c0 + j * PER) * sizeof(Real))));
 #pragma unroll
       for (int j = 0; j < VPT / PER; ++j) {
-        const float4 xv = *reinterpret_cast<const float4*>(xr + swz128((uint32_t)((c0 + j * PER) * sizeof(Real))));
-        const Real* x = reinterpret_cast<const Real*>(&xv);
+        const Real* x = reinterpret_cast<const Real*>(&xv[j]);
 #pragma unroll
         for (int w = 0; w < PER; ++w) {
           const int v = j * PER + w;
@@ -275,41 +282,37 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
             agg[2] = fma(wv * wv, y, agg[2]);
           }
           const Real vv = (Real)v;
-          bag[0] += y;
           bag[1] = fma(vv, y, bag[1]);
           if constexpr (K >= 2) bag[2] = fma(vv * vv, y, bag[2]);
         }
       }
-      // Butterfly over the lanes: the warp's moments about its start.
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        Real o[K + 1];
-#pragma unroll
-        for (int r = 0; r <= K; ++r) o[r] = __shfl_xor_sync(0xffffffffu, bag[r], d);
-        // The right block's moments move to the left block's start.
-        if (lane & d) {
-#pragma unroll
-          for (int r = 0; r <= K; ++r) {
-            const Real tmp = o[r];
-            o[r] = bag[r];
-            bag[r] = tmp;
-          }
-        }
-        shift_real<K>(o, (Real)(d * VPT));
-#pragma unroll
-        for (int r = 0; r <= K; ++r) bag[r] += o[r];
+      bag[0] = agg[0];
+      // The chunk's moments about the warp start: sum_u C(r,u) o0^{r-u} bag_u
+      // (non-negative terms).  Summed over the lanes below (plain butterfly).
+      Real csum[K + 1];
+      {
+        const Real of = (Real)o0;
+        csum[0] = bag[0];
+        csum[1] = fma(of, bag[0], bag[1]);
+        if constexpr (K >= 2) csum[2] = fma(of, fma(of, bag[0], (Real)2 * bag[1]), bag[2]);
       }
-      // Lane scan (float), inclusive, about my chunk end.
+      // Lane scan of agg (float, inclusive, about my chunk end) interleaved
+      // with the butterfly sum of csum.
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
-        Real o[K + 1];
+        Real o[K + 1], oc[K + 1];
 #pragma unroll
-        for (int r = 0; r <= K; ++r) o[r] = __shfl_up_sync(0xffffffffu, agg[r], d);
+        for (int r = 0; r <= K; ++r) {
+          o[r] = __shfl_up_sync(0xffffffffu, agg[r], d);
+          oc[r] = __shfl_xor_sync(0xffffffffu, csum[r], d);
+        }
         shift_real<K>(o, (Real)(d * VPT));
         if (lane >= d) {
 #pragma unroll
           for (int r = 0; r <= K; ++r) agg[r] += o[r];
         }
+#pragma unroll
+        for (int r = 0; r <= K; ++r) csum[r] += oc[r];
       }
 #pragma unroll
       for (int r = 0; r <= K; ++r) {
@@ -324,7 +327,7 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
       if (lane == 0) {
         Real* wt = wtot + ((t & 1) * NW + warp) * 2 * (K + 1) + (K + 1);
 #pragma unroll
-        for (int r = 0; r <= K; ++r) wt[r] = bag[r];
+        for (int r = 0; r <= K; ++r) wt[r] = csum[r];
       }
       named_arrive(1 + (t & 1), ALL);
     }
@@ -365,6 +368,12 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
         if constexpr (K & 1) small0 = fma(CK, ex_prev[K], small0);
       }
       const Real big0 = fma(-scale, ZW[0], cxh_prev);
+      // lo(v) = cx.lo - s (small0 + sum_e ZT_e v^e + c_K F_local(v)), folded.
+      Real LC[K + 1];
+      LC[0] = fma(-scale, small0, cxl_prev);
+#pragma unroll
+      for (int e = 1; e <= K; ++e) LC[e] = -scale * ZT[e];
+      const Real cks = -scale * CK;
       Real* grow = G + (size_t)i * m + c0;
       const bool vec_store = (c0 + VPT <= m) && ((((uintptr_t)grow) & 15) == 0);
       // Four (float) or two (double) columns at a time: their constant term
@@ -384,12 +393,11 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
         for (int w = 0; w < PER; ++w) {
           const int v = j * PER + w;
           const Real vv = (Real)v;
-          Real sm2 = ZT[K];
+          Real lo = LC[K];
 #pragma unroll
-          for (int e = K - 1; e >= 1; --e) sm2 = fma(sm2, vv, ZT[e]);
-          sm2 = fma(sm2, vv, small0);
-          if constexpr (K & 1) sm2 = fma(CK, flp[w], sm2);
-          out[w] = (big0 + ch[w]) + fma(-scale, sm2, cxl_prev + cl[w]);
+          for (int e = K - 1; e >= 0; --e) lo = fma(lo, vv, LC[e]);
+          if constexpr (K & 1) lo = fma(cks, flp[w], lo);
+          out[w] = (big0 + ch[w]) + (lo + cl[w]);
         }
         if (vec_store) {
           if constexpr (sizeof(Real) == 4)

@@ -50,20 +50,6 @@ __device__ __forceinline__ void kahan_add(double& s, double& c, double x) {
   s = t;
 }
 
-// ff from a non-negative integer below 2^48 (exact).
-__device__ __forceinline__ ff ff_from_u64(unsigned long long v) {
-  float hi = __ull2float_rn(v);
-  long long d = (long long)v - (long long)__float2ull_rn(hi);
-  return {hi, __ll2float_rn(d)};
-}
-
-// S * c for an integer c >= 0, with c exact in the accumulator type.
-__device__ __forceinline__ ff acc_mul_int(ff S, unsigned long long c) {
-  if (c < (1ull << 24)) return ff_mul(S, (float)c);
-  return ff_mul(S, ff_from_u64(c));
-}
-__device__ __forceinline__ double acc_mul_int(double S, unsigned long long c) { return S * (double)c; }
-
 // a * c for a float c that is exact (an integer below 2^24).
 __device__ __forceinline__ ff acc_mulf(ff a, float c) { return ff_mul(a, c); }
 __device__ __forceinline__ double acc_mulf(double a, double c) { return a * c; }
@@ -76,7 +62,7 @@ template <> struct AccReal<double> { using type = double; };
 //   S_r <- sum_{u<=r} C(r,u) d^{r-u} S_u,
 // evaluated by Horner in d (d < 2^24, so every multiplier is exact).
 template <int K, typename A>
-__device__ __forceinline__ void shift_acc(A (&S)[K + 1], long long d) {
+__device__ __forceinline__ void shift_acc(A (&S)[K + 1], int d) {
   using F = typename AccReal<A>::type;
   const F df = (F)d;
 #pragma unroll
@@ -177,6 +163,9 @@ __global__ void __launch_bounds__(1024) k1a_band_moments(const Real* __restrict_
   const int NT = blockDim.x;
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
+  // blockIdx.y splits the row into column slices of NT*VEC*CPT columns.
+  const int col0 = blockIdx.y * NT * VEC * CPT;
+  const int wbase = blockIdx.y * (NT >> 5) * CPT;
   Real m0[CPT][VEC], c0[CPT][VEC], mr[CPT][K][VEC];
 #pragma unroll
   for (int g = 0; g < CPT; ++g)
@@ -193,7 +182,7 @@ __global__ void __launch_bounds__(1024) k1a_band_moments(const Real* __restrict_
     Real x[CPT][VEC];
 #pragma unroll
     for (int g = 0; g < CPT; ++g) {
-      const int p0 = (g * NT + (int)threadIdx.x) * VEC;
+      const int p0 = col0 + (g * NT + (int)threadIdx.x) * VEC;
       if (VEC > 1 && p0 + VEC <= m) {
         if constexpr (VEC == 4 && sizeof(Real) == 4) {
           float4 f = __ldg(reinterpret_cast<const float4*>(row + p0));
@@ -226,7 +215,7 @@ __global__ void __launch_bounds__(1024) k1a_band_moments(const Real* __restrict_
     if (exact) {
 #pragma unroll
       for (int g = 0; g < CPT; ++g) {
-        const int wchunk = g * (NT >> 5) + warp;
+        const int wchunk = wbase + g * (NT >> 5) + warp;
         if (wchunk * 32 * VEC >= m) continue;  // warp-uniform
         Real loc = 0;
 #pragma unroll
@@ -261,7 +250,7 @@ __global__ void __launch_bounds__(1024) k1a_band_moments(const Real* __restrict_
   for (int g = 0; g < CPT; ++g)
 #pragma unroll
     for (int v = 0; v < VEC; ++v) {
-      const int p = (g * NT + (int)threadIdx.x) * VEC + v;
+      const int p = col0 + (g * NT + (int)threadIdx.x) * VEC + v;
       if (p < m) {
         Real* base = mu + (size_t)a * (K + 2) * m + p;
         base[0] = m0[g][v];
@@ -299,7 +288,7 @@ struct K1bOps {
   }
   // End-relative band moments nu_r = sum_t (R_a - t)^r x = sum_u C(r,u) R^{r-u} (-1)^u mu_u,
   // by Horner in R.
-  static __device__ __forceinline__ void nu_of(const A (&M)[K + 1], long long Ra, A (&N)[K + 1]) {
+  static __device__ __forceinline__ void nu_of(const A (&M)[K + 1], int Ra, A (&N)[K + 1]) {
     using F = typename AccReal<A>::type;
     const F rf = (F)Ra;
     N[0] = M[0];
@@ -331,7 +320,7 @@ __global__ void __launch_bounds__(256) k1b_agg(const Real* __restrict__ mu, int 
 #pragma unroll
   for (int r = 0; r <= K; ++r) FA[r] = acc_zero((A*)nullptr);
   for (int a = a0; a < a1; ++a) {
-    const long long Ra = min(R, n - a * R);
+    const int Ra = min(R, n - a * R);
     O::load_mu(mu, m, a, p, M);
     O::nu_of(M, Ra, N);
     shift_acc<K>(FA, Ra);
@@ -361,7 +350,7 @@ __global__ void __launch_bounds__(256) k1b_scan(int n, int m, int R, int B, int 
       aS[((size_t)S * (K + 1) + r) * m + p] = C[r];
       G[r] = agg[((size_t)S * (K + 1) + r) * m + p];
     }
-    const long long L = (long long)min(n, (S + 1) * kSuper * R) - (long long)S * kSuper * R;
+    const int L = min(n, (S + 1) * kSuper * R) - S * kSuper * R;
     shift_acc<K>(C, L);
 #pragma unroll
     for (int r = 0; r <= K; ++r) C[r] = acc_add(C[r], G[r]);
@@ -392,7 +381,7 @@ __global__ void __launch_bounds__(256) k1b_walk(const Real* __restrict__ mu, int
     Nt[r] = ntot[(size_t)r * m + p];
   }
   for (int a = a0; a < a1; ++a) {
-    const long long sa = (long long)a * R;
+    const int sa = a * R;
     using F = typename AccReal<A>::type;
     const F dn = (F)(n - sa);
     // Moments about s_a of the whole column (Horner in n - s_a, alternating
@@ -418,7 +407,7 @@ __global__ void __launch_bounds__(256) k1b_walk(const Real* __restrict__ mu, int
       if (cb != 1) t = acc_mulf(t, (typename AccReal<A>::type)cb);
       q[((size_t)a * (K + 1) + e) * m + p] = (Real)acc_round(t);
     }
-    const long long Ra = min(R, n - a * R);
+    const int Ra = min(R, n - a * R);
     O::load_mu(mu, m, a, p, M);
     O::nu_of(M, Ra, N);
     shift_acc<K>(Af, Ra);
@@ -472,7 +461,8 @@ __global__ void __launch_bounds__(NT, 1)
   const size_t ring_bytes = ((size_t)stages * m_pad * sizeof(Real) + 15) & ~(size_t)15;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + ring_bytes);
   Real* wtot = reinterpret_cast<Real*>(smem_raw + ring_bytes + 8 * (size_t)stages);  // [2][NW][K+1]
-  A* wpre = reinterpret_cast<A*>((reinterpret_cast<uintptr_t>(wtot + 2 * NW * (K + 1)) + 15) & ~(uintptr_t)15);
+  unsigned char* wpraw = reinterpret_cast<unsigned char*>(wtot + 2 * NW * (K + 1));
+  A* wpre = reinterpret_cast<A*>(wpraw + ((16u - (smem_u32(wpraw) & 15u)) & 15u));
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
@@ -664,8 +654,8 @@ __global__ void __launch_bounds__(NT, 1)
       Al[r] = wpre[warp * (K + 1) + r];
       Bc[r] = wpre[(NW + warp) * (K + 1) + r];
     }
-    shift_acc<K>(Al, (long long)(lane * VPT));
-    shift_acc<K>(Bc, (long long)((32 - lane) * VPT));
+    shift_acc<K>(Al, lane * VPT);
+    shift_acc<K>(Bc, (32 - lane) * VPT);
 #pragma unroll
     for (int r = 0; r <= K; ++r) {
       Al[r] = acc_add(Al[r], acc_of(ex[r]));
@@ -825,7 +815,8 @@ template <int K, typename Real, int VEC, int CPT>
 void launch_k1a(const Grad1DArgs& g, int B, int R, Real* mu, Real* rowpart, cudaStream_t st) {
   int nt = (g.m + VEC * CPT - 1) / (VEC * CPT);
   nt = std::min(1024, (nt + 31) / 32 * 32);
-  k1a_band_moments<K, Real, VEC, CPT><<<B, nt, 0, st>>>((const Real*)g.T, g.n, g.m, R, mu, rowpart, g.exact);
+  dim3 grid(B, 1);
+  k1a_band_moments<K, Real, VEC, CPT><<<grid, nt, 0, st>>>((const Real*)g.T, g.n, g.m, R, mu, rowpart, g.exact);
 }
 
 template <int K, typename Real>
@@ -882,7 +873,7 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
     A* ntot = (A*)(ws + L.ntot_off);
     dim3 grid2((m + 255) / 256, L.NS);
     k1b_agg<K, Real><<<grid2, 256, 0, st>>>(mu, n, m, R, B, agg);
-    k1b_scan<K, Real><<<(m + 255) / 256, 256, 0, st>>>(n, m, R, B, L.NS, agg, aS, ntot, g.exact ? c : nullptr);
+    k1b_scan<K, Real><<<(m + 63) / 64, 64, 0, st>>>(n, m, R, B, L.NS, agg, aS, ntot, g.exact ? c : nullptr);
     k1b_walk<K, Real><<<grid2, 256, 0, st>>>(mu, n, m, R, B, aS, ntot, (Real*)(ws + L.q_off));
   }
   if (cudaPeekAtLastError() != cudaSuccess) return GW_ERR_CUDA;
