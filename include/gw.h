@@ -133,6 +133,39 @@ gw_status gw_ctx_profile_report(gw_ctx* ctx, char* buf, size_t len, int reset);
 gw_status gw_grad(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const double* d_v,
                   const void* d_T, void* d_G, int marginals, void* stream);
 
+/*
+ * gw_solve - entropic (fused) Gromov-Wasserstein by mirror descent with
+ * tau = eps (Sec. 2.1, eq. "GW sinkhorn" and the Remark on tau = eps; fused
+ * GW by the Remark "FGW").
+ *
+ * Starting from T^0 = u v^T, each of prob->n_outer steps forms the cost
+ *     Pi = 2 theta G(T) + (1 - theta) C o C,   G = L(C_X, C_Y) (x) T with the
+ *     target marginals (gw_grad), C o C_ip = ||phi_i - psi_p||^2,
+ * and runs prob->n_inner log-domain Sinkhorn iterations from f = g = 0
+ * (f then g each iteration), then sets T_ip = exp((f_i + g_p - Pi_ip) / eps).
+ *
+ *   prob         dim 1; nx, ny, hx, hy, k as for gw_grad; eps > 0;
+ *                n_outer >= 0; n_inner >= 1; theta in [0, 1]; feat_dim in
+ *                [1, 64] when theta < 1; dtype GW_F32 or GW_F64 (the
+ *                arithmetic precision of the whole solve).
+ *   d_u, d_v     target marginals (double, lengths n and m, positive).
+ *   d_phi,d_psi  fused-GW features, double, row-major n x feat_dim and
+ *                m x feat_dim; read only when theta < 1 (else may be NULL).
+ *   d_T          output plan, n x m row-major, prob->dtype.
+ *   d_f, d_g     output potentials (double, lengths n and m) or NULL.
+ *   d_stats      NULL or 8 doubles on the device: [0] objective
+ *                (1 - theta) <C o C, T> + theta E(T), [1] E(T) (the GW
+ *                energy, Sec. 2), [2] <C o C, T>, [3] eps H(T),
+ *                [4] sum_i |(T 1)_i - u_i|, [5] sum_p |(T^T 1)_p - v_p|,
+ *                [6] outer iterations run, [7] 0.
+ *
+ * The call enqueues the whole solve on `stream` and returns.  The context
+ * workspace holds Pi (n*m reals) plus O(n + m) state.
+ */
+gw_status gw_solve(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const double* d_v,
+                   const double* d_phi, const double* d_psi, void* d_T, double* d_f, double* d_g,
+                   double* d_stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -85,6 +85,7 @@ def load() -> ctypes.CDLL:
         "gw_ctx_profile": (S, [P, I]),
         "gw_ctx_profile_report": (S, [P, ctypes.c_char_p, ctypes.c_size_t, I]),
         "gw_grad": (S, [P, prob, P, P, P, P, I, P]),
+        "gw_solve": (S, [P, prob, P, P, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -170,3 +171,9 @@ class Context:
         st = self.lib.gw_grad(self.h, ctypes.byref(prob), _ptr(u), _ptr(v), _ptr(T), _ptr(G), marginals,
                               _stream(stream))
         return self._check(st, "gw_grad")
+
+    def gw_solve(self, prob: gw_problem, u, v, T, f=None, g=None, stats=None, phi=None, psi=None,
+                 stream=None) -> int:
+        st = self.lib.gw_solve(self.h, ctypes.byref(prob), _ptr(u), _ptr(v), _ptr(phi), _ptr(psi), _ptr(T),
+                               _ptr(f), _ptr(g), _ptr(stats), _stream(stream))
+        return self._check(st, "gw_solve")

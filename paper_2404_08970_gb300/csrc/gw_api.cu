@@ -275,4 +275,57 @@ gw_status gw_grad(gw_ctx* c, const gw_problem* p, const double* d_u, const doubl
   return GW_OK;
 }
 
+gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const double* d_v, const double* d_phi,
+                   const double* d_psi, void* d_T, double* d_f, double* d_g, double* d_stats, void* stream) {
+  if (!c) return GW_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  gw_status s = check_grid(c, p);
+  if (s != GW_OK) return s;
+  if (p->dim != 1) return fail(c, GW_ERR_INVALID, "gw_solve: 2D grids are not available in this call");
+  if (p->k > 3) return fail(c, GW_ERR_INVALID, "gw_solve: k must be <= 3 (got %d)", p->k);
+  if (p->ny > 16384) return fail(c, GW_ERR_INVALID, "gw_solve: ny must be <= 16384 (got %d)", p->ny);
+  if (!finite_pos(p->eps)) return fail(c, GW_ERR_INVALID, "gw_solve: eps must be finite and > 0");
+  if (p->n_outer < 0 || p->n_inner < 1)
+    return fail(c, GW_ERR_INVALID, "gw_solve: need n_outer >= 0 and n_inner >= 1");
+  if (!(p->theta >= 0.0 && p->theta <= 1.0)) return fail(c, GW_ERR_INVALID, "gw_solve: theta must be in [0, 1]");
+  if (p->theta != 1.0 && (p->feat_dim < 1 || p->feat_dim > 64 || !d_phi || !d_psi))
+    return fail(c, GW_ERR_INVALID, "gw_solve: fused GW (theta < 1) needs 1 <= feat_dim <= 64 and both feature arrays");
+  if (!d_u || !d_v || !d_T) return fail(c, GW_ERR_INVALID, "gw_solve: d_u, d_v and d_T must not be NULL");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
+  gw::Solve1DArgs a{};
+  a.n = p->nx;
+  a.m = p->ny;
+  a.k = p->k;
+  a.dtype = p->dtype;
+  a.hx = p->hx;
+  a.hy = p->hy;
+  a.eps = p->eps;
+  a.theta = p->theta;
+  a.n_outer = p->n_outer;
+  a.n_inner = p->n_inner;
+  a.feat_dim = p->theta != 1.0 ? p->feat_dim : 0;
+  a.u = d_u;
+  a.v = d_v;
+  a.phi = d_phi;
+  a.psi = d_psi;
+  a.T = d_T;
+  a.f = d_f;
+  a.g = d_g;
+  a.stats = d_stats;
+  a.stream = (cudaStream_t)stream;
+  a.status = c->status;
+  a.num_sms = c->num_sms;
+  a.tracer = c->tr();
+  a.force_generic = c->force_generic;
+  s = ensure_ws(c, gw::solve1d_workspace_bytes(a.n, a.m, a.k, a.dtype, a.num_sms));
+  if (s != GW_OK) return s;
+  int rc = gw::solve1d_launch(a, c->ws, c->ws_bytes);
+  if (rc != GW_OK) {
+    cudaError_t e = cudaGetLastError();
+    return fail(c, (gw_status)rc, "gw_solve launch failed: %s", cudaGetErrorString(e));
+  }
+  c->err.clear();
+  return GW_OK;
+}
+
 }  // extern "C"

@@ -101,4 +101,22 @@ int marg_const_launch(const double* w, int len, int k, double h, void* out, int 
 int marg_const2_launch(const double* wx, int n, double fx, void* outx, const double* wy, int m, double fy,
                        void* outy, int k, int dtype, double* part, cudaStream_t stream, Tracer* tracer);
 
+// Entropic (fused) GW by mirror descent on 1D grids (sinkhorn.cu).
+struct Solve1DArgs {
+  int n, m, k, dtype;
+  double hx, hy, eps, theta;
+  int n_outer, n_inner, feat_dim;
+  const double *u, *v, *phi, *psi;
+  void* T;
+  double *f, *g, *stats;
+  cudaStream_t stream;
+  unsigned* status;
+  int num_sms;
+  Tracer* tracer;
+  int force_generic;
+};
+
+size_t solve1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms);
+int solve1d_launch(const Solve1DArgs& a, void* ws, size_t ws_bytes);
+
 }  // namespace gw

@@ -1,0 +1,637 @@
+// Entropic mirror descent for 1D grids: log-domain Sinkhorn on a stored cost
+// Pi, the plan, and the solve statistics.
+//
+// Mirror descent with tau = eps (Sec. 2.1, eq. "GW sinkhorn" and the Remark
+// on tau = eps) solves, at every outer step, the entropic OT problem whose
+// cost is Pi = 2 theta G(T) + (1 - theta) C o C (Remark "FGW"), then replaces
+// T by that problem's plan T_ip = exp((f_i + g_p - Pi_ip) / eps).  The inner
+// Sinkhorn iterations update f then g (log-sum-exp along rows, then columns)
+// from f = g = 0, for a fixed count.
+//
+// Arithmetic is in base 2: F = f log2(e) / eps, G = g log2(e) / eps and
+// c = log2(e) / eps, so a plan entry is 2^(F_i + G_p - c Pi_ip) and every
+// exponential is one exp2.  One pass over Pi per iteration:
+//   sk_pass  one CTA per band of rows streams the band's rows of Pi (TMA
+//            ring).  Per row: S_i = sum_p 2^(F_i + G_p - c Pi_ip) (previous
+//            F as reference; after a column update every term is <= v_p), the
+//            new F_i = F_i + log2 u_i - log2 S_i; then, per column, the band's
+//            partial sum of 2^(F_i + G_p - c Pi_ip) with the new F (every term
+//            <= u_i).  A column whose band sum underflows is recomputed for
+//            that band with a max shift.
+//   sk_cols  per column: combines the band partials (FP64) into the new G_p.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "gw_common.cuh"
+#include "gw_internal.h"
+#include "gw_tma.cuh"
+
+namespace gw {
+
+__device__ __forceinline__ float ex2(float x) { return exp2f(x); }
+__device__ __forceinline__ double ex2(double x) { return exp2(x); }
+__device__ __forceinline__ float lg2(float x) { return log2f(x); }
+__device__ __forceinline__ double lg2(double x) { return log2(x); }
+
+template <typename Real>
+__device__ __forceinline__ Real warp_sum(Real x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+template <typename Real>
+__device__ __forceinline__ Real warp_max(Real x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+// Below this a band's column sum is treated as underflowed and recomputed
+// with a max shift.
+constexpr float kTiny = 1e-30f;
+
+// A band's column partial (M, S): the band's sum is S * 2^M relative to the
+// column's current potential.
+template <typename Real> struct PartT;
+template <> struct PartT<float> { using type = float2; };
+template <> struct PartT<double> { using type = double2; };
+
+// ---------------------------------------------------------------------------
+// Shared-memory layout of the row-streaming kernels (1024-aligned base):
+//   ring [stages][slot_bytes] | G (swizzled, vec_bytes) | red [2][NW] Real |
+//   Fband [Rmax] Real | bars [stages]
+// ---------------------------------------------------------------------------
+struct RowGeom {
+  int slot_bytes, vec_bytes, stages, use_tma, box_cols;
+};
+
+template <int NW, typename Real>
+size_t rows_smem_bytes(const RowGeom& g, int Rmax) {
+  return 1024 + (size_t)g.stages * g.slot_bytes + g.vec_bytes + sizeof(Real) * (2 * NW + Rmax) + 16 +
+         8 * (size_t)g.stages + 64;
+}
+
+template <typename Real>
+struct RowRing {
+  unsigned char* ring;
+  uint64_t* bars;
+  int stages, slot_bytes, use_tma, box_cols;
+  const CUtensorMap* tm;
+  const Real* src;
+  int m, s, Ra;
+
+  __device__ void issue(int tl) {  // row s + tl into slot tl % stages
+    const int slot = tl % stages;
+    mbar_arrive_expect_tx(&bars[slot], (unsigned)(m * sizeof(Real)));
+    tma_load_3d(ring + (size_t)slot * slot_bytes, tm, 0, 0, s + tl, &bars[slot]);
+  }
+  // Returns the slot holding row tl; all NT threads call it.
+  __device__ const unsigned char* get(int tl, int NT, unsigned* status) {
+    if (use_tma) {
+      const int slot = tl % stages;
+      mbar_wait_bounded(&bars[slot], (unsigned)((tl / stages) & 1), status);
+      return ring + (size_t)slot * slot_bytes;
+    }
+    unsigned char* dst = ring + (size_t)(tl & 1) * slot_bytes;
+    const Real* row = src + (size_t)(s + tl) * m;
+    for (int p = threadIdx.x; p < m; p += NT) sts_swz<Real>(dst, p, row[p]);
+    __syncthreads();
+    return dst;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// sk_pass
+// ---------------------------------------------------------------------------
+template <int NW, int VPT, typename Real>
+__global__ void __launch_bounds__(32 * NW, 1)
+    sk_pass(const __grid_constant__ CUtensorMap tmP, const Real* __restrict__ Pi, int n, int m, int R, Real c,
+            const Real* __restrict__ lu, Real* __restrict__ F, const Real* __restrict__ Gp,
+            typename PartT<Real>::type* __restrict__ part, RowGeom geo, unsigned* status) {
+  constexpr int NT = 32 * NW;
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  unsigned char* sm = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+  unsigned char* ring = sm;
+  unsigned char* Gs = ring + (size_t)geo.stages * geo.slot_bytes;
+  Real* red = reinterpret_cast<Real*>(Gs + geo.vec_bytes);  // [2][NW]
+  Real* Fband = red + 2 * NW;
+  unsigned char* braw = reinterpret_cast<unsigned char*>(Fband + R);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(braw + ((8u - (smem_u32(braw) & 7u)) & 7u));
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int a = blockIdx.x, s = a * R, Ra = min(R, n - s);
+  const int c0 = tid * VPT;
+  const int m_pad = geo.vec_bytes / (int)sizeof(Real);
+
+  RowRing<Real> rr{ring, bars, geo.stages, geo.slot_bytes, geo.use_tma, geo.box_cols, &tmP, Pi, m, s, Ra};
+  if (geo.use_tma && tid == 0) {
+    for (int st = 0; st < geo.stages; ++st) mbar_init(&bars[st], 1);
+    fence_mbar_init();
+  }
+  for (int p = tid; p < m_pad; p += NT) sts_swz<Real>(Gs, p, p < m ? Gp[p] : (Real)0);
+  for (int st = 0; st < geo.stages; ++st)
+    for (int p = m + tid; p < m_pad; p += NT) sts_swz<Real>(ring + (size_t)st * geo.slot_bytes, p, (Real)0);
+  __syncthreads();
+  if (geo.use_tma && tid == 0)
+    for (int tl = 0; tl < geo.stages - 1 && tl < Ra; ++tl) rr.issue(tl);
+
+  Real Gv[VPT];
+  lds_swz<Real, VPT>(Gs, c0, Gv);
+  Real acc[VPT], mx[VPT];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    acc[v] = 0;
+    mx[v] = -INFINITY;
+  }
+
+  for (int t = 0; t < Ra; ++t) {
+    const int i = s + t;
+    const unsigned char* xr = rr.get(t, NT, status);
+    Real x[VPT];
+    lds_swz<Real, VPT>(xr, c0, x);
+    const Real Fo = F[i];
+    // Row sum with the previous F as reference.
+    Real e[VPT];
+    Real sum = 0;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      e[v] = (c0 + v < m) ? fma(-c, x[v], Gv[v] + Fo) : (Real)-INFINITY;
+      sum += ex2(e[v]);
+    }
+    sum = warp_sum(sum);
+    Real* rb = red + (t & 1) * NW;
+    if (lane == 0) rb[warp] = sum;
+    __syncthreads();
+    // The slot of row t-1 is free: refill it with row t + stages - 1.
+    if (geo.use_tma && tid == 0 && t + geo.stages - 1 < Ra) {
+      fence_proxy_async_smem();
+      rr.issue(t + geo.stages - 1);
+    }
+    Real S = 0;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) S += rb[w];
+    Real Fn;
+    if (S >= (Real)kTiny && S <= (Real)1e30) {
+      Fn = Fo + lu[i] - lg2(S);
+    } else {
+      // Underflow or overflow of the row sum: redo it with a max shift.
+      Real lm = -INFINITY;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) lm = fmax(lm, e[v]);
+      lm = warp_max(lm);
+      __syncthreads();
+      if (lane == 0) rb[warp] = lm;
+      __syncthreads();
+      Real M = -INFINITY;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) M = fmax(M, rb[w]);
+      Real s2 = 0;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) s2 += ex2(e[v] - M);
+      s2 = warp_sum(s2);
+      __syncthreads();
+      if (lane == 0) rb[warp] = s2;
+      __syncthreads();
+      Real S2 = 0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) S2 += rb[w];
+      Fn = Fo + lu[i] - (M + lg2(S2));
+      __syncthreads();
+    }
+    if (tid == 0) {
+      F[i] = Fn;
+      Fband[t] = Fn;
+    }
+    // Column partial sums with the new F (every term <= u_i).
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const Real xp = fma(-c, x[v], Gv[v] + Fn);
+      acc[v] += ex2(xp);
+      mx[v] = fmax(mx[v], xp);
+    }
+  }
+  __syncthreads();
+  // Write the band partials; recompute underflowed columns with a max shift.
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    const int p = c0 + v;
+    if (p >= m) continue;
+    typename PartT<Real>::type out;
+    if (acc[v] >= (Real)kTiny) {
+      out.x = 0;
+      out.y = acc[v];
+    } else {
+      Real s2 = 0;
+      for (int t = 0; t < Ra; ++t) s2 += ex2(fma(-c, Pi[(size_t)(s + t) * m + p], Gv[v] + Fband[t]) - mx[v]);
+      out.x = mx[v];
+      out.y = s2;
+    }
+    part[(size_t)a * m + p] = out;
+  }
+}
+
+// Combines the band partials (M_b, S_b) of each column: sum_b S_b 2^(M_b - M).
+template <typename Real>
+__global__ void sk_cols(const typename PartT<Real>::type* __restrict__ part, int B, int m,
+                        const Real* __restrict__ lv, Real* __restrict__ G) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m) return;
+  Real M = -INFINITY;
+  for (int b = 0; b < B; ++b) M = fmax(M, part[(size_t)b * m + p].x);
+  double S = 0.0;
+  for (int b = 0; b < B; ++b) {
+    const auto q = part[(size_t)b * m + p];
+    S += (double)q.y * (double)ex2(q.x - M);
+  }
+  G[p] = (Real)((double)G[p] + (double)lv[p] - ((double)M + log2(S)));
+}
+
+// ---------------------------------------------------------------------------
+// Plan and statistics: T = 2^(F_i + G_p - c Pi_ip); per CTA the entropy
+// partial sum_ip T (ln T - 1), the row-marginal error sum_i |T_i. - u_i| and
+// the band's column sums.
+// ---------------------------------------------------------------------------
+template <int NW, int VPT, typename Real>
+__global__ void __launch_bounds__(32 * NW, 1)
+    sk_plan(const __grid_constant__ CUtensorMap tmP, const Real* __restrict__ Pi, int n, int m, int R, Real c,
+            const Real* __restrict__ F, const Real* __restrict__ Gp, const double* __restrict__ u,
+            Real* __restrict__ T, double* __restrict__ colpart, double* __restrict__ cta_stats, RowGeom geo,
+            unsigned* status) {
+  constexpr int NT = 32 * NW;
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  unsigned char* sm = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+  unsigned char* ring = sm;
+  unsigned char* Gs = ring + (size_t)geo.stages * geo.slot_bytes;
+  Real* red = reinterpret_cast<Real*>(Gs + geo.vec_bytes);
+  Real* Fband = red + 2 * NW;
+  unsigned char* braw = reinterpret_cast<unsigned char*>(Fband + R);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(braw + ((8u - (smem_u32(braw) & 7u)) & 7u));
+  __shared__ double dred[2][32];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int a = blockIdx.x, s = a * R, Ra = min(R, n - s);
+  const int c0 = tid * VPT;
+  const int m_pad = geo.vec_bytes / (int)sizeof(Real);
+  RowRing<Real> rr{ring, bars, geo.stages, geo.slot_bytes, geo.use_tma, geo.box_cols, &tmP, Pi, m, s, Ra};
+  if (geo.use_tma && tid == 0) {
+    for (int st = 0; st < geo.stages; ++st) mbar_init(&bars[st], 1);
+    fence_mbar_init();
+  }
+  for (int p = tid; p < m_pad; p += NT) sts_swz<Real>(Gs, p, p < m ? Gp[p] : (Real)0);
+  for (int st = 0; st < geo.stages; ++st)
+    for (int p = m + tid; p < m_pad; p += NT) sts_swz<Real>(ring + (size_t)st * geo.slot_bytes, p, (Real)0);
+  __syncthreads();
+  if (geo.use_tma && tid == 0)
+    for (int tl = 0; tl < geo.stages - 1 && tl < Ra; ++tl) rr.issue(tl);
+  Real Gv[VPT];
+  lds_swz<Real, VPT>(Gs, c0, Gv);
+  double csum[VPT];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) csum[v] = 0.0;
+  double ent = 0.0, rowerr = 0.0;
+  const Real ln2 = (Real)0.69314718055994530942;
+  for (int t = 0; t < Ra; ++t) {
+    const int i = s + t;
+    const unsigned char* xr = rr.get(t, NT, status);
+    Real x[VPT];
+    lds_swz<Real, VPT>(xr, c0, x);
+    const Real Fi = F[i];
+    Real rs = 0, en = 0;
+    Real* trow = T + (size_t)i * m;
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int p = c0 + v;
+      if (p < m) {
+        const Real lt = fma(-c, x[v], Gv[v] + Fi);  // log2 T
+        const Real tv = ex2(lt);
+        trow[p] = tv;
+        rs += tv;
+        en += tv * (lt * ln2 - (Real)1);
+        csum[v] += (double)tv;
+      }
+    }
+    double rsd = warp_sum((double)rs);
+    ent += (double)en;
+    if (lane == 0) dred[t & 1][warp] = rsd;
+    __syncthreads();
+    if (geo.use_tma && tid == 0 && t + geo.stages - 1 < Ra) {
+      fence_proxy_async_smem();
+      rr.issue(t + geo.stages - 1);
+    }
+    if (tid == 0) {
+      double r = 0.0;
+      for (int w = 0; w < NW; ++w) r += dred[t & 1][w];
+      rowerr += fabs(r - u[i]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < VPT; ++v)
+    if (c0 + v < m) colpart[(size_t)a * m + c0 + v] = csum[v];
+  ent = warp_sum(ent);
+  __syncthreads();
+  if (lane == 0) dred[0][warp] = ent;
+  __syncthreads();
+  if (tid == 0) {
+    double e = 0.0;
+    for (int w = 0; w < NW; ++w) e += dred[0][w];
+    cta_stats[2 * a + 0] = e;
+    cta_stats[2 * a + 1] = rowerr;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Small kernels
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void fill_product(const double* __restrict__ u, const double* __restrict__ v, int n, int m,
+                             Real* __restrict__ T) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t N = (size_t)n * m;
+  for (size_t k = idx; k < N; k += (size_t)gridDim.x * blockDim.x) T[k] = (Real)(u[k / m] * v[k % m]);
+}
+
+template <typename Real>
+__global__ void log2_scaled(const double* __restrict__ w, int len, Real* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < len) out[i] = (Real)log2(w[i]);
+}
+
+template <typename Real>
+__global__ void fill_val(Real* __restrict__ x, int len, Real val) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < len) x[i] = val;
+}
+
+// Pi += (1 - theta) ||phi_i - psi_p||^2, features as doubles (row-major,
+// n x D and m x D).  One block per row, psi read through L1/L2.
+template <typename Real>
+__global__ void add_feature_cost(Real* __restrict__ Pi, int n, int m, int D, const double* __restrict__ phi,
+                                 const double* __restrict__ psi, double w) {
+  __shared__ double ph[64];
+  const int i = blockIdx.x;
+  if (threadIdx.x < D) ph[threadIdx.x] = phi[(size_t)i * D + threadIdx.x];
+  __syncthreads();
+  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+    double acc = 0.0;
+    for (int d = 0; d < D; ++d) {
+      const double diff = ph[d] - psi[(size_t)p * D + d];
+      acc += diff * diff;
+    }
+    Pi[(size_t)i * m + p] += (Real)(w * acc);
+  }
+}
+
+// Deterministic dot products: per-block partial sums (FP64), then one block.
+template <typename Real>
+__global__ void dot_partial(const Real* __restrict__ A, const Real* __restrict__ B, size_t N, double* __restrict__ part) {
+  double acc = 0.0;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
+    acc += (double)A[k] * (double)B[k];
+  __shared__ double sm[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+// <CC, T> with CC_ip = ||phi_i - psi_p||^2 computed on the fly.
+template <typename Real>
+__global__ void feature_dot_partial(const Real* __restrict__ T, int n, int m, int D, const double* __restrict__ phi,
+                                    const double* __restrict__ psi, double* __restrict__ part) {
+  double acc = 0.0;
+  const size_t N = (size_t)n * m;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = k / m, p = k % m;
+    double cc = 0.0;
+    for (int d = 0; d < D; ++d) {
+      const double diff = phi[i * D + d] - psi[p * D + d];
+      cc += diff * diff;
+    }
+    acc += cc * (double)T[k];
+  }
+  __shared__ double sm[32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w];
+    part[blockIdx.x] = s;
+  }
+}
+
+// stats: [0] objective, [1] E(T), [2] <CC,T>, [3] eps H(T), [4] sum|T1-u|,
+// [5] sum|T^T 1 - v|, [6] outer iterations, [7] 0.
+__global__ void finish_stats(const double* __restrict__ dotE, int nE, const double* __restrict__ dotC, int nC,
+                             const double* __restrict__ cta_stats, int B, const double* __restrict__ colpart, int m,
+                             const double* __restrict__ v, double eps, double theta, int n_outer,
+                             double* __restrict__ stats) {
+  __shared__ double sm[32];
+  // column marginal error (all threads), then scalar sums by thread 0
+  double ce = 0.0;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+    double cs = 0.0;
+    for (int b = 0; b < B; ++b) cs += colpart[(size_t)b * m + p];
+    ce += fabs(cs - v[p]);
+  }
+  ce = warp_sum(ce);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = ce;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double colerr = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) colerr += sm[w];
+    double E = 0.0, C = 0.0, H = 0.0, re = 0.0;
+    for (int k = 0; k < nE; ++k) E += dotE[k];
+    for (int k = 0; k < nC; ++k) C += dotC[k];
+    for (int b = 0; b < B; ++b) {
+      H += cta_stats[2 * b];
+      re += cta_stats[2 * b + 1];
+    }
+    stats[0] = (1.0 - theta) * C + theta * E;
+    stats[1] = E;
+    stats[2] = C;
+    stats[3] = eps * H;
+    stats[4] = re;
+    stats[5] = colerr;
+    stats[6] = (double)n_outer;
+    stats[7] = 0.0;
+  }
+}
+
+template <typename Real>
+__global__ void potentials_out(const Real* __restrict__ F, int len, double scale, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < len) out[i] = (double)F[i] * scale;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+template <int NW, int VPT, typename Real>
+RowGeom row_geom(const void* Pi, int n, int m, CUtensorMap* tm, int Rmax) {
+  RowGeom g{};
+  const int cover = 32 * NW * VPT;
+  g.vec_bytes = (int)(((size_t)cover * sizeof(Real) + 1023) / 1024 * 1024);
+  g.slot_bytes = g.vec_bytes;
+  memset(tm, 0, sizeof(*tm));
+  g.use_tma = ((((uintptr_t)Pi) & 15) == 0) && encode_rows_tmap(tm, Pi, n, m, sizeof(Real), &g.box_cols) &&
+              (m * (int)sizeof(Real)) <= 256 * 128;
+  const size_t fixed = 1024 + g.vec_bytes + sizeof(Real) * (2 * NW + Rmax) + 128;
+  g.stages = g.use_tma ? (int)std::max<size_t>(2, std::min<size_t>(4, (200 * 1024 - fixed) / g.slot_bytes)) : 2;
+  return g;
+}
+
+template <int NW, int VPT, typename Real>
+int solve1d_typed(const Solve1DArgs& A, void* wsv, size_t ws_bytes) {
+  const int n = A.n, m = A.m;
+  cudaStream_t st = A.stream;
+  const Bands bands = choose_bands(n, A.num_sms);
+  const int B = bands.B, R = bands.R;
+  // Workspace: Pi | F | G | lu | lv | part | colpart | cta_stats | dots | gradient workspace
+  char* ws = (char*)wsv;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = ws + off;
+    off = (off + bytes + 255) / 256 * 256;
+    return p;
+  };
+  Real* Pi = (Real*)take((size_t)n * m * sizeof(Real));
+  Real* F = (Real*)take((size_t)n * sizeof(Real));
+  Real* G = (Real*)take((size_t)m * sizeof(Real));
+  Real* lu = (Real*)take((size_t)n * sizeof(Real));
+  Real* lv = (Real*)take((size_t)m * sizeof(Real));
+  using Part = typename PartT<Real>::type;
+  Part* part = (Part*)take((size_t)B * m * sizeof(Part));
+  double* colpart = (double*)take((size_t)B * m * sizeof(double));
+  double* cta_stats = (double*)take((size_t)2 * B * sizeof(double));
+  const int ndot = 256;
+  double* dotE = (double*)take((size_t)ndot * sizeof(double));
+  double* dotC = (double*)take((size_t)ndot * sizeof(double));
+  char* gws = take(0);
+  if (off > ws_bytes) return GW_ERR_OOM;
+  const size_t gws_bytes = ws_bytes - off;
+
+  const Real c = (Real)(1.4426950408889634 / A.eps);
+  CUtensorMap tm;
+  const RowGeom geo = row_geom<NW, VPT, Real>(Pi, n, m, &tm, R);
+  const size_t smem = rows_smem_bytes<NW, Real>(geo, R);
+  if (cudaFuncSetAttribute(sk_pass<NW, VPT, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(sk_plan<NW, VPT, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess)
+    return GW_ERR_CUDA;
+
+  {
+    TraceScope ts(A.tracer, "solve_setup", st);
+    log2_scaled<Real><<<(n + 255) / 256, 256, 0, st>>>(A.u, n, lu);
+    log2_scaled<Real><<<(m + 255) / 256, 256, 0, st>>>(A.v, m, lv);
+    fill_product<Real><<<4 * A.num_sms, 256, 0, st>>>(A.u, A.v, n, m, (Real*)A.T);
+  }
+  Grad1DArgs ga{};
+  ga.n = n;
+  ga.m = m;
+  ga.k = A.k;
+  ga.hx = A.hx;
+  ga.hy = A.hy;
+  ga.dtype = A.dtype;
+  ga.T = A.T;
+  ga.G = Pi;
+  ga.u = A.u;
+  ga.v = A.v;
+  ga.exact = 0;
+  ga.out_scale = 2.0 * A.theta;
+  ga.stream = st;
+  ga.status = A.status;
+  ga.num_sms = A.num_sms;
+  ga.tracer = A.tracer;
+  ga.force_generic = A.force_generic;
+  const bool fgw = A.theta != 1.0 && A.feat_dim > 0 && A.phi && A.psi;
+
+  for (int l = 0; l < A.n_outer; ++l) {
+    int rc = grad1d_launch(ga, gws, gws_bytes);
+    if (rc != GW_OK) return rc;
+    if (fgw) {
+      TraceScope ts(A.tracer, "add_feature_cost", st);
+      add_feature_cost<Real><<<n, 256, 0, st>>>(Pi, n, m, A.feat_dim, A.phi, A.psi, 1.0 - A.theta);
+    }
+    {
+      TraceScope ts(A.tracer, "solve_setup", st);
+      fill_val<Real><<<(n + 255) / 256, 256, 0, st>>>(F, n, (Real)0);
+      fill_val<Real><<<(m + 255) / 256, 256, 0, st>>>(G, m, (Real)0);
+    }
+    for (int it = 0; it < A.n_inner; ++it) {
+      {
+        TraceScope ts(A.tracer, "sk_pass", st);
+        sk_pass<NW, VPT, Real><<<B, 32 * NW, smem, st>>>(tm, Pi, n, m, R, c, lu, F, G, part, geo, A.status);
+      }
+      {
+        TraceScope ts(A.tracer, "sk_cols", st);
+        sk_cols<Real><<<(m + 255) / 256, 256, 0, st>>>(part, B, m, lv, G);
+      }
+    }
+    {
+      TraceScope ts(A.tracer, "sk_plan", st);
+      sk_plan<NW, VPT, Real><<<B, 32 * NW, smem, st>>>(tm, Pi, n, m, R, c, F, G, A.u, (Real*)A.T, colpart,
+                                                       cta_stats, geo, A.status);
+    }
+  }
+  if (A.f) potentials_out<Real><<<(n + 255) / 256, 256, 0, st>>>(F, n, A.eps / 1.4426950408889634, A.f);
+  if (A.g) potentials_out<Real><<<(m + 255) / 256, 256, 0, st>>>(G, m, A.eps / 1.4426950408889634, A.g);
+  if (A.stats) {
+    TraceScope ts(A.tracer, "solve_stats", st);
+    // E(T) = <G(T; T's marginals), T>; the gradient overwrites Pi.
+    Grad1DArgs ge = ga;
+    ge.exact = 1;
+    ge.out_scale = 1.0;
+    int rc = grad1d_launch(ge, gws, gws_bytes);
+    if (rc != GW_OK) return rc;
+    dot_partial<Real><<<ndot, 256, 0, st>>>(Pi, (const Real*)A.T, (size_t)n * m, dotE);
+    if (fgw)
+      feature_dot_partial<Real><<<ndot, 256, 0, st>>>((const Real*)A.T, n, m, A.feat_dim, A.phi, A.psi, dotC);
+    else
+      fill_val<double><<<1, 256, 0, st>>>(dotC, ndot, 0.0);
+    finish_stats<<<1, 256, 0, st>>>(dotE, ndot, dotC, ndot, cta_stats, B, colpart, m, A.v, A.eps, A.theta,
+                                    A.n_outer, A.stats);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+}
+
+size_t solve1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms) {
+  const size_t rb = dtype == GW_F32 ? 4 : 8;
+  const Bands bands = choose_bands(n, num_sms);
+  size_t b = 0;
+  auto add = [&](size_t x) { b = (b + x + 255) / 256 * 256; };
+  add((size_t)n * m * rb);
+  add(n * rb);
+  add(m * rb);
+  add(n * rb);
+  add(m * rb);
+  add((size_t)bands.B * m * 2 * rb);
+  add((size_t)bands.B * m * 8);
+  add((size_t)2 * bands.B * 8);
+  add(256 * 8);
+  add(256 * 8);
+  return b + grad1d_workspace_bytes(n, m, k, dtype, num_sms) + 4096;
+}
+
+int solve1d_launch(const Solve1DArgs& A, void* ws, size_t ws_bytes) {
+  const int m = A.m;
+  if (A.dtype == GW_F32) {
+    if (m <= 1024) return solve1d_typed<8, 4, float>(A, ws, ws_bytes);
+    if (m <= 4096) return solve1d_typed<16, 8, float>(A, ws, ws_bytes);
+    if (m <= 8192) return solve1d_typed<16, 16, float>(A, ws, ws_bytes);
+    return solve1d_typed<32, 16, float>(A, ws, ws_bytes);
+  }
+  if (m <= 1024) return solve1d_typed<8, 4, double>(A, ws, ws_bytes);
+  if (m <= 4096) return solve1d_typed<16, 8, double>(A, ws, ws_bytes);
+  return solve1d_typed<32, 16, double>(A, ws, ws_bytes);
+}
+
+}  // namespace gw

@@ -1,0 +1,140 @@
+"""Parity of the 1D entropic (F)GW solve (CUDA, through the C ABI) with the
+FP64 oracle's mirror descent (same schedule: T^0 = u v^T, f = g = 0 at every
+outer step, f then g, fixed iteration counts).
+
+Tolerances: double arithmetic reproduces the oracle to 1e-9 (plan) and 1e-10
+(value); float arithmetic keeps the GW value within 1e-5 relative."""
+import numpy as np
+import pytest
+
+from oracle import gw_oracle as O
+from paper_2404_08970_gb300 import inputs as I
+from tests import gwtest_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_solve(w, dtype, theta=1.0, phi=None, psi=None):
+    import torch
+    from paper_2404_08970_gb300 import _lib as L
+    c = U.ctx()
+    n, m = w["nx"], w["ny"]
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    T = torch.empty(n, m, dtype=tdt, device="cuda")
+    f = torch.empty(n, dtype=torch.float64, device="cuda")
+    g = torch.empty(m, dtype=torch.float64, device="cuda")
+    stats = torch.zeros(8, dtype=torch.float64, device="cuda")
+    du = torch.from_numpy(w["u"]).cuda()
+    dv = torch.from_numpy(w["v"]).cuda()
+    D = 0 if phi is None else phi.shape[1]
+    dphi = None if phi is None else torch.from_numpy(np.ascontiguousarray(phi)).cuda()
+    dpsi = None if psi is None else torch.from_numpy(np.ascontiguousarray(psi)).cuda()
+    prob = L.problem(dim=1, nx=n, ny=m, hx=w["hx"], hy=w["hy"], k=w["k"], eps=w["eps"], n_outer=w["n_outer"],
+                     n_inner=w["n_inner"], theta=theta, feat_dim=D,
+                     dtype=L.GW_F32 if dtype == "f32" else L.GW_F64)
+    c.gw_solve(prob, du, dv, T, f, g, stats, dphi, dpsi)
+    c.gw_ctx_check()
+    return T.double().cpu().numpy(), f.cpu().numpy(), g.cpu().numpy(), stats.cpu().numpy()
+
+
+def oracle_solve(w, theta=1.0, phi=None, psi=None):
+    n, m, k = w["nx"], w["ny"], w["k"]
+    DX, DY = O.grid_dist_1d(n, w["hx"], k), O.grid_dist_1d(m, w["hy"], k)
+    CC = None if phi is None else O.fgw_feature_cost(phi, psi)
+    T, f, g = O.mirror_descent(DX, DY, w["u"], w["v"], w["eps"], w["n_outer"], w["n_inner"], theta=theta, CC=CC)
+    E = O.value(DX, DY, T)
+    lin = 0.0 if CC is None else float(np.sum(CC * T))
+    return T, f, g, dict(E=E, lin=lin, obj=(1 - theta) * lin + theta * E, H=w["eps"] * O.entropy(T),
+                         row=float(np.sum(np.abs(T.sum(1) - w["u"]))), col=float(np.sum(np.abs(T.sum(0) - w["v"]))))
+
+
+def fro(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_solve_small_workload_fp64():
+    """n = m = 200, k = 1, Dirichlet(1) marginals, eps = 1e-2, 20 x 100."""
+    w = I.workload_1d_small(0)
+    T, f, g, st = gpu_solve(w, "f64")
+    Ts, fs, gs, ss = oracle_solve(w)
+    assert U.relerr(T, Ts) < 1e-9
+    assert abs(st[1] - ss["E"]) <= 1e-10 * abs(ss["E"])
+    assert abs(st[0] - ss["obj"]) <= 1e-10 * abs(ss["obj"])
+    assert abs(st[3] - ss["H"]) <= 1e-9 * abs(ss["H"])
+    assert st[5] < 1e-12 and abs(st[4] - ss["row"]) < 1e-10
+    assert U.relerr(g, gs) < 1e-9 and U.relerr(f, fs) < 1e-9
+
+
+def test_solve_small_workload_fp32():
+    w = I.workload_1d_small(0)
+    T, f, g, st = gpu_solve(w, "f32")
+    Ts, fs, gs, ss = oracle_solve(w)
+    assert abs(st[1] - ss["E"]) <= 1e-5 * abs(ss["E"]), (st[1], ss["E"])
+    err_T = fro(T, Ts)
+    assert err_T < 1e-3, err_T
+    assert st[5] < 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("shape,k", [((1, 7), 1), ((5, 1), 1), ((37, 23), 2), ((64, 150), 1), ((150, 64), 2),
+                                     ((513, 301), 1)])
+def test_solve_shapes(shape, k, dtype):
+    n, m = shape
+    rng = np.random.default_rng(n * 7 + m)
+    w = dict(nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=k, eps=5e-2, n_outer=5, n_inner=40,
+             u=I.dirichlet(n, 1.0, rng), v=I.dirichlet(m, 1.0, rng))
+    T, f, g, st = gpu_solve(w, dtype)
+    Ts, fs, gs, ss = oracle_solve(w)
+    if dtype == "f64":
+        assert U.relerr(T, Ts) < 1e-9
+        assert abs(st[1] - ss["E"]) <= 1e-10 * max(abs(ss["E"]), 1e-300) + 1e-300
+    else:
+        assert abs(st[1] - ss["E"]) <= 1e-5 * abs(ss["E"]) + 1e-12
+        assert fro(T, Ts) < 1e-3
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_solve_fused_gw(dtype):
+    """theta = 0.5, 16-dim N(0,1) features, squared feature distance."""
+    rng = np.random.default_rng(9)
+    n, m = 80, 96
+    w = dict(nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=1, eps=5e-2, n_outer=5, n_inner=50,
+             u=I.dirichlet(n, 1.0, rng), v=I.dirichlet(m, 1.0, rng))
+    phi, psi = I.features(n, 16, rng) * 0.1, I.features(m, 16, rng) * 0.1
+    T, f, g, st = gpu_solve(w, dtype, theta=0.5, phi=phi, psi=psi)
+    Ts, fs, gs, ss = oracle_solve(w, theta=0.5, phi=phi, psi=psi)
+    tol = 1e-9 if dtype == "f64" else 1e-5
+    assert abs(st[0] - ss["obj"]) <= tol * abs(ss["obj"])
+    assert abs(st[2] - ss["lin"]) <= tol * abs(ss["lin"])
+    if dtype == "f64":
+        assert U.relerr(T, Ts) < 1e-9
+
+
+def test_solve_reflection_and_single_point():
+    """Reversing v's grid reverses the plan's columns; n = 1 gives T = v^T."""
+    rng = np.random.default_rng(12)
+    n, m = 60, 45
+    w = dict(nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=1, eps=5e-2, n_outer=4, n_inner=30,
+             u=I.dirichlet(n, 1.0, rng), v=I.dirichlet(m, 1.0, rng))
+    T, *_ = gpu_solve(w, "f32")
+    w2 = dict(w, v=w["v"][::-1].copy())
+    T2, *_ = gpu_solve(w2, "f32")
+    assert U.relerr(T2[:, ::-1], T) < 1e-4
+    w1 = dict(w, nx=1, hx=1.0, u=np.ones(1))
+    T1, *_ = gpu_solve(w1, "f64")
+    assert U.relerr(T1[0], w1["v"]) < 1e-12
+
+
+def test_solve_invalid_arguments():
+    from paper_2404_08970_gb300 import _lib as L
+    import torch
+    c = U.ctx()
+    u = torch.full((4,), 0.25, dtype=torch.float64, device="cuda")
+    T = torch.empty(4, 4, device="cuda")
+    for p in [L.problem(dim=1, nx=4, ny=4, eps=0.0, n_outer=1, n_inner=1),
+              L.problem(dim=1, nx=4, ny=4, eps=0.1, n_outer=1, n_inner=0),
+              L.problem(dim=1, nx=4, ny=4, eps=0.1, n_outer=1, n_inner=1, theta=0.5, feat_dim=0),
+              L.problem(dim=1, nx=4, ny=4, eps=0.1, n_outer=1, n_inner=1, theta=1.5)]:
+        with pytest.raises(L.GWError) as e:
+            c.gw_solve(p, u, u, T)
+        assert e.value.status == L.GW_ERR_INVALID
