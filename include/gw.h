@@ -61,6 +61,9 @@ typedef enum { GW_F32 = 0, GW_F64 = 1 } gw_dtype;
  * only cost, h^k |i-j|^k.  GW_COST_SQEUCLID: h^2 ((a-a')^2 + (b-b')^2). */
 typedef enum { GW_COST_POW = 0, GW_COST_SQEUCLID = 1 } gw_cost;
 
+/* Arithmetic of the dense comparison gradient (gw_grad_dense). */
+typedef enum { GW_DENSE_FP32 = 0, GW_DENSE_TF32 = 1, GW_DENSE_BF16 = 2, GW_DENSE_FP64 = 3 } gw_dense_precision;
+
 /* Which marginals build the constant term c_x, c_y of the gradient. */
 typedef enum { GW_MARG_TARGET = 0, GW_MARG_EXACT = 1 } gw_marginals;
 
@@ -132,6 +135,23 @@ gw_status gw_ctx_profile_report(gw_ctx* ctx, char* buf, size_t len, int reset);
  */
 gw_status gw_grad(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const double* d_v,
                   const void* d_T, void* d_G, int marginals, void* stream);
+
+/*
+ * gw_grad_dense - the same gradient G as gw_grad, computed the original way
+ * (Sec. 2.1, gradient decomposition): the distance matrices D_X (n x n) and
+ * D_Y (m x m) are materialised and G = c_x 1^T + 1 c_y^T - 2 (D_X T) D_Y is
+ * formed with two cuBLAS matrix products, O(n^2 m + n m^2).  It exists as the
+ * comparison baseline of the structured method.
+ *
+ *   precision  GW_DENSE_FP32 (FP32 CUDA cores), GW_DENSE_TF32 or GW_DENSE_BF16
+ *              (tensor cores, FP32 accumulation; BF16 rounds T, D and the
+ *              intermediate D_X T to bfloat16), GW_DENSE_FP64.
+ *   prob->dtype must be GW_F64 for GW_DENSE_FP64 and GW_F32 otherwise; the
+ *   other arguments are as for gw_grad (dim 1 only).  The dense distance
+ *   matrices are cached in the context between calls.
+ */
+gw_status gw_grad_dense(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const double* d_v,
+                        const void* d_T, void* d_G, int marginals, int precision, void* stream);
 
 /*
  * gw_solve - entropic (fused) Gromov-Wasserstein by mirror descent with

@@ -32,6 +32,11 @@ GW_F64 = 1
 # gw_cost
 GW_COST_POW = 0
 GW_COST_SQEUCLID = 1
+# gw_dense_precision
+GW_DENSE_FP32 = 0
+GW_DENSE_TF32 = 1
+GW_DENSE_BF16 = 2
+GW_DENSE_FP64 = 3
 # gw_marginals
 GW_MARG_TARGET = 0
 GW_MARG_EXACT = 1
@@ -86,6 +91,7 @@ def load() -> ctypes.CDLL:
         "gw_ctx_profile_report": (S, [P, ctypes.c_char_p, ctypes.c_size_t, I]),
         "gw_grad": (S, [P, prob, P, P, P, P, I, P]),
         "gw_solve": (S, [P, prob, P, P, P, P, P, P, P, P, P]),
+        "gw_grad_dense": (S, [P, prob, P, P, P, P, I, I, P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -177,3 +183,9 @@ class Context:
         st = self.lib.gw_solve(self.h, ctypes.byref(prob), _ptr(u), _ptr(v), _ptr(phi), _ptr(psi), _ptr(T),
                                _ptr(f), _ptr(g), _ptr(stats), _stream(stream))
         return self._check(st, "gw_solve")
+
+    def gw_grad_dense(self, prob: gw_problem, u, v, T, G, marginals=GW_MARG_TARGET, precision=GW_DENSE_BF16,
+                      stream=None) -> int:
+        st = self.lib.gw_grad_dense(self.h, ctypes.byref(prob), _ptr(u), _ptr(v), _ptr(T), _ptr(G), marginals,
+                                    precision, _stream(stream))
+        return self._check(st, "gw_grad_dense")

@@ -1,0 +1,219 @@
+// Dense comparison gradient: G = c_x 1^T + 1 c_y^T - 2 D_X T D_Y with the
+// distance matrices materialised and the two products D_X T and (D_X T) D_Y
+// done by cuBLAS (the "original" O(n^2 m + n m^2) route of Sec. 2.1 that the
+// structured recursion replaces).  Precisions: FP32 (CUDA cores), TF32 and
+// BF16 tensor cores with FP32 accumulation, FP64.
+#include <cublas_v2.h>
+#include <cuda_bf16.h>
+
+#include <cmath>
+
+#include "gw_common.cuh"
+#include "gw_internal.h"
+
+namespace gw {
+
+template <typename Out>
+__global__ void build_dist(Out* __restrict__ D, int n, double hk, int k) {
+  const size_t N = (size_t)n * n;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
+    const long long i = (long long)(idx / n), j = (long long)(idx % n);
+    double d = (double)(i > j ? i - j : j - i);
+    double v = 1.0;
+    for (int e = 0; e < k; ++e) v *= d;
+    D[idx] = (Out)(hk * v);
+  }
+}
+
+__global__ void to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, size_t N) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// G = cx_i + cy_p - s * Z_ip, in place on Z (= G).  cx, cy hold hi parts first.
+template <typename Real>
+__global__ void dense_epilogue(Real* __restrict__ G, int n, int m, const Real* __restrict__ cx,
+                               const Real* __restrict__ cy, Real s) {
+  const size_t N = (size_t)n * m;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = idx / m, p = idx % m;
+    G[idx] = fma(-s, G[idx], cx[i] + cy[p]);
+  }
+}
+
+template <typename Real>
+__global__ void row_sums(const Real* __restrict__ T, int n, int m, double* __restrict__ r) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int p = threadIdx.x & 31; p < m; p += 32) acc += (double)T[(size_t)i * m + p];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) r[i] = acc;
+}
+
+template <typename Real>
+__global__ void col_sums(const Real* __restrict__ T, int n, int m, double* __restrict__ c) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m) return;
+  double acc = 0.0;
+  for (int i = 0; i < n; ++i) acc += (double)T[(size_t)i * m + p];
+  c[p] = acc;
+}
+
+struct DenseCache {
+  int n = 0, k = 0, prec = -1;
+  double h = 0;
+  void* D = nullptr;
+};
+
+struct DenseState {
+  cublasHandle_t handle = nullptr;
+  DenseCache X, Y;
+};
+
+static int ensure_dist(DenseCache& c, int n, double h, int k, int prec, cudaStream_t st) {
+  if (c.D && c.n == n && c.h == h && c.k == k && c.prec == prec) return GW_OK;
+  if (c.D) {
+    cudaStreamSynchronize(st);
+    cudaFree(c.D);
+    c.D = nullptr;
+  }
+  const size_t esz = prec == GW_DENSE_BF16 ? 2 : (prec == GW_DENSE_FP64 ? 8 : 4);
+  if (cudaMalloc(&c.D, (size_t)n * n * esz) != cudaSuccess) {
+    cudaGetLastError();
+    c.D = nullptr;
+    return GW_ERR_OOM;
+  }
+  const double hk = std::pow(h, k);
+  if (prec == GW_DENSE_BF16)
+    build_dist<__nv_bfloat16><<<1024, 256, 0, st>>>((__nv_bfloat16*)c.D, n, hk, k);
+  else if (prec == GW_DENSE_FP64)
+    build_dist<double><<<1024, 256, 0, st>>>((double*)c.D, n, hk, k);
+  else
+    build_dist<float><<<1024, 256, 0, st>>>((float*)c.D, n, hk, k);
+  c.n = n;
+  c.h = h;
+  c.k = k;
+  c.prec = prec;
+  return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+}
+
+void* dense_state_create() { return new DenseState(); }
+
+void dense_state_destroy(void* p) {
+  DenseState* s = (DenseState*)p;
+  if (!s) return;
+  if (s->X.D) cudaFree(s->X.D);
+  if (s->Y.D) cudaFree(s->Y.D);
+  if (s->handle) cublasDestroy(s->handle);
+  delete s;
+}
+
+size_t dense_workspace_bytes(int n, int m, int prec) {
+  const size_t nm = (size_t)n * m;
+  size_t b = 0;
+  if (prec == GW_DENSE_BF16) b += 2 * nm * 2;           // T and Y in bf16
+  else if (prec == GW_DENSE_FP64) b += nm * 8;          // Y
+  else b += nm * 4;                                     // Y
+  b += ((size_t)2 * (n + m) * 8) + (size_t)(n + m) * 8 + marg_part_doubles(n, 3) * 8 + marg_part_doubles(m, 3) * 8 + 8192;
+  return b;
+}
+
+int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_bytes) {
+  DenseState* S = (DenseState*)state;
+  cudaStream_t st = a.stream;
+  if (!S->handle) {
+    if (cublasCreate(&S->handle) != CUBLAS_STATUS_SUCCESS) return GW_ERR_CUDA;
+  }
+  cublasSetStream(S->handle, st);
+  const int n = a.n, m = a.m;
+  int rc = ensure_dist(S->X, n, a.hx, a.k, a.prec, st);
+  if (rc != GW_OK) return rc;
+  rc = ensure_dist(S->Y, m, a.hy, a.k, a.prec, st);
+  if (rc != GW_OK) return rc;
+  char* ws = (char*)wsv;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    char* p = ws + off;
+    off = (off + bytes + 255) / 256 * 256;
+    return p;
+  };
+  const size_t nm = (size_t)n * m;
+  const bool dbl = a.prec == GW_DENSE_FP64;
+  const size_t rb = dbl ? 8 : 4;
+  void* Tin = (void*)a.T;
+  void* Y = nullptr;
+  if (a.prec == GW_DENSE_BF16) {
+    Tin = take(nm * 2);
+    Y = take(nm * 2);
+  } else {
+    Y = take(nm * rb);
+  }
+  void* cx = take((size_t)2 * n * rb);
+  void* cy = take((size_t)2 * m * rb);
+  double* r = (double*)take((size_t)n * 8);
+  double* cc = (double*)take((size_t)m * 8);
+  double* part = (double*)take((marg_part_doubles(n, a.k) + marg_part_doubles(m, a.k)) * 8 + 512);
+  if (off > ws_bytes) return GW_ERR_OOM;
+
+  const double* wx = a.u;
+  const double* wy = a.v;
+  if (a.exact) {
+    TraceScope ts(a.tracer, "dense_marginals", st);
+    if (dbl) {
+      row_sums<double><<<(n + 7) / 8, 256, 0, st>>>((const double*)a.T, n, m, r);
+      col_sums<double><<<(m + 255) / 256, 256, 0, st>>>((const double*)a.T, n, m, cc);
+    } else {
+      row_sums<float><<<(n + 7) / 8, 256, 0, st>>>((const float*)a.T, n, m, r);
+      col_sums<float><<<(m + 255) / 256, 256, 0, st>>>((const float*)a.T, n, m, cc);
+    }
+    wx = r;
+    wy = cc;
+  }
+  rc = marg_const2_launch(wx, n, std::pow(a.hx, 2 * a.k), cx, wy, m, std::pow(a.hy, 2 * a.k), cy, a.k,
+                          dbl ? GW_F64 : GW_F32, part, st, a.tracer);
+  if (rc != GW_OK) return rc;
+
+  // Row-major n x m arrays are column-major m x n.  Y^T = T^T D_X and
+  // Z^T = D_Y Y^T in column-major terms.
+  cublasStatus_t cs;
+  {
+    TraceScope ts(a.tracer, "dense_gemm", st);
+    if (a.prec == GW_DENSE_BF16) {
+      to_bf16<<<4 * 152, 256, 0, st>>>((const float*)a.T, (__nv_bfloat16*)Tin, nm);
+      const float one = 1.f, zero = 0.f;
+      cs = cublasGemmEx(S->handle, CUBLAS_OP_N, CUBLAS_OP_N, m, n, n, &one, Tin, CUDA_R_16BF, m, S->X.D,
+                        CUDA_R_16BF, n, &zero, Y, CUDA_R_16BF, m, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+      if (cs == CUBLAS_STATUS_SUCCESS)
+        cs = cublasGemmEx(S->handle, CUBLAS_OP_N, CUBLAS_OP_N, m, n, m, &one, S->Y.D, CUDA_R_16BF, m, Y,
+                          CUDA_R_16BF, m, &zero, a.G, CUDA_R_32F, m, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+    } else if (dbl) {
+      const double one = 1.0, zero = 0.0;
+      cs = cublasDgemm(S->handle, CUBLAS_OP_N, CUBLAS_OP_N, m, n, n, &one, (const double*)Tin, m,
+                       (const double*)S->X.D, n, &zero, (double*)Y, m);
+      if (cs == CUBLAS_STATUS_SUCCESS)
+        cs = cublasDgemm(S->handle, CUBLAS_OP_N, CUBLAS_OP_N, m, n, m, &one, (const double*)S->Y.D, m,
+                         (const double*)Y, m, &zero, (double*)a.G, m);
+    } else {
+      const float one = 1.f, zero = 0.f;
+      const cublasComputeType_t ct = a.prec == GW_DENSE_TF32 ? CUBLAS_COMPUTE_32F_FAST_TF32 : CUBLAS_COMPUTE_32F;
+      cs = cublasGemmEx(S->handle, CUBLAS_OP_N, CUBLAS_OP_N, m, n, n, &one, Tin, CUDA_R_32F, m, S->X.D, CUDA_R_32F,
+                        n, &zero, Y, CUDA_R_32F, m, ct, CUBLAS_GEMM_DEFAULT);
+      if (cs == CUBLAS_STATUS_SUCCESS)
+        cs = cublasGemmEx(S->handle, CUBLAS_OP_N, CUBLAS_OP_N, m, n, m, &one, S->Y.D, CUDA_R_32F, m, Y, CUDA_R_32F,
+                          m, &zero, a.G, CUDA_R_32F, m, ct, CUBLAS_GEMM_DEFAULT);
+    }
+  }
+  if (cs != CUBLAS_STATUS_SUCCESS) return GW_ERR_CUDA;
+  {
+    TraceScope ts(a.tracer, "dense_epilogue", st);
+    if (dbl)
+      dense_epilogue<double><<<4 * 152, 256, 0, st>>>((double*)a.G, n, m, (const double*)cx, (const double*)cy, 2.0);
+    else
+      dense_epilogue<float><<<4 * 152, 256, 0, st>>>((float*)a.G, n, m, (const float*)cx, (const float*)cy, 2.f);
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+}
+
+}  // namespace gw

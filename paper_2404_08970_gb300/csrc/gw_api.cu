@@ -80,6 +80,7 @@ struct gw_ctx {
   unsigned* status = nullptr;  // device status word
   EventTracer* tracer = nullptr;  // non-null while profiling is on
   int force_generic = 0;          // GW_FORCE_GENERIC set at creation: block-scan row kernel only
+  void* dense = nullptr;          // cuBLAS handle and cached dense distance matrices
   gw::Tracer* tr() { return tracer; }
 };
 
@@ -166,6 +167,7 @@ void gw_ctx_destroy(gw_ctx* c) {
   cudaDeviceSynchronize();
   if (c->ws) cudaFree(c->ws);
   if (c->status) cudaFree(c->status);
+  gw::dense_state_destroy(c->dense);
   delete c->tracer;
   delete c;
 }
@@ -270,6 +272,54 @@ gw_status gw_grad(gw_ctx* c, const gw_problem* p, const double* d_u, const doubl
   if (rc != GW_OK) {
     cudaError_t e = cudaGetLastError();
     return fail(c, (gw_status)rc, "gw_grad launch failed: %s", cudaGetErrorString(e));
+  }
+  c->err.clear();
+  return GW_OK;
+}
+
+gw_status gw_grad_dense(gw_ctx* c, const gw_problem* p, const double* d_u, const double* d_v, const void* d_T,
+                        void* d_G, int marginals, int precision, void* stream) {
+  if (!c) return GW_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  gw_status s = check_grid(c, p);
+  if (s != GW_OK) return s;
+  if (p->dim != 1) return fail(c, GW_ERR_INVALID, "gw_grad_dense: dim must be 1");
+  if (precision < GW_DENSE_FP32 || precision > GW_DENSE_FP64)
+    return fail(c, GW_ERR_INVALID, "gw_grad_dense: unknown precision %d", precision);
+  if ((precision == GW_DENSE_FP64) != (p->dtype == GW_F64))
+    return fail(c, GW_ERR_INVALID, "gw_grad_dense: dtype must be GW_F64 exactly for GW_DENSE_FP64");
+  if (marginals != GW_MARG_TARGET && marginals != GW_MARG_EXACT)
+    return fail(c, GW_ERR_INVALID, "marginals must be GW_MARG_TARGET or GW_MARG_EXACT");
+  if (!d_T || !d_G) return fail(c, GW_ERR_INVALID, "d_T and d_G must not be NULL");
+  if (marginals == GW_MARG_TARGET && (!d_u || !d_v))
+    return fail(c, GW_ERR_INVALID, "target marginals requested but d_u or d_v is NULL");
+  const size_t esz = p->dtype == GW_F32 ? 4 : 8;
+  const size_t nm = (size_t)p->nx * (size_t)p->ny;
+  const char* t0 = (const char*)d_T;
+  const char* g0 = (const char*)d_G;
+  if (t0 < g0 + nm * esz && g0 < t0 + nm * esz) return fail(c, GW_ERR_INVALID, "d_T and d_G overlap");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
+  if (!c->dense) c->dense = gw::dense_state_create();
+  gw::DenseArgs a{};
+  a.n = p->nx;
+  a.m = p->ny;
+  a.k = p->k;
+  a.prec = precision;
+  a.exact = marginals == GW_MARG_EXACT;
+  a.hx = p->hx;
+  a.hy = p->hy;
+  a.u = d_u;
+  a.v = d_v;
+  a.T = d_T;
+  a.G = d_G;
+  a.stream = (cudaStream_t)stream;
+  a.tracer = c->tr();
+  s = ensure_ws(c, gw::dense_workspace_bytes(a.n, a.m, precision));
+  if (s != GW_OK) return s;
+  int rc = gw::dense_grad_launch(c->dense, a, c->ws, c->ws_bytes);
+  if (rc != GW_OK) {
+    cudaError_t e = cudaGetLastError();
+    return fail(c, (gw_status)rc, "gw_grad_dense failed: %s", cudaGetErrorString(e));
   }
   c->err.clear();
   return GW_OK;

@@ -101,6 +101,21 @@ int marg_const_launch(const double* w, int len, int k, double h, void* out, int 
 int marg_const2_launch(const double* wx, int n, double fx, void* outx, const double* wy, int m, double fy,
                        void* outy, int k, int dtype, double* part, cudaStream_t stream, Tracer* tracer);
 
+// Dense comparison gradient through cuBLAS (dense.cu).
+struct DenseArgs {
+  int n, m, k, prec, exact;
+  double hx, hy;
+  const double *u, *v;
+  const void* T;
+  void* G;
+  cudaStream_t stream;
+  Tracer* tracer;
+};
+void* dense_state_create();
+void dense_state_destroy(void* state);
+size_t dense_workspace_bytes(int n, int m, int prec);
+int dense_grad_launch(void* state, const DenseArgs& a, void* ws, size_t ws_bytes);
+
 // Entropic (fused) GW by mirror descent on 1D grids (sinkhorn.cu).
 struct Solve1DArgs {
   int n, m, k, dtype;
