@@ -116,10 +116,10 @@ class Clocks:
     def start(self):
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
-            self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+                                          "--format=csv,noheader,nounits", "-lms", "50", "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.5)
         except Exception:
             self.proc = None
 
@@ -131,8 +131,9 @@ class Clocks:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        self.fh.close()
         sm, smax, reasons = [], [], set()
+        if not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
@@ -239,13 +240,13 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    clocks = Clocks(local)
+    clocks.start()  # sampled from warm-up through the dense and solve sections
     for _ in range(max(3, args.warmup)):
         step()
     ctx.gw_ctx_check(stream)
     barrier()
 
-    clocks = Clocks(local)
-    clocks.start()
     ctx.gw_ctx_profile(True)
     ctx.gw_ctx_profile_report(reset=True)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -259,7 +260,6 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     prof = ctx.gw_ctx_profile_report(reset=True)
     ctx.gw_ctx_profile(False)
-    clk = clocks.stop()
     ctx.gw_ctx_check(stream)
 
     ms_max = ms
@@ -364,6 +364,8 @@ def run_ours(args):
                  "dense_solves_per_s_estimate": (1e3 / (other + 20 * dense_grad_ms)) if dense_grad_ms else None,
                  "note": "Sinkhorn passes dominate the solve (2000 passes vs 20 gradients); the dense estimate "
                          "replaces only the 20 gradients by the best dense gradient time"}
+
+    clk = clocks.stop()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
