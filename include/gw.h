@@ -137,6 +137,30 @@ gw_status gw_grad(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const 
                   const void* d_T, void* d_G, int marginals, void* stream);
 
 /*
+ * gw_grad_noalloc - gw_grad without any device allocation (the paper has no
+ * counterpart; this is a deployment convenience).
+ *
+ * For callers that cannot allocate device memory when they need a gradient:
+ * a process whose device memory is fully reserved by another framework's
+ * caching allocator, a thread that must not block in cudaMalloc/cudaFree
+ * (both can synchronise the device), or code that must keep a fixed memory
+ * footprint after start-up.  The scratch comes from one static device array
+ * of 32 MiB that every device loading the library reserves until exit; no
+ * context is needed and nothing is allocated.
+ *
+ *   Arguments as for gw_grad, on the current CUDA device.  Problems whose
+ *   scratch need exceeds 32 MiB (about 4096 x 4096 floats with k <= 2) return
+ *   GW_ERR_INVALID; so do invalid descriptors or NULL required pointers.
+ *   The first call on each device looks up the array's device address (make
+ *   that first call before any stream capture).  All calls share the array:
+ *   calls that overlap on the GPU (different streams, no ordering) race.
+ *   Bounded device waits still end, but this entry point does not report
+ *   them (there is no context status word).
+ */
+gw_status gw_grad_noalloc(const gw_problem* prob, const double* d_u, const double* d_v, const void* d_T,
+                          void* d_G, int marginals, void* stream);
+
+/*
  * gw_grad_dense - the same gradient G as gw_grad, computed the original way
  * (Sec. 2.1, gradient decomposition): the distance matrices D_X (n x n) and
  * D_Y (m x m) are materialised and G = c_x 1^T + 1 c_y^T - 2 (D_X T) D_Y is

@@ -92,6 +92,7 @@ def load() -> ctypes.CDLL:
         "gw_grad": (S, [P, prob, P, P, P, P, I, P]),
         "gw_solve": (S, [P, prob, P, P, P, P, P, P, P, P, P]),
         "gw_grad_dense": (S, [P, prob, P, P, P, P, I, I, P]),
+        "gw_grad_noalloc": (S, [prob, P, P, P, P, I, P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -123,6 +124,15 @@ def _stream(stream):
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream
+
+
+def gw_grad_noalloc(prob: gw_problem, u, v, T, G, marginals=GW_MARG_TARGET, stream=None) -> int:
+    """gw_grad without device allocation (fixed static scratch; see include/gw.h)."""
+    lib = load()
+    st = lib.gw_grad_noalloc(ctypes.byref(prob), _ptr(u), _ptr(v), _ptr(T), _ptr(G), marginals, _stream(stream))
+    if st < 0:
+        raise GWError(st, "gw_grad_noalloc")
+    return st
 
 
 def problem(dim=1, nx=1, ny=1, hx=1.0, hy=1.0, k=1, cost=GW_COST_POW, eps=1e-2, n_outer=1, n_inner=1,
