@@ -81,6 +81,11 @@ struct gw_ctx {
   EventTracer* tracer = nullptr;  // non-null while profiling is on
   int force_generic = 0;          // GW_FORCE_GENERIC set at creation: block-scan row kernel only
   void* dense = nullptr;          // cuBLAS handle and cached dense distance matrices
+  // Graph of the last solve (the whole mirror descent), relaunched while the
+  // arguments stay the same.
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t solve_exec = nullptr;
+  std::string solve_key;
   gw::Tracer* tr() { return tracer; }
 };
 
@@ -168,6 +173,8 @@ void gw_ctx_destroy(gw_ctx* c) {
   if (c->ws) cudaFree(c->ws);
   if (c->status) cudaFree(c->status);
   gw::dense_state_destroy(c->dense);
+  if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+  if (c->cap) cudaStreamDestroy(c->cap);
   delete c->tracer;
   delete c;
 }
@@ -369,7 +376,47 @@ gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const doub
   a.force_generic = c->force_generic;
   s = ensure_ws(c, gw::solve1d_workspace_bytes(a.n, a.m, a.k, a.dtype, a.num_sms));
   if (s != GW_OK) return s;
-  int rc = gw::solve1d_launch(a, c->ws, c->ws_bytes);
+  int rc;
+  if (c->tracer) {
+    // Per-kernel timing wants eager launches.
+    rc = gw::solve1d_launch(a, c->ws, c->ws_bytes);
+  } else {
+    // The whole solve (thousands of short launches) as one CUDA graph,
+    // captured on a side stream and relaunched while the arguments match.
+    char key[512];
+    snprintf(key, sizeof key, "%d %d %d %d %.17g %.17g %.17g %.17g %d %d %d %p %p %p %p %p %p %p %p %p %zu",
+             a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.theta, a.n_outer, a.n_inner, a.feat_dim, (void*)a.u,
+             (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.f, (void*)a.g, (void*)a.stats, c->ws, c->ws_bytes);
+    if (!c->solve_exec || c->solve_key != key) {
+      if (c->solve_exec) {
+        cudaGraphExecDestroy(c->solve_exec);
+        c->solve_exec = nullptr;
+      }
+      if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "capture stream");
+      gw::Solve1DArgs ac = a;
+      ac.stream = c->cap;
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+      rc = gw::solve1d_launch(ac, c->ws, c->ws_bytes);
+      e = cudaStreamEndCapture(c->cap, &graph);
+      if (rc != GW_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(c, rc != GW_OK ? (gw_status)rc : GW_ERR_CUDA, "gw_solve capture failed");
+      }
+      e = cudaGraphInstantiate(&c->solve_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        c->solve_exec = nullptr;
+        return cuda_fail(c, e, "graph instantiate");
+      }
+      c->solve_key = key;
+    }
+    cudaError_t e = cudaGraphLaunch(c->solve_exec, a.stream);
+    rc = e == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+  }
   if (rc != GW_OK) {
     cudaError_t e = cudaGetLastError();
     return fail(c, (gw_status)rc, "gw_solve launch failed: %s", cudaGetErrorString(e));

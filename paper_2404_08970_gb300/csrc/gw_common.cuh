@@ -14,9 +14,9 @@ enum : unsigned {
 };
 
 // Upper bound on the polls of one bounded wait before it gives up.  A healthy
-// wait ends within a few thousand polls; 2^24 polls with a short sleep is
-// well above a second.
-constexpr unsigned kWaitLimit = 1u << 24;
+// wait ends within a few thousand polls; 2^22 polls with a short sleep is
+// about half a second.
+constexpr unsigned kWaitLimit = 1u << 22;
 
 __device__ __forceinline__ void set_status(unsigned* status, unsigned bit) {
   if (status) atomicOr(status, bit);
@@ -165,6 +165,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 // Bounded wait on an mbarrier phase.  Returns false (and sets ERR_TIMEOUT)
 // if the phase did not complete within kWaitLimit polls.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned* status) {
+  if (mbar_try_wait(bar, parity)) return true;
+  // Once any wait has given up, the results are already invalid: later waits
+  // return at once so that the launch finishes quickly and reports.
+  if (status && (*(volatile unsigned*)status & ERR_TIMEOUT)) return false;
   for (unsigned it = 0; it < kWaitLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if (it > 64) __nanosleep(64);

@@ -31,7 +31,14 @@
 
 namespace gw {
 
-__device__ __forceinline__ float ex2(float x) { return exp2f(x); }
+// exp2 on the special-function unit (relative error about 2 ulp, subnormal
+// results flushed to zero, which only drops terms below 2^-126 of a sum of
+// terms bounded by 1).
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ double ex2(double x) { return exp2(x); }
 __device__ __forceinline__ float lg2(float x) { return log2f(x); }
 __device__ __forceinline__ double lg2(double x) { return log2(x); }
@@ -70,7 +77,7 @@ struct RowGeom {
 
 template <int NW, typename Real>
 size_t rows_smem_bytes(const RowGeom& g, int Rmax) {
-  return 1024 + (size_t)g.stages * g.slot_bytes + g.vec_bytes + sizeof(Real) * (2 * NW + Rmax) + 16 +
+  return 1024 + (size_t)g.stages * g.slot_bytes + g.vec_bytes + sizeof(Real) * (2 * NW + 3 * Rmax) + 16 +
          8 * (size_t)g.stages + 64;
 }
 
@@ -103,6 +110,52 @@ struct RowRing {
   }
 };
 
+__device__ __forceinline__ float u_or_exp(float lu) { return exp2f(lu); }
+__device__ __forceinline__ double u_or_exp(double lu) { return exp2(lu); }
+
+// Row sum out of range: redo row `tl` with a max shift from the ring slot
+// (block-uniform branch; sfb holds 32 scratch reals).
+template <int VPT, typename Real>
+__device__ __forceinline__ void row_fallback(RowRing<Real>& rr, int tl, int NT, unsigned* status, Real c, Real (&x)[VPT],
+                                          const Real (&Gv)[VPT], Real Fo, Real lui, Real (&acc)[VPT], Real* F,
+                                          Real* Fband, int ip, Real* sfb, int lane, int warp, int tid) {
+  const int slot = tl % rr.stages;
+  const unsigned char* xr = rr.use_tma ? rr.ring + (size_t)slot * rr.slot_bytes : rr.ring + (size_t)(tl & 1) * rr.slot_bytes;
+  lds_swz<Real, VPT>(xr, tid * VPT, x);
+  const int NW = NT / 32;
+  Real e[VPT];
+  Real lm = -INFINITY;
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    e[v] = fma(-c, x[v], Gv[v] + Fo);
+    lm = fmax(lm, e[v]);
+  }
+  lm = warp_max(lm);
+  __syncthreads();
+  if (lane == 0) sfb[warp] = lm;
+  __syncthreads();
+  Real M = -INFINITY;
+  for (int w = 0; w < NW; ++w) M = fmax(M, sfb[w]);
+  Real s2 = 0;
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) s2 += ex2(e[v] - M);
+  s2 = warp_sum(s2);
+  __syncthreads();
+  if (lane == 0) sfb[warp] = s2;
+  __syncthreads();
+  Real S2 = 0;
+  for (int w = 0; w < NW; ++w) S2 += sfb[w];
+  const Real Fn = Fo + lui - (M + lg2(S2));
+  // Column terms 2^(Fn + G - c Pi) directly.
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) acc[v] += ex2(Fn + e[v] - Fo);
+  if (tid == 0) {
+    F[ip] = Fn;
+    Fband[tl] = Fn;
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // sk_pass
 // ---------------------------------------------------------------------------
@@ -117,8 +170,10 @@ __global__ void __launch_bounds__(32 * NW, 1)
   unsigned char* ring = sm;
   unsigned char* Gs = ring + (size_t)geo.stages * geo.slot_bytes;
   Real* red = reinterpret_cast<Real*>(Gs + geo.vec_bytes);  // [2][NW]
-  Real* Fband = red + 2 * NW;
-  unsigned char* braw = reinterpret_cast<unsigned char*>(Fband + R);
+  Real* Fband = red + 2 * NW;  // new potentials of the band's rows
+  Real* Fold = Fband + R;      // previous potentials of the band's rows
+  Real* LU = Fold + R;         // log2 u of the band's rows
+  unsigned char* braw = reinterpret_cast<unsigned char*>(LU + R);
   uint64_t* bars = reinterpret_cast<uint64_t*>(braw + ((8u - (smem_u32(braw) & 7u)) & 7u));
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -131,86 +186,105 @@ __global__ void __launch_bounds__(32 * NW, 1)
     for (int st = 0; st < geo.stages; ++st) mbar_init(&bars[st], 1);
     fence_mbar_init();
   }
-  for (int p = tid; p < m_pad; p += NT) sts_swz<Real>(Gs, p, p < m ? Gp[p] : (Real)0);
+  // The band's previous potentials and log2 u, staged once so that no row
+  // waits on a dependent global load.
+  for (int t = tid; t < Ra; t += NT) {
+    Fold[t] = F[s + t];
+    LU[t] = lu[s + t];
+  }
+  // Padded columns get G = -inf, so their terms are exactly zero.
+  for (int p = tid; p < m_pad; p += NT) sts_swz<Real>(Gs, p, p < m ? Gp[p] : (Real)-INFINITY);
   for (int st = 0; st < geo.stages; ++st)
     for (int p = m + tid; p < m_pad; p += NT) sts_swz<Real>(ring + (size_t)st * geo.slot_bytes, p, (Real)0);
   __syncthreads();
+  // Every slot is free at the start: rows 0 .. stages-1.  Later, the slot of
+  // row j-1 is refilled (with row j-1+stages) after iteration j.
   if (geo.use_tma && tid == 0)
-    for (int tl = 0; tl < geo.stages - 1 && tl < Ra; ++tl) rr.issue(tl);
+    for (int tl = 0; tl < geo.stages && tl < Ra; ++tl) rr.issue(tl);
 
   Real Gv[VPT];
   lds_swz<Real, VPT>(Gs, c0, Gv);
-  Real acc[VPT], mx[VPT];
+  Real acc[VPT];
 #pragma unroll
-  for (int v = 0; v < VPT; ++v) {
-    acc[v] = 0;
-    mx[v] = -INFINITY;
-  }
+  for (int v = 0; v < VPT; ++v) acc[v] = 0;
+  __shared__ Real sfb[32];  // fallback reductions
 
-  for (int t = 0; t < Ra; ++t) {
-    const int i = s + t;
-    const unsigned char* xr = rr.get(t, NT, status);
-    Real x[VPT];
-    lds_swz<Real, VPT>(xr, c0, x);
-    const Real Fo = F[i];
-    // Row sum with the previous F as reference.
-    Real e[VPT];
-    Real sum = 0;
+  // Row j: w_j,p = 2^(F_old,j + G_p - c Pi_jp) (every w <= v_p after a column
+  // update), S_j = sum_p w_j,p.  The new potential is F_j + log2(u_j / S_j) and
+  // the column sums need 2^(F_new,j + G_p - c Pi_jp) = (u_j / S_j) w_j,p, so one
+  // exp2 per element serves both halves.  Row j's column update runs after the
+  // row pass of row j + 1, so each block barrier has work on both sides.
+  Real wcur[VPT], wprev[VPT];
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      e[v] = (c0 + v < m) ? fma(-c, x[v], Gv[v] + Fo) : (Real)-INFINITY;
-      sum += ex2(e[v]);
-    }
-    sum = warp_sum(sum);
-    Real* rb = red + (t & 1) * NW;
-    if (lane == 0) rb[warp] = sum;
-    __syncthreads();
-    // The slot of row t-1 is free: refill it with row t + stages - 1.
-    if (geo.use_tma && tid == 0 && t + geo.stages - 1 < Ra) {
-      fence_proxy_async_smem();
-      rr.issue(t + geo.stages - 1);
-    }
-    Real S = 0;
+  for (int v = 0; v < VPT; ++v) wprev[v] = 0;
+  Real Fo_prev = 0;
+  for (int j = 0; j <= Ra; ++j) {
+    if (j < Ra) {
+      const unsigned char* xr = rr.get(j, NT, status);
+      Real x[VPT];
+      lds_swz<Real, VPT>(xr, c0, x);
+      const Real Fo = Fold[j];
+      Real sum = 0;
 #pragma unroll
-    for (int w = 0; w < NW; ++w) S += rb[w];
-    Real Fn;
-    if (S >= (Real)kTiny && S <= (Real)1e30) {
-      Fn = Fo + lu[i] - lg2(S);
+      for (int v = 0; v < VPT; ++v) {
+        wcur[v] = ex2(fma(-c, x[v], Gv[v] + Fo));
+        sum += wcur[v];
+      }
+      sum = warp_sum(sum);
+      if (lane == 0) red[(j & 1) * NW + warp] = sum;
+      if (j >= 1) {
+        // Column update of row j - 1 (its row sum was posted before the last barrier).
+        const Real* rb = red + ((j - 1) & 1) * NW;
+        Real S = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) S += rb[w];
+        const int ip = s + j - 1;
+        const Real lui = LU[j - 1];
+        if (S >= (Real)kTiny && S <= (Real)1e30) {
+          const Real r = (Real)u_or_exp(lui) / S;
+#pragma unroll
+          for (int v = 0; v < VPT; ++v) acc[v] = fma(r, wprev[v], acc[v]);
+          if (tid == 0) {
+            const Real Fn = Fo_prev + lui - lg2(S);
+            F[ip] = Fn;
+            Fband[j - 1] = Fn;
+          }
+        } else {
+          row_fallback(rr, j - 1, NT, status, c, x, Gv, Fo_prev, lui, acc, F, Fband, ip, sfb, lane, warp, tid);
+        }
+      }
+      Fo_prev = Fo;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) wprev[v] = wcur[v];
     } else {
-      // Underflow or overflow of the row sum: redo it with a max shift.
-      Real lm = -INFINITY;
+      // Last row's column update.
+      const Real* rb = red + ((j - 1) & 1) * NW;
+      Real S = 0;
 #pragma unroll
-      for (int v = 0; v < VPT; ++v) lm = fmax(lm, e[v]);
-      lm = warp_max(lm);
-      __syncthreads();
-      if (lane == 0) rb[warp] = lm;
-      __syncthreads();
-      Real M = -INFINITY;
+      for (int w = 0; w < NW; ++w) S += rb[w];
+      const int ip = s + j - 1;
+      const Real lui = LU[j - 1];
+      Real x[VPT];
 #pragma unroll
-      for (int w = 0; w < NW; ++w) M = fmax(M, rb[w]);
-      Real s2 = 0;
+      for (int v = 0; v < VPT; ++v) x[v] = 0;
+      if (S >= (Real)kTiny && S <= (Real)1e30) {
+        const Real r = (Real)u_or_exp(lui) / S;
 #pragma unroll
-      for (int v = 0; v < VPT; ++v) s2 += ex2(e[v] - M);
-      s2 = warp_sum(s2);
-      __syncthreads();
-      if (lane == 0) rb[warp] = s2;
-      __syncthreads();
-      Real S2 = 0;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) S2 += rb[w];
-      Fn = Fo + lu[i] - (M + lg2(S2));
-      __syncthreads();
+        for (int v = 0; v < VPT; ++v) acc[v] = fma(r, wprev[v], acc[v]);
+        if (tid == 0) {
+          const Real Fn = Fo_prev + lui - lg2(S);
+          F[ip] = Fn;
+          Fband[j - 1] = Fn;
+        }
+      } else {
+        row_fallback(rr, j - 1, NT, status, c, x, Gv, Fo_prev, lui, acc, F, Fband, ip, sfb, lane, warp, tid);
+      }
     }
-    if (tid == 0) {
-      F[i] = Fn;
-      Fband[t] = Fn;
-    }
-    // Column partial sums with the new F (every term <= u_i).
-#pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      const Real xp = fma(-c, x[v], Gv[v] + Fn);
-      acc[v] += ex2(xp);
-      mx[v] = fmax(mx[v], xp);
+    __syncthreads();
+    // Rows <= j - 1 are done with their slots: refill the slot of row j - 1.
+    if (geo.use_tma && tid == 0 && j >= 1 && (j - 1) + geo.stages < Ra) {
+      fence_proxy_async_smem();
+      rr.issue(j - 1 + geo.stages);
     }
   }
   __syncthreads();
@@ -224,9 +298,12 @@ __global__ void __launch_bounds__(32 * NW, 1)
       out.x = 0;
       out.y = acc[v];
     } else {
+      // Recompute this band's column sum with a max shift (rare).
+      Real mx = -INFINITY;
+      for (int t = 0; t < Ra; ++t) mx = fmax(mx, fma(-c, Pi[(size_t)(s + t) * m + p], Gv[v] + Fband[t]));
       Real s2 = 0;
-      for (int t = 0; t < Ra; ++t) s2 += ex2(fma(-c, Pi[(size_t)(s + t) * m + p], Gv[v] + Fband[t]) - mx[v]);
-      out.x = mx[v];
+      for (int t = 0; t < Ra; ++t) s2 += ex2(fma(-c, Pi[(size_t)(s + t) * m + p], Gv[v] + Fband[t]) - mx);
+      out.x = mx;
       out.y = s2;
     }
     part[(size_t)a * m + p] = out;
@@ -234,19 +311,66 @@ __global__ void __launch_bounds__(32 * NW, 1)
 }
 
 // Combines the band partials (M_b, S_b) of each column: sum_b S_b 2^(M_b - M).
+// A block covers 32 columns x 8 band groups: each thread reduces its group
+// with an online max and a compensated sum (almost every partial has M_b = 0,
+// so the common step is one add), the 8 groups are combined in FP64.
 template <typename Real>
-__global__ void sk_cols(const typename PartT<Real>::type* __restrict__ part, int B, int m,
-                        const Real* __restrict__ lv, Real* __restrict__ G) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= m) return;
-  Real M = -INFINITY;
-  for (int b = 0; b < B; ++b) M = fmax(M, part[(size_t)b * m + p].x);
-  double S = 0.0;
-  for (int b = 0; b < B; ++b) {
-    const auto q = part[(size_t)b * m + p];
-    S += (double)q.y * (double)ex2(q.x - M);
+__global__ void __launch_bounds__(256) sk_cols(const typename PartT<Real>::type* __restrict__ part, int B, int m,
+                                               const Real* __restrict__ lv, Real* __restrict__ G) {
+  __shared__ Real sM[8][32];
+  __shared__ double sS[8][32];
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + lane;
+  const int per = (B + 7) / 8;
+  const int b0 = min(B, grp * per), b1 = min(B, b0 + per);
+  Real M = -INFINITY, S = 0, C = 0;
+  if (p < m) {
+    int b = b0;
+    for (; b + 4 <= b1; b += 4) {
+      typename PartT<Real>::type q[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) q[r] = part[(size_t)(b + r) * m + p];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (q[r].x > M) {
+          const Real sc = (M == -INFINITY) ? (Real)0 : ex2(M - q[r].x);
+          S *= sc;
+          C *= sc;
+          M = q[r].x;
+        }
+        const Real t = (q[r].x == M) ? q[r].y : q[r].y * ex2(q[r].x - M);
+        const Real yk = t - C;
+        const Real tk = S + yk;
+        C = (tk - S) - yk;
+        S = tk;
+      }
+    }
+    for (; b < b1; ++b) {
+      const auto q = part[(size_t)b * m + p];
+      if (q.x > M) {
+        const Real sc = (M == -INFINITY) ? (Real)0 : ex2(M - q.x);
+        S *= sc;
+        C *= sc;
+        M = q.x;
+      }
+      const Real t = (q.x == M) ? q.y : q.y * ex2(q.x - M);
+      const Real yk = t - C;
+      const Real tk = S + yk;
+      C = (tk - S) - yk;
+      S = tk;
+    }
   }
-  G[p] = (Real)((double)G[p] + (double)lv[p] - ((double)M + log2(S)));
+  sM[grp][lane] = M;
+  sS[grp][lane] = (double)S - (double)C;
+  __syncthreads();
+  if (grp == 0 && p < m) {
+    Real Mt = -INFINITY;
+    for (int g = 0; g < 8; ++g) Mt = fmax(Mt, sM[g][lane]);
+    double St = 0.0;
+    for (int g = 0; g < 8; ++g)
+      if (sS[g][lane] > 0.0) St += sS[g][lane] * (double)ex2(sM[g][lane] - Mt);
+    G[p] = (Real)((double)G[p] + (double)lv[p] - ((double)Mt + log2(St)));
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -573,7 +697,7 @@ int solve1d_typed(const Solve1DArgs& A, void* wsv, size_t ws_bytes) {
       }
       {
         TraceScope ts(A.tracer, "sk_cols", st);
-        sk_cols<Real><<<(m + 255) / 256, 256, 0, st>>>(part, B, m, lv, G);
+        sk_cols<Real><<<(m + 31) / 32, 256, 0, st>>>(part, B, m, lv, G);
       }
     }
     {
