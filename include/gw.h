@@ -120,16 +120,21 @@ gw_status gw_ctx_profile_report(gw_ctx* ctx, char* buf, size_t len, int reset);
  * "2D kronecker").
  *
  *   prob       dim 1: any k >= 1 up to 3, nx, ny >= 1, ny <= 16384.
- *              dim 2 is not available through this call yet (GW_ERR_INVALID).
- *              Only dim, nx, ny, hx, hy, k, dtype are read.
+ *              dim 2: grid sides nx, ny in [1, 256] (n = nx^2, m = ny^2
+ *              points, index a * side + b), cost GW_COST_SQEUCLID, or
+ *              GW_COST_POW with k = 1 (Manhattan): the costs that split over
+ *              the two axes, so that D_X T D_Y reduces to four side x side
+ *              partial sums of T (k = 1 case of eq. "2D kronecker").
+ *              Only dim, nx, ny, hx, hy, k, cost, dtype are read.
  *   d_u, d_v   target marginals, double, lengths n and m; read only with
  *              marginals == GW_MARG_TARGET (may be NULL otherwise).
  *   d_T        the coupling, n x m row-major, prob->dtype.
  *   d_G        output, n x m row-major, prob->dtype; must not overlap d_T.
  *   marginals  GW_MARG_TARGET or GW_MARG_EXACT.
  *
- * Cost O(n m): the DP recursion along columns and rows replaces the dense
- * products.  With dtype GW_F32 the arithmetic is float with compensated band
+ * Cost O(n m): the DP recursion along columns and rows (1D), or one pass
+ * over T plus side x side transforms (2D), replaces the dense products.
+ * With dtype GW_F32 the arithmetic is float with compensated sums and
  * carries; GW_F64 computes in double throughout.
  * Errors: GW_ERR_INVALID for a bad descriptor or a NULL required pointer.
  */
@@ -148,7 +153,7 @@ gw_status gw_grad(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const 
  * of 32 MiB that every device loading the library reserves until exit; no
  * context is needed and nothing is allocated.
  *
- *   Arguments as for gw_grad, on the current CUDA device.  Problems whose
+ *   Arguments as for gw_grad (dim 1 only), on the current CUDA device.  Problems whose
  *   scratch need exceeds 32 MiB (about 4096 x 4096 floats with k <= 2) return
  *   GW_ERR_INVALID; so do invalid descriptors or NULL required pointers.
  *   The first call on each device looks up the array's device address (make
@@ -171,7 +176,8 @@ gw_status gw_grad_noalloc(const gw_problem* prob, const double* d_u, const doubl
  *              (tensor cores, FP32 accumulation; BF16 rounds T, D and the
  *              intermediate D_X T to bfloat16), GW_DENSE_FP64.
  *   prob->dtype must be GW_F64 for GW_DENSE_FP64 and GW_F32 otherwise; the
- *   other arguments are as for gw_grad (dim 1 only).  The dense distance
+ *   other arguments are as for gw_grad (dim 1 or 2; in 2D the distance
+ *   matrices are n x n and m x m over the grid points).  The dense distance
  *   matrices are cached in the context between calls.
  */
 gw_status gw_grad_dense(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const double* d_v,
@@ -188,7 +194,7 @@ gw_status gw_grad_dense(gw_ctx* ctx, const gw_problem* prob, const double* d_u, 
  * and runs prob->n_inner log-domain Sinkhorn iterations from f = g = 0
  * (f then g each iteration), then sets T_ip = exp((f_i + g_p - Pi_ip) / eps).
  *
- *   prob         dim 1; nx, ny, hx, hy, k as for gw_grad; eps > 0;
+ *   prob         dim 1 or 2; nx, ny, hx, hy, k, cost as for gw_grad; eps > 0;
  *                n_outer >= 0; n_inner >= 1; theta in [0, 1]; feat_dim in
  *                [1, 64] when theta < 1; dtype GW_F32 or GW_F64 (the
  *                arithmetic precision of the whole solve).

@@ -13,14 +13,23 @@
 
 namespace gw {
 
+// D[i][j] = d(i, j) for n points: 1D grid (side = 0): h^k |i - j|^k; 2D grid
+// of side x side points (i = a * side + b): Manhattan h (|a-a'| + |b-b'|)
+// (sq = 0) or squared Euclidean h^2 ((a-a')^2 + (b-b')^2) (sq = 1).
 template <typename Out>
-__global__ void build_dist(Out* __restrict__ D, int n, double hk, int k) {
+__global__ void build_dist(Out* __restrict__ D, int n, double hk, int k, int side, int sq) {
   const size_t N = (size_t)n * n;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
     const long long i = (long long)(idx / n), j = (long long)(idx % n);
-    double d = (double)(i > j ? i - j : j - i);
-    double v = 1.0;
-    for (int e = 0; e < k; ++e) v *= d;
+    double v;
+    if (side > 0) {
+      const double da = (double)llabs(i / side - j / side), db = (double)llabs(i % side - j % side);
+      v = sq ? da * da + db * db : da + db;
+    } else {
+      const double d = (double)(i > j ? i - j : j - i);
+      v = 1.0;
+      for (int e = 0; e < k; ++e) v *= d;
+    }
     D[idx] = (Out)(hk * v);
   }
 }
@@ -38,6 +47,34 @@ __global__ void dense_epilogue(Real* __restrict__ G, int n, int m, const Real* _
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
     const size_t i = idx / m, p = idx % m;
     G[idx] = fma(-s, G[idx], cx[i] + cy[p]);
+  }
+}
+
+// Constant term on a 2D grid, pointwise: c[i] = scale * sum_j d(i,j)^2 w_j
+// with d the Manhattan or squared Euclidean grid distance (one block per i).
+template <typename Real>
+__global__ void dist2_const_2d(const double* __restrict__ w, int side, int sq, double scale, Real* __restrict__ out) {
+  const int n = side * side;
+  const int i = blockIdx.x;
+  const int a = i / side, b = i % side;
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double da = (double)abs(a - j / side), db = (double)abs(b - j % side);
+    const double d = sq ? da * da + db * db : da + db;
+    acc += d * d * w[j];
+  }
+  __shared__ double sm[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sm[k];
+    t *= scale;
+    // hi part, then the rounding remainder (read by the epilogue as cx + cy).
+    out[i] = (Real)t;
+    out[n + i] = (Real)(t - (double)(Real)t);
   }
 }
 
@@ -62,7 +99,7 @@ __global__ void col_sums(const Real* __restrict__ T, int n, int m, double* __res
 }
 
 struct DenseCache {
-  int n = 0, k = 0, prec = -1;
+  int n = 0, k = 0, prec = -1, side = 0, sq = 0;
   double h = 0;
   void* D = nullptr;
 };
@@ -72,8 +109,8 @@ struct DenseState {
   DenseCache X, Y;
 };
 
-static int ensure_dist(DenseCache& c, int n, double h, int k, int prec, cudaStream_t st) {
-  if (c.D && c.n == n && c.h == h && c.k == k && c.prec == prec) return GW_OK;
+static int ensure_dist(DenseCache& c, int n, double h, int k, int side, int sq, int prec, cudaStream_t st) {
+  if (c.D && c.n == n && c.h == h && c.k == k && c.side == side && c.sq == sq && c.prec == prec) return GW_OK;
   if (c.D) {
     cudaStreamSynchronize(st);
     cudaFree(c.D);
@@ -85,16 +122,18 @@ static int ensure_dist(DenseCache& c, int n, double h, int k, int prec, cudaStre
     c.D = nullptr;
     return GW_ERR_OOM;
   }
-  const double hk = std::pow(h, k);
+  const double hk = side > 0 ? (sq ? h * h : h) : std::pow(h, k);
   if (prec == GW_DENSE_BF16)
-    build_dist<__nv_bfloat16><<<1024, 256, 0, st>>>((__nv_bfloat16*)c.D, n, hk, k);
+    build_dist<__nv_bfloat16><<<1024, 256, 0, st>>>((__nv_bfloat16*)c.D, n, hk, k, side, sq);
   else if (prec == GW_DENSE_FP64)
-    build_dist<double><<<1024, 256, 0, st>>>((double*)c.D, n, hk, k);
+    build_dist<double><<<1024, 256, 0, st>>>((double*)c.D, n, hk, k, side, sq);
   else
-    build_dist<float><<<1024, 256, 0, st>>>((float*)c.D, n, hk, k);
+    build_dist<float><<<1024, 256, 0, st>>>((float*)c.D, n, hk, k, side, sq);
   c.n = n;
   c.h = h;
   c.k = k;
+  c.side = side;
+  c.sq = sq;
   c.prec = prec;
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }
@@ -128,9 +167,10 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
   }
   cublasSetStream(S->handle, st);
   const int n = a.n, m = a.m;
-  int rc = ensure_dist(S->X, n, a.hx, a.k, a.prec, st);
+  const int sq = a.dim == 2 && a.cost == GW_COST_SQEUCLID;
+  int rc = ensure_dist(S->X, n, a.hx, a.k, a.dim == 2 ? a.sx : 0, sq, a.prec, st);
   if (rc != GW_OK) return rc;
-  rc = ensure_dist(S->Y, m, a.hy, a.k, a.prec, st);
+  rc = ensure_dist(S->Y, m, a.hy, a.k, a.dim == 2 ? a.sy : 0, sq, a.prec, st);
   if (rc != GW_OK) return rc;
   char* ws = (char*)wsv;
   size_t off = 0;
@@ -171,9 +211,21 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
     wx = r;
     wy = cc;
   }
-  rc = marg_const2_launch(wx, n, std::pow(a.hx, 2 * a.k), cx, wy, m, std::pow(a.hy, 2 * a.k), cy, a.k,
-                          dbl ? GW_F64 : GW_F32, part, st, a.tracer);
-  if (rc != GW_OK) return rc;
+  if (a.dim == 2) {
+    TraceScope ts(a.tracer, "dense_const", st);
+    const double fx = sq ? a.hx * a.hx : a.hx, fy = sq ? a.hy * a.hy : a.hy;
+    if (dbl) {
+      dist2_const_2d<double><<<n, 256, 0, st>>>(wx, a.sx, sq, fx * fx, (double*)cx);
+      dist2_const_2d<double><<<m, 256, 0, st>>>(wy, a.sy, sq, fy * fy, (double*)cy);
+    } else {
+      dist2_const_2d<float><<<n, 256, 0, st>>>(wx, a.sx, sq, fx * fx, (float*)cx);
+      dist2_const_2d<float><<<m, 256, 0, st>>>(wy, a.sy, sq, fy * fy, (float*)cy);
+    }
+  } else {
+    rc = marg_const2_launch(wx, n, std::pow(a.hx, 2 * a.k), cx, wy, m, std::pow(a.hy, 2 * a.k), cy, a.k,
+                            dbl ? GW_F64 : GW_F32, part, st, a.tracer);
+    if (rc != GW_OK) return rc;
+  }
 
   // Row-major n x m arrays are column-major m x n.  Y^T = T^T D_X and
   // Z^T = D_Y Y^T in column-major terms.

@@ -227,7 +227,10 @@ bool encode_rows_tmap(void* tmap, const void* base, int n, int m, int elem_bytes
   if (!fn) return false;
   const int E = 128 / elem_bytes;
   if (m % E != 0 || n < 1) return false;
-  const int bc = std::min(256, m / E);
+  // Box height: the largest divisor of m / E that is at most 256, so that a
+  // row is a whole number of boxes with no out-of-range fill.
+  int bc = std::min(256, m / E);
+  while ((m / E) % bc != 0) --bc;
   cuuint64_t dims[3] = {(cuuint64_t)E, (cuuint64_t)(m / E), (cuuint64_t)n};
   cuuint64_t strides[2] = {128, (cuuint64_t)m * (cuuint64_t)elem_bytes};
   cuuint32_t box[3] = {(cuuint32_t)E, (cuuint32_t)bc, 1};

@@ -135,8 +135,23 @@ gw_status check_grid(gw_ctx* c, const gw_problem* p) {
   if (!finite_pos(p->hx) || !finite_pos(p->hy)) return fail(c, GW_ERR_INVALID, "grid spacings must be finite and > 0");
   if (p->k < 1) return fail(c, GW_ERR_INVALID, "distance exponent k must be >= 1 (got %d)", p->k);
   if (p->dtype != GW_F32 && p->dtype != GW_F64) return fail(c, GW_ERR_INVALID, "dtype must be GW_F32 or GW_F64");
+  if (p->dim == 1) {
+    if (p->k > 3) return fail(c, GW_ERR_INVALID, "k must be <= 3 (got %d)", p->k);
+    if (p->ny > 16384) return fail(c, GW_ERR_INVALID, "ny must be <= 16384 (got %d)", p->ny);
+  } else {
+    if (p->cost != GW_COST_POW && p->cost != GW_COST_SQEUCLID)
+      return fail(c, GW_ERR_INVALID, "2D cost must be GW_COST_POW or GW_COST_SQEUCLID (got %d)", p->cost);
+    if (p->cost == GW_COST_POW && p->k != 1)
+      return fail(c, GW_ERR_INVALID, "2D Manhattan cost is available for k = 1 only (got %d)", p->k);
+    if (p->nx > gw::kMax2DSide || p->ny > gw::kMax2DSide)
+      return fail(c, GW_ERR_INVALID, "2D grid sides must be <= %d (got %d, %d)", gw::kMax2DSide, p->nx, p->ny);
+  }
   return GW_OK;
 }
+
+// Points of each space: nx, ny in 1D, nx^2, ny^2 on 2D grids.
+size_t points_x(const gw_problem* p) { return p->dim == 2 ? (size_t)p->nx * p->nx : (size_t)p->nx; }
+size_t points_y(const gw_problem* p) { return p->dim == 2 ? (size_t)p->ny * p->ny : (size_t)p->ny; }
 
 }  // namespace
 
@@ -240,20 +255,46 @@ gw_status gw_grad(gw_ctx* c, const gw_problem* p, const double* d_u, const doubl
   std::lock_guard<std::mutex> lk(c->mu);
   gw_status s = check_grid(c, p);
   if (s != GW_OK) return s;
-  if (p->dim != 1) return fail(c, GW_ERR_INVALID, "gw_grad: 2D grids are not available in this call");
-  if (p->k > 3) return fail(c, GW_ERR_INVALID, "gw_grad: k must be <= 3 (got %d)", p->k);
-  if (p->ny > 16384) return fail(c, GW_ERR_INVALID, "gw_grad: ny must be <= 16384 (got %d)", p->ny);
   if (marginals != GW_MARG_TARGET && marginals != GW_MARG_EXACT)
     return fail(c, GW_ERR_INVALID, "marginals must be GW_MARG_TARGET or GW_MARG_EXACT");
   if (!d_T || !d_G) return fail(c, GW_ERR_INVALID, "d_T and d_G must not be NULL");
   if (marginals == GW_MARG_TARGET && (!d_u || !d_v))
     return fail(c, GW_ERR_INVALID, "target marginals requested but d_u or d_v is NULL");
   const size_t esz = p->dtype == GW_F32 ? 4 : 8;
-  const size_t nm = (size_t)p->nx * (size_t)p->ny;
+  const size_t nm = points_x(p) * points_y(p);
   const char* t0 = (const char*)d_T;
   const char* g0 = (const char*)d_G;
   if (t0 < g0 + nm * esz && g0 < t0 + nm * esz) return fail(c, GW_ERR_INVALID, "d_T and d_G overlap");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
+
+  if (p->dim == 2) {
+    gw::Grad2DArgs a{};
+    a.sx = p->nx;
+    a.sy = p->ny;
+    a.cost = p->cost;
+    a.hx = p->hx;
+    a.hy = p->hy;
+    a.dtype = p->dtype;
+    a.T = d_T;
+    a.G = d_G;
+    a.u = d_u;
+    a.v = d_v;
+    a.exact = marginals == GW_MARG_EXACT;
+    a.out_scale = 1.0;
+    a.stream = (cudaStream_t)stream;
+    a.status = c->status;
+    a.num_sms = c->num_sms;
+    a.tracer = c->tr();
+    s = ensure_ws(c, gw::grad2d_workspace_bytes(a.sx, a.sy, a.dtype));
+    if (s != GW_OK) return s;
+    int rc = gw::grad2d_launch(a, c->ws, c->ws_bytes);
+    if (rc != GW_OK) {
+      cudaError_t e = cudaGetLastError();
+      return fail(c, (gw_status)rc, "gw_grad (2D) launch failed: %s", cudaGetErrorString(e));
+    }
+    c->err.clear();
+    return GW_OK;
+  }
 
   gw::Grad1DArgs a{};
   a.n = p->nx;
@@ -290,7 +331,6 @@ gw_status gw_grad_dense(gw_ctx* c, const gw_problem* p, const double* d_u, const
   std::lock_guard<std::mutex> lk(c->mu);
   gw_status s = check_grid(c, p);
   if (s != GW_OK) return s;
-  if (p->dim != 1) return fail(c, GW_ERR_INVALID, "gw_grad_dense: dim must be 1");
   if (precision < GW_DENSE_FP32 || precision > GW_DENSE_FP64)
     return fail(c, GW_ERR_INVALID, "gw_grad_dense: unknown precision %d", precision);
   if ((precision == GW_DENSE_FP64) != (p->dtype == GW_F64))
@@ -301,15 +341,19 @@ gw_status gw_grad_dense(gw_ctx* c, const gw_problem* p, const double* d_u, const
   if (marginals == GW_MARG_TARGET && (!d_u || !d_v))
     return fail(c, GW_ERR_INVALID, "target marginals requested but d_u or d_v is NULL");
   const size_t esz = p->dtype == GW_F32 ? 4 : 8;
-  const size_t nm = (size_t)p->nx * (size_t)p->ny;
+  const size_t nm = points_x(p) * points_y(p);
   const char* t0 = (const char*)d_T;
   const char* g0 = (const char*)d_G;
   if (t0 < g0 + nm * esz && g0 < t0 + nm * esz) return fail(c, GW_ERR_INVALID, "d_T and d_G overlap");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
   if (!c->dense) c->dense = gw::dense_state_create();
   gw::DenseArgs a{};
-  a.n = p->nx;
-  a.m = p->ny;
+  a.dim = p->dim;
+  a.cost = p->cost;
+  a.sx = p->nx;
+  a.sy = p->ny;
+  a.n = (int)points_x(p);
+  a.m = (int)points_y(p);
   a.k = p->k;
   a.prec = precision;
   a.exact = marginals == GW_MARG_EXACT;
@@ -338,9 +382,6 @@ gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const doub
   std::lock_guard<std::mutex> lk(c->mu);
   gw_status s = check_grid(c, p);
   if (s != GW_OK) return s;
-  if (p->dim != 1) return fail(c, GW_ERR_INVALID, "gw_solve: 2D grids are not available in this call");
-  if (p->k > 3) return fail(c, GW_ERR_INVALID, "gw_solve: k must be <= 3 (got %d)", p->k);
-  if (p->ny > 16384) return fail(c, GW_ERR_INVALID, "gw_solve: ny must be <= 16384 (got %d)", p->ny);
   if (!finite_pos(p->eps)) return fail(c, GW_ERR_INVALID, "gw_solve: eps must be finite and > 0");
   if (p->n_outer < 0 || p->n_inner < 1)
     return fail(c, GW_ERR_INVALID, "gw_solve: need n_outer >= 0 and n_inner >= 1");
@@ -349,9 +390,13 @@ gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const doub
     return fail(c, GW_ERR_INVALID, "gw_solve: fused GW (theta < 1) needs 1 <= feat_dim <= 64 and both feature arrays");
   if (!d_u || !d_v || !d_T) return fail(c, GW_ERR_INVALID, "gw_solve: d_u, d_v and d_T must not be NULL");
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
-  gw::Solve1DArgs a{};
-  a.n = p->nx;
-  a.m = p->ny;
+  gw::SolveArgs a{};
+  a.dim = p->dim;
+  a.cost = p->cost;
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.n = (int)points_x(p);
+  a.m = (int)points_y(p);
   a.k = p->k;
   a.dtype = p->dtype;
   a.hx = p->hx;
@@ -374,18 +419,18 @@ gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const doub
   a.num_sms = c->num_sms;
   a.tracer = c->tr();
   a.force_generic = c->force_generic;
-  s = ensure_ws(c, gw::solve1d_workspace_bytes(a.n, a.m, a.k, a.dtype, a.num_sms));
+  s = ensure_ws(c, gw::solve_workspace_bytes(a));
   if (s != GW_OK) return s;
   int rc;
   if (c->tracer) {
     // Per-kernel timing wants eager launches.
-    rc = gw::solve1d_launch(a, c->ws, c->ws_bytes);
+    rc = gw::solve_launch(a, c->ws, c->ws_bytes);
   } else {
     // The whole solve (thousands of short launches) as one CUDA graph,
     // captured on a side stream and relaunched while the arguments match.
     char key[512];
-    snprintf(key, sizeof key, "%d %d %d %d %.17g %.17g %.17g %.17g %d %d %d %p %p %p %p %p %p %p %p %p %zu",
-             a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.theta, a.n_outer, a.n_inner, a.feat_dim, (void*)a.u,
+    snprintf(key, sizeof key, "%d %d %d %d %d %d %.17g %.17g %.17g %.17g %d %d %d %p %p %p %p %p %p %p %p %p %zu",
+             a.dim, a.cost, a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.theta, a.n_outer, a.n_inner, a.feat_dim, (void*)a.u,
              (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.f, (void*)a.g, (void*)a.stats, c->ws, c->ws_bytes);
     if (!c->solve_exec || c->solve_key != key) {
       if (c->solve_exec) {
@@ -394,12 +439,12 @@ gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const doub
       }
       if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
         return cuda_fail(c, cudaGetLastError(), "capture stream");
-      gw::Solve1DArgs ac = a;
+      gw::SolveArgs ac = a;
       ac.stream = c->cap;
       cudaGraph_t graph = nullptr;
       cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
-      rc = gw::solve1d_launch(ac, c->ws, c->ws_bytes);
+      rc = gw::solve_launch(ac, c->ws, c->ws_bytes);
       e = cudaStreamEndCapture(c->cap, &graph);
       if (rc != GW_OK || e != cudaSuccess) {
         if (graph) cudaGraphDestroy(graph);

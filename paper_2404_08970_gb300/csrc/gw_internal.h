@@ -76,8 +76,9 @@ struct Grad1DArgs {
 
 // Encodes a TMA tensor map over the rows of an n x m row-major array of
 // elem_bytes-sized reals, viewed as [n][m / E][E] with E*elem_bytes = 128,
-// 128-byte swizzle, box {E, box_cols, 1}.  False if m is not a multiple of E
-// or the driver rejects the map.
+// 128-byte swizzle, box {E, box_cols, 1}, box_cols the largest divisor of
+// m / E up to 256.  False if m is not a multiple of E or the driver rejects
+// the map.
 bool encode_rows_tmap(void* tmap, const void* base, int n, int m, int elem_bytes, int* box_cols);
 
 // Bytes of workspace the structured 1D gradient needs.
@@ -101,8 +102,31 @@ int marg_const_launch(const double* w, int len, int k, double h, void* out, int 
 int marg_const2_launch(const double* wx, int n, double fx, void* outx, const double* wy, int m, double fy,
                        void* outy, int k, int dtype, double* part, cudaStream_t stream, Tracer* tracer);
 
+// Structured gradient on side x side grids with an axis-separable cost
+// (grad2d.cu): Manhattan with k = 1, or squared Euclidean.
+constexpr int kMax2DSide = 256;
+struct Grad2DArgs {
+  int sx, sy;           // grid sides; n = sx^2 points of X, m = sy^2 points of Y
+  int cost;             // GW_COST_POW (k = 1) or GW_COST_SQEUCLID
+  double hx, hy;
+  int dtype;
+  const void* T;        // n x m row-major, dtype
+  void* G;              // n x m row-major, dtype
+  const double* u;      // target marginals (n and m) or nullptr with exact
+  const double* v;
+  int exact;
+  double out_scale;
+  cudaStream_t stream;
+  unsigned* status;
+  int num_sms;
+  Tracer* tracer;
+};
+size_t grad2d_workspace_bytes(int sx, int sy, int dtype);
+int grad2d_launch(const Grad2DArgs& a, void* ws, size_t ws_bytes);
+
 // Dense comparison gradient through cuBLAS (dense.cu).
 struct DenseArgs {
+  int dim, cost, sx, sy;  // dim 2: sx, sy grid sides, n = sx^2, m = sy^2
   int n, m, k, prec, exact;
   double hx, hy;
   const double *u, *v;
@@ -116,8 +140,11 @@ void dense_state_destroy(void* state);
 size_t dense_workspace_bytes(int n, int m, int prec);
 int dense_grad_launch(void* state, const DenseArgs& a, void* ws, size_t ws_bytes);
 
-// Entropic (fused) GW by mirror descent on 1D grids (sinkhorn.cu).
-struct Solve1DArgs {
+// Entropic (fused) GW by mirror descent (sinkhorn.cu).  dim 1: n = nx and
+// m = ny points; dim 2: nx, ny are grid sides (n = nx^2, m = ny^2).
+struct SolveArgs {
+  int dim, cost;
+  int nx, ny;
   int n, m, k, dtype;
   double hx, hy, eps, theta;
   int n_outer, n_inner, feat_dim;
@@ -131,7 +158,7 @@ struct Solve1DArgs {
   int force_generic;
 };
 
-size_t solve1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms);
-int solve1d_launch(const Solve1DArgs& a, void* ws, size_t ws_bytes);
+size_t solve_workspace_bytes(const SolveArgs& a);
+int solve_launch(const SolveArgs& a, void* ws, size_t ws_bytes);
 
 }  // namespace gw

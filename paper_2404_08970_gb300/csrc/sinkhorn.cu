@@ -16,9 +16,10 @@
 //            F as reference; after a column update every term is <= v_p), the
 //            new F_i = F_i + log2 u_i - log2 S_i; then, per column, the band's
 //            partial sum of 2^(F_i + G_p - c Pi_ip) with the new F (every term
-//            <= u_i).  A column whose band sum underflows is recomputed for
-//            that band with a max shift.
-//   sk_cols  per column: combines the band partials (FP64) into the new G_p.
+//            <= u_i).
+//   sk_cols  per column: sums the band partials (FP64 combine) into the new
+//            G_p.  A column whose total underflows (a cold start far from the
+//            fixed point) is recomputed over all rows with a running max.
 #include <cuda.h>
 
 #include <algorithm>
@@ -56,15 +57,33 @@ __device__ __forceinline__ Real warp_max(Real x) {
   return x;
 }
 
-// Below this a band's column sum is treated as underflowed and recomputed
-// with a max shift.
-constexpr float kTiny = 1e-30f;
+// Pairwise sums (short dependency chains; a fixed order, so results do not
+// depend on scheduling).
+template <int N, typename Real>
+__device__ __forceinline__ Real tree_sum(const Real (&x)[N]) {
+  Real t[N];
+#pragma unroll
+  for (int v = 0; v < N; ++v) t[v] = x[v];
+#pragma unroll
+  for (int w = 1; w < N; w *= 2)
+#pragma unroll
+    for (int v = 0; v + w < N; v += 2 * w) t[v] += t[v + w];
+  return t[0];
+}
+template <int N, typename Real>
+__device__ __forceinline__ Real tree_sum_smem(const Real* p) {
+  Real t[N];
+#pragma unroll
+  for (int v = 0; v < N; ++v) t[v] = p[v];
+  return tree_sum<N>(t);
+}
 
-// A band's column partial (M, S): the band's sum is S * 2^M relative to the
-// column's current potential.
-template <typename Real> struct PartT;
-template <> struct PartT<float> { using type = float2; };
-template <> struct PartT<double> { using type = double2; };
+// A row or column sum below this is redone with a max shift.  In FP32 the
+// exp2 results below 2^-126 are flushed, so a sum of up to 2^20 terms above
+// 1e-24 is short by at most 2^20 * 2^-126 / 1e-24 ~ 1e-8 of itself.
+template <typename Real> __device__ __forceinline__ Real tiny_sum();
+template <> __device__ __forceinline__ float tiny_sum<float>() { return 1e-24f; }
+template <> __device__ __forceinline__ double tiny_sum<double>() { return 1e-250; }
 
 // ---------------------------------------------------------------------------
 // Shared-memory layout of the row-streaming kernels (1024-aligned base):
@@ -90,10 +109,12 @@ struct RowRing {
   const Real* src;
   int m, s, Ra;
 
-  __device__ void issue(int tl) {  // row s + tl into slot tl % stages
+  __device__ void issue(int tl) {  // row s + tl into slot tl % stages, in boxes of box_cols 128-byte lines
     const int slot = tl % stages;
+    const int lines = (int)(m * sizeof(Real) / 128);
     mbar_arrive_expect_tx(&bars[slot], (unsigned)(m * sizeof(Real)));
-    tma_load_3d(ring + (size_t)slot * slot_bytes, tm, 0, 0, s + tl, &bars[slot]);
+    for (int y = 0; y < lines; y += box_cols)
+      tma_load_3d(ring + (size_t)slot * slot_bytes + (size_t)y * 128, tm, 0, y, s + tl, &bars[slot]);
   }
   // Returns the slot holding row tl; all NT threads call it.
   __device__ const unsigned char* get(int tl, int NT, unsigned* status) {
@@ -162,8 +183,8 @@ __device__ __forceinline__ void row_fallback(RowRing<Real>& rr, int tl, int NT, 
 template <int NW, int VPT, typename Real>
 __global__ void __launch_bounds__(32 * NW, 1)
     sk_pass(const __grid_constant__ CUtensorMap tmP, const Real* __restrict__ Pi, int n, int m, int R, Real c,
-            const Real* __restrict__ lu, Real* __restrict__ F, const Real* __restrict__ Gp,
-            typename PartT<Real>::type* __restrict__ part, RowGeom geo, unsigned* status) {
+            const Real* __restrict__ lu, Real* __restrict__ F, const Real* __restrict__ Gp, Real* __restrict__ part,
+            RowGeom geo, unsigned* status) {
   constexpr int NT = 32 * NW;
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   unsigned char* sm = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
@@ -224,23 +245,17 @@ __global__ void __launch_bounds__(32 * NW, 1)
       Real x[VPT];
       lds_swz<Real, VPT>(xr, c0, x);
       const Real Fo = Fold[j];
-      Real sum = 0;
 #pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        wcur[v] = ex2(fma(-c, x[v], Gv[v] + Fo));
-        sum += wcur[v];
-      }
+      for (int v = 0; v < VPT; ++v) wcur[v] = ex2(fma(-c, x[v], Gv[v] + Fo));
+      Real sum = tree_sum<VPT>(wcur);
       sum = warp_sum(sum);
       if (lane == 0) red[(j & 1) * NW + warp] = sum;
       if (j >= 1) {
         // Column update of row j - 1 (its row sum was posted before the last barrier).
-        const Real* rb = red + ((j - 1) & 1) * NW;
-        Real S = 0;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) S += rb[w];
+        const Real S = tree_sum_smem<NW>(red + ((j - 1) & 1) * NW);
         const int ip = s + j - 1;
         const Real lui = LU[j - 1];
-        if (S >= (Real)kTiny && S <= (Real)1e30) {
+        if (S >= tiny_sum<Real>() && S <= (Real)1e30) {
           const Real r = (Real)u_or_exp(lui) / S;
 #pragma unroll
           for (int v = 0; v < VPT; ++v) acc[v] = fma(r, wprev[v], acc[v]);
@@ -258,16 +273,13 @@ __global__ void __launch_bounds__(32 * NW, 1)
       for (int v = 0; v < VPT; ++v) wprev[v] = wcur[v];
     } else {
       // Last row's column update.
-      const Real* rb = red + ((j - 1) & 1) * NW;
-      Real S = 0;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) S += rb[w];
+      const Real S = tree_sum_smem<NW>(red + ((j - 1) & 1) * NW);
       const int ip = s + j - 1;
       const Real lui = LU[j - 1];
       Real x[VPT];
 #pragma unroll
       for (int v = 0; v < VPT; ++v) x[v] = 0;
-      if (S >= (Real)kTiny && S <= (Real)1e30) {
+      if (S >= tiny_sum<Real>() && S <= (Real)1e30) {
         const Real r = (Real)u_or_exp(lui) / S;
 #pragma unroll
         for (int v = 0; v < VPT; ++v) acc[v] = fma(r, wprev[v], acc[v]);
@@ -287,89 +299,82 @@ __global__ void __launch_bounds__(32 * NW, 1)
       rr.issue(j - 1 + geo.stages);
     }
   }
-  __syncthreads();
-  // Write the band partials; recompute underflowed columns with a max shift.
+  // Band partials of the column sums (relative to the current G).
 #pragma unroll
-  for (int v = 0; v < VPT; ++v) {
-    const int p = c0 + v;
-    if (p >= m) continue;
-    typename PartT<Real>::type out;
-    if (acc[v] >= (Real)kTiny) {
-      out.x = 0;
-      out.y = acc[v];
-    } else {
-      // Recompute this band's column sum with a max shift (rare).
-      Real mx = -INFINITY;
-      for (int t = 0; t < Ra; ++t) mx = fmax(mx, fma(-c, Pi[(size_t)(s + t) * m + p], Gv[v] + Fband[t]));
-      Real s2 = 0;
-      for (int t = 0; t < Ra; ++t) s2 += ex2(fma(-c, Pi[(size_t)(s + t) * m + p], Gv[v] + Fband[t]) - mx);
-      out.x = mx;
-      out.y = s2;
-    }
-    part[(size_t)a * m + p] = out;
-  }
+  for (int v = 0; v < VPT; ++v)
+    if (c0 + v < m) part[(size_t)a * m + c0 + v] = acc[v];
 }
 
-// Combines the band partials (M_b, S_b) of each column: sum_b S_b 2^(M_b - M).
-// A block covers 32 columns x 8 band groups: each thread reduces its group
-// with an online max and a compensated sum (almost every partial has M_b = 0,
-// so the common step is one add), the 8 groups are combined in FP64.
+// Per column: S_p = sum_b part_bp (FP32 compensated sums over 8 band groups,
+// combined in FP64) and G_p += log2 v_p - log2 S_p.  A block covers 32
+// columns.  If any of them has S_p out of range, the block recomputes its 32
+// columns from Pi and the new F with a running max (8 warps over the rows,
+// one lane per column).
 template <typename Real>
-__global__ void __launch_bounds__(256) sk_cols(const typename PartT<Real>::type* __restrict__ part, int B, int m,
-                                               const Real* __restrict__ lv, Real* __restrict__ G) {
-  __shared__ Real sM[8][32];
+__global__ void __launch_bounds__(256) sk_cols(const Real* __restrict__ part, int B, int n, int m,
+                                               const Real* __restrict__ lv, Real* __restrict__ G,
+                                               const Real* __restrict__ Pi, const Real* __restrict__ F, Real c) {
   __shared__ double sS[8][32];
+  __shared__ Real sM[8][32];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
   const int p = blockIdx.x * 32 + lane;
   const int per = (B + 7) / 8;
   const int b0 = min(B, grp * per), b1 = min(B, b0 + per);
-  Real M = -INFINITY, S = 0, C = 0;
+  Real S = 0, C = 0;
   if (p < m) {
-    int b = b0;
-    for (; b + 4 <= b1; b += 4) {
-      typename PartT<Real>::type q[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) q[r] = part[(size_t)(b + r) * m + p];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        if (q[r].x > M) {
-          const Real sc = (M == -INFINITY) ? (Real)0 : ex2(M - q[r].x);
-          S *= sc;
-          C *= sc;
-          M = q[r].x;
-        }
-        const Real t = (q[r].x == M) ? q[r].y : q[r].y * ex2(q[r].x - M);
-        const Real yk = t - C;
-        const Real tk = S + yk;
-        C = (tk - S) - yk;
-        S = tk;
-      }
-    }
-    for (; b < b1; ++b) {
-      const auto q = part[(size_t)b * m + p];
-      if (q.x > M) {
-        const Real sc = (M == -INFINITY) ? (Real)0 : ex2(M - q.x);
-        S *= sc;
-        C *= sc;
-        M = q.x;
-      }
-      const Real t = (q.x == M) ? q.y : q.y * ex2(q.x - M);
-      const Real yk = t - C;
+    for (int b = b0; b < b1; ++b) {
+      const Real yk = part[(size_t)b * m + p] - C;
       const Real tk = S + yk;
       C = (tk - S) - yk;
       S = tk;
     }
   }
-  sM[grp][lane] = M;
   sS[grp][lane] = (double)S - (double)C;
+  __syncthreads();
+  double St = 0.0;
+  for (int g = 0; g < 8; ++g) St += sS[g][lane];
+  const bool bad = p < m && !(St >= (double)tiny_sum<Real>() && St <= 1e30);
+  if (!__syncthreads_or(bad)) {
+    if (grp == 0 && p < m) G[p] = (Real)((double)G[p] + (double)lv[p] - log2(St));
+    return;
+  }
+  // Recompute: log2 sum_i 2^(F_i + G_p - c Pi_ip) with a running max.
+  const Real Gp = p < m ? G[p] : (Real)0;
+  Real M = -INFINITY;
+  S = 0;
+  if (p < m) {
+    constexpr int U = 8;
+    int i = grp;
+    for (; i + 8 * (U - 1) < n; i += 8 * U) {
+      Real e[U];
+#pragma unroll
+      for (int r = 0; r < U; ++r) e[r] = fma(-c, Pi[(size_t)(i + 8 * r) * m + p], Gp + F[i + 8 * r]);
+      Real mx = M;
+#pragma unroll
+      for (int r = 0; r < U; ++r) mx = fmax(mx, e[r]);
+      S = (M == -INFINITY) ? (Real)0 : S * ex2(M - mx);
+#pragma unroll
+      for (int r = 0; r < U; ++r) S += ex2(e[r] - mx);
+      M = mx;
+    }
+    for (; i < n; i += 8) {
+      const Real e = fma(-c, Pi[(size_t)i * m + p], Gp + F[i]);
+      const Real mx = fmax(M, e);
+      S = ((M == -INFINITY) ? (Real)0 : S * ex2(M - mx)) + ex2(e - mx);
+      M = mx;
+    }
+  }
+  __syncthreads();
+  sM[grp][lane] = M;
+  sS[grp][lane] = (double)S;
   __syncthreads();
   if (grp == 0 && p < m) {
     Real Mt = -INFINITY;
     for (int g = 0; g < 8; ++g) Mt = fmax(Mt, sM[g][lane]);
-    double St = 0.0;
+    double St2 = 0.0;
     for (int g = 0; g < 8; ++g)
-      if (sS[g][lane] > 0.0) St += sS[g][lane] * (double)ex2(sM[g][lane] - Mt);
-    G[p] = (Real)((double)G[p] + (double)lv[p] - ((double)Mt + log2(St)));
+      if (sS[g][lane] > 0.0) St2 += sS[g][lane] * exp2((double)(sM[g][lane] - Mt));
+    G[p] = (Real)((double)Gp + (double)lv[p] - ((double)Mt + log2(St2)));
   }
 }
 
@@ -606,14 +611,14 @@ RowGeom row_geom(const void* Pi, int n, int m, CUtensorMap* tm, int Rmax) {
   g.slot_bytes = g.vec_bytes;
   memset(tm, 0, sizeof(*tm));
   g.use_tma = ((((uintptr_t)Pi) & 15) == 0) && encode_rows_tmap(tm, Pi, n, m, sizeof(Real), &g.box_cols) &&
-              (m * (int)sizeof(Real)) <= 256 * 128;
+              g.box_cols >= 8;
   const size_t fixed = 1024 + g.vec_bytes + sizeof(Real) * (2 * NW + Rmax) + 128;
   g.stages = g.use_tma ? (int)std::max<size_t>(2, std::min<size_t>(4, (200 * 1024 - fixed) / g.slot_bytes)) : 2;
   return g;
 }
 
 template <int NW, int VPT, typename Real>
-int solve1d_typed(const Solve1DArgs& A, void* wsv, size_t ws_bytes) {
+int solve_typed(const SolveArgs& A, void* wsv, size_t ws_bytes) {
   const int n = A.n, m = A.m;
   cudaStream_t st = A.stream;
   const Bands bands = choose_bands(n, A.num_sms);
@@ -631,8 +636,7 @@ int solve1d_typed(const Solve1DArgs& A, void* wsv, size_t ws_bytes) {
   Real* G = (Real*)take((size_t)m * sizeof(Real));
   Real* lu = (Real*)take((size_t)n * sizeof(Real));
   Real* lv = (Real*)take((size_t)m * sizeof(Real));
-  using Part = typename PartT<Real>::type;
-  Part* part = (Part*)take((size_t)B * m * sizeof(Part));
+  Real* part = (Real*)take((size_t)B * m * sizeof(Real));
   double* colpart = (double*)take((size_t)B * m * sizeof(double));
   double* cta_stats = (double*)take((size_t)2 * B * sizeof(double));
   const int ndot = 256;
@@ -658,28 +662,53 @@ int solve1d_typed(const Solve1DArgs& A, void* wsv, size_t ws_bytes) {
     log2_scaled<Real><<<(m + 255) / 256, 256, 0, st>>>(A.v, m, lv);
     fill_product<Real><<<4 * A.num_sms, 256, 0, st>>>(A.u, A.v, n, m, (Real*)A.T);
   }
-  Grad1DArgs ga{};
-  ga.n = n;
-  ga.m = m;
-  ga.k = A.k;
-  ga.hx = A.hx;
-  ga.hy = A.hy;
-  ga.dtype = A.dtype;
-  ga.T = A.T;
-  ga.G = Pi;
-  ga.u = A.u;
-  ga.v = A.v;
-  ga.exact = 0;
-  ga.out_scale = 2.0 * A.theta;
-  ga.stream = st;
-  ga.status = A.status;
-  ga.num_sms = A.num_sms;
-  ga.tracer = A.tracer;
-  ga.force_generic = A.force_generic;
+  // Pi = out_scale * G(T) with target marginals (out_scale = 2 theta), or,
+  // for the value, G(T) with T's own marginals.
+  auto gradient = [&](int exact, double out_scale) -> int {
+    if (A.dim == 2) {
+      Grad2DArgs g2{};
+      g2.sx = A.nx;
+      g2.sy = A.ny;
+      g2.cost = A.cost;
+      g2.hx = A.hx;
+      g2.hy = A.hy;
+      g2.dtype = A.dtype;
+      g2.T = A.T;
+      g2.G = Pi;
+      g2.u = A.u;
+      g2.v = A.v;
+      g2.exact = exact;
+      g2.out_scale = out_scale;
+      g2.stream = st;
+      g2.status = A.status;
+      g2.num_sms = A.num_sms;
+      g2.tracer = A.tracer;
+      return grad2d_launch(g2, gws, gws_bytes);
+    }
+    Grad1DArgs ga{};
+    ga.n = n;
+    ga.m = m;
+    ga.k = A.k;
+    ga.hx = A.hx;
+    ga.hy = A.hy;
+    ga.dtype = A.dtype;
+    ga.T = A.T;
+    ga.G = Pi;
+    ga.u = A.u;
+    ga.v = A.v;
+    ga.exact = exact;
+    ga.out_scale = out_scale;
+    ga.stream = st;
+    ga.status = A.status;
+    ga.num_sms = A.num_sms;
+    ga.tracer = A.tracer;
+    ga.force_generic = A.force_generic;
+    return grad1d_launch(ga, gws, gws_bytes);
+  };
   const bool fgw = A.theta != 1.0 && A.feat_dim > 0 && A.phi && A.psi;
 
   for (int l = 0; l < A.n_outer; ++l) {
-    int rc = grad1d_launch(ga, gws, gws_bytes);
+    int rc = gradient(0, 2.0 * A.theta);
     if (rc != GW_OK) return rc;
     if (fgw) {
       TraceScope ts(A.tracer, "add_feature_cost", st);
@@ -697,7 +726,7 @@ int solve1d_typed(const Solve1DArgs& A, void* wsv, size_t ws_bytes) {
       }
       {
         TraceScope ts(A.tracer, "sk_cols", st);
-        sk_cols<Real><<<(m + 31) / 32, 256, 0, st>>>(part, B, m, lv, G);
+        sk_cols<Real><<<(m + 31) / 32, 256, 0, st>>>(part, B, n, m, lv, G, Pi, F, c);
       }
     }
     {
@@ -711,10 +740,7 @@ int solve1d_typed(const Solve1DArgs& A, void* wsv, size_t ws_bytes) {
   if (A.stats) {
     TraceScope ts(A.tracer, "solve_stats", st);
     // E(T) = <G(T; T's marginals), T>; the gradient overwrites Pi.
-    Grad1DArgs ge = ga;
-    ge.exact = 1;
-    ge.out_scale = 1.0;
-    int rc = grad1d_launch(ge, gws, gws_bytes);
+    int rc = gradient(1, 1.0);
     if (rc != GW_OK) return rc;
     dot_partial<Real><<<ndot, 256, 0, st>>>(Pi, (const Real*)A.T, (size_t)n * m, dotE);
     if (fgw)
@@ -727,9 +753,10 @@ int solve1d_typed(const Solve1DArgs& A, void* wsv, size_t ws_bytes) {
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }
 
-size_t solve1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms) {
-  const size_t rb = dtype == GW_F32 ? 4 : 8;
-  const Bands bands = choose_bands(n, num_sms);
+size_t solve_workspace_bytes(const SolveArgs& A) {
+  const int n = A.n, m = A.m;
+  const size_t rb = A.dtype == GW_F32 ? 4 : 8;
+  const Bands bands = choose_bands(n, A.num_sms);
   size_t b = 0;
   auto add = [&](size_t x) { b = (b + x + 255) / 256 * 256; };
   add((size_t)n * m * rb);
@@ -737,25 +764,28 @@ size_t solve1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms) {
   add(m * rb);
   add(n * rb);
   add(m * rb);
-  add((size_t)bands.B * m * 2 * rb);
+  add((size_t)bands.B * m * rb);
   add((size_t)bands.B * m * 8);
   add((size_t)2 * bands.B * 8);
   add(256 * 8);
   add(256 * 8);
-  return b + grad1d_workspace_bytes(n, m, k, dtype, num_sms) + 4096;
+  const size_t g = A.dim == 2 ? grad2d_workspace_bytes(A.nx, A.ny, A.dtype)
+                              : grad1d_workspace_bytes(n, m, A.k, A.dtype, A.num_sms);
+  return b + g + 4096;
 }
 
-int solve1d_launch(const Solve1DArgs& A, void* ws, size_t ws_bytes) {
+int solve_launch(const SolveArgs& A, void* ws, size_t ws_bytes) {
   const int m = A.m;
   if (A.dtype == GW_F32) {
-    if (m <= 1024) return solve1d_typed<8, 4, float>(A, ws, ws_bytes);
-    if (m <= 4096) return solve1d_typed<16, 8, float>(A, ws, ws_bytes);
-    if (m <= 8192) return solve1d_typed<16, 16, float>(A, ws, ws_bytes);
-    return solve1d_typed<32, 16, float>(A, ws, ws_bytes);
+    if (m <= 1024) return solve_typed<8, 4, float>(A, ws, ws_bytes);
+    if (m <= 4096) return solve_typed<16, 8, float>(A, ws, ws_bytes);
+    if (m <= 8192) return solve_typed<16, 16, float>(A, ws, ws_bytes);
+    if (m <= 9216) return solve_typed<18, 16, float>(A, ws, ws_bytes);
+    return solve_typed<32, 16, float>(A, ws, ws_bytes);
   }
-  if (m <= 1024) return solve1d_typed<8, 4, double>(A, ws, ws_bytes);
-  if (m <= 4096) return solve1d_typed<16, 8, double>(A, ws, ws_bytes);
-  return solve1d_typed<32, 16, double>(A, ws, ws_bytes);
+  if (m <= 1024) return solve_typed<8, 4, double>(A, ws, ws_bytes);
+  if (m <= 4096) return solve_typed<16, 8, double>(A, ws, ws_bytes);
+  return solve_typed<32, 16, double>(A, ws, ws_bytes);
 }
 
 }  // namespace gw

@@ -1,0 +1,107 @@
+"""Parity of the 2D entropic (F)GW solve (CUDA, through the C ABI) with the
+FP64 oracle's mirror descent on the dense 2D distance matrices (same
+schedule as the 1D solve: T^0 = u v^T, f = g = 0 at every outer step, f then
+g, fixed counts).  The cost inside each step is the 2D separable gradient.
+
+Tolerances as for the 1D solve: double 1e-9 (plan) and 1e-10 (value); float
+3e-5 on the value (the float gradient's ~1e-7 relative error is amplified by
+up to ~1/eps through the mirror descent)."""
+import numpy as np
+import pytest
+
+from oracle import gw_oracle as O
+from paper_2404_08970_gb300 import inputs as I
+from tests import gwtest_util as U
+
+pytestmark = pytest.mark.gpu
+
+COSTS = {"manhattan": 0, "sqeuclid": 1}
+
+
+def gpu_solve_2d(w, dtype, theta=1.0, phi=None, psi=None):
+    import torch
+    from paper_2404_08970_gb300 import _lib as L
+    c = U.ctx()
+    n, m = w["nx"] ** 2, w["ny"] ** 2
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    T = torch.empty(n, m, dtype=tdt, device="cuda")
+    f = torch.empty(n, dtype=torch.float64, device="cuda")
+    g = torch.empty(m, dtype=torch.float64, device="cuda")
+    stats = torch.zeros(8, dtype=torch.float64, device="cuda")
+    du = torch.from_numpy(w["u"]).cuda()
+    dv = torch.from_numpy(w["v"]).cuda()
+    D = 0 if phi is None else phi.shape[1]
+    dphi = None if phi is None else torch.from_numpy(np.ascontiguousarray(phi)).cuda()
+    dpsi = None if psi is None else torch.from_numpy(np.ascontiguousarray(psi)).cuda()
+    prob = L.problem(dim=2, nx=w["nx"], ny=w["ny"], hx=w["hx"], hy=w["hy"], k=1, cost=COSTS[w["cost"]],
+                     eps=w["eps"], n_outer=w["n_outer"], n_inner=w["n_inner"], theta=theta, feat_dim=D,
+                     dtype=L.GW_F32 if dtype == "f32" else L.GW_F64)
+    c.gw_solve(prob, du, dv, T, f, g, stats, dphi, dpsi)
+    c.gw_ctx_check()
+    return T.double().cpu().numpy(), f.cpu().numpy(), g.cpu().numpy(), stats.cpu().numpy()
+
+
+def oracle_solve_2d(w, theta=1.0, phi=None, psi=None):
+    DX = O.grid_dist_2d(w["nx"], w["hx"], w["cost"])
+    DY = O.grid_dist_2d(w["ny"], w["hy"], w["cost"])
+    CC = None if phi is None else O.fgw_feature_cost(phi, psi)
+    T, f, g = O.mirror_descent(DX, DY, w["u"], w["v"], w["eps"], w["n_outer"], w["n_inner"], theta=theta, CC=CC)
+    E = O.value(DX, DY, T)
+    lin = 0.0 if CC is None else float(np.sum(CC * T))
+    return T, f, g, dict(E=E, lin=lin, obj=(1 - theta) * lin + theta * E, H=w["eps"] * O.entropy(T))
+
+
+def small_2d(sx, sy, cost, eps, n_outer, n_inner, seed):
+    rng = I.rng_for(seed)
+    return dict(nx=sx, ny=sy, hx=1.0 / (sx - 1), hy=1.0 / (sy - 1), cost=cost, eps=eps, n_outer=n_outer,
+                n_inner=n_inner, u=I.abs_normal_image(sx, rng), v=I.abs_normal_image(sy, rng))
+
+
+@pytest.mark.parametrize("cost", ["sqeuclid", "manhattan"])
+@pytest.mark.parametrize("shape", [(6, 8), (16, 20), (12, 9)])
+def test_solve2d_fp64(shape, cost):
+    w = small_2d(*shape, cost, eps=2e-2, n_outer=6, n_inner=60, seed=shape[0] * 10 + shape[1])
+    T, f, g, st = gpu_solve_2d(w, "f64")
+    Ts, fs, gs, ss = oracle_solve_2d(w)
+    assert U.relerr(T, Ts) < 1e-9, U.relerr(T, Ts)
+    assert abs(st[1] - ss["E"]) <= 1e-10 * abs(ss["E"])
+    assert abs(st[3] - ss["H"]) <= 1e-9 * abs(ss["H"])
+    assert st[5] < 1e-12
+
+
+@pytest.mark.parametrize("cost", ["sqeuclid", "manhattan"])
+def test_solve2d_fp32_image_workload(cost):
+    """|N(0,1)| image marginals on the unit square, eps = 5e-3, 20 x 100 (the
+    2D benchmark schedule) on 16 x 16 against 20 x 20 grids."""
+    w = small_2d(16, 20, cost, eps=5e-3, n_outer=20, n_inner=100, seed=5)
+    T, f, g, st = gpu_solve_2d(w, "f32")
+    Ts, fs, gs, ss = oracle_solve_2d(w)
+    assert abs(st[1] - ss["E"]) <= 3e-5 * abs(ss["E"]), (st[1], ss["E"])
+    assert st[5] < 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_solve2d_fused(dtype):
+    """theta = 0.5 with 16-dim N(0,1) features (scaled by 0.1)."""
+    w = small_2d(8, 10, "sqeuclid", eps=5e-2, n_outer=5, n_inner=50, seed=21)
+    rng = np.random.default_rng(4)
+    phi, psi = I.features(64, 16, rng) * 0.1, I.features(100, 16, rng) * 0.1
+    T, f, g, st = gpu_solve_2d(w, dtype, theta=0.5, phi=phi, psi=psi)
+    Ts, fs, gs, ss = oracle_solve_2d(w, theta=0.5, phi=phi, psi=psi)
+    tol = 1e-9 if dtype == "f64" else 3e-5
+    assert abs(st[0] - ss["obj"]) <= tol * abs(ss["obj"])
+    if dtype == "f64":
+        assert U.relerr(T, Ts) < 1e-9
+
+
+def test_solve2d_full_size_invariants():
+    """64 x 64 against 96 x 96 at eps = 5e-3 with 2 x 50 iterations: column
+    marginals exact after the g update, E >= 0, a finite value."""
+    rng = I.rng_for(0)
+    w = dict(nx=64, ny=96, hx=1 / 63, hy=1 / 95, cost="sqeuclid", eps=5e-3, n_outer=2, n_inner=50,
+             u=I.abs_normal_image(64, rng), v=I.abs_normal_image(96, rng))
+    T, f, g, st = gpu_solve_2d(w, "f32")
+    assert np.all(np.isfinite(st[:6]))
+    assert st[1] >= 0.0
+    assert st[5] < 1e-4
+    assert abs(T.sum() - 1.0) < 1e-4
