@@ -21,8 +21,9 @@
 //   g2_marg    M1..M4, R and C (the marginals as side x side matrices).
 //   g2_vec     row and column sums of R and C.
 //   g2_tx      small transforms by A from the left, then from the right.
-//   g2_cy      the column constant c_y as a hi/lo table.
-//   g2_epi     writes G row by row from per-row tables in shared memory.
+//   g2_tab     the epilogue tables: c_y per column, and per row of X the parts
+//              of G that depend on (row, c) and on (row, d).
+//   g2_epi     writes G, one warp per row.
 //
 // Sums are compensated: Kahan in the row pass, float-float (double for
 // double data) everywhere after it; outputs are rounded once.
@@ -70,8 +71,9 @@ __device__ __forceinline__ double acc_w(double x, float w) { return x * (double)
 // base + l): 31 shuffles per 32 sums.
 // ---------------------------------------------------------------------------
 template <typename Real, int NQ>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 1)
     g2_rows(const Real* __restrict__ T, int n, int sy, AccOf<Real>* __restrict__ Rc, AccOf<Real>* __restrict__ Rd) {
+  constexpr int SG = NQ <= 2 ? 16 : 8;  // c's whose loads are issued together
   const int lane = threadIdx.x & 31;
   const int w0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
@@ -84,22 +86,30 @@ __global__ void __launch_bounds__(256, 2)
     for (int cg = 0; cg < sy; cg += 32) {
       Real xs[32];
 #pragma unroll
-      for (int cc = 0; cc < 32; ++cc) {
-        const int c = cg + cc;
-        Real x = 0;
-        if (c < sy) {
+      for (int sg = 0; sg < 32; sg += SG) {
+        Real t[SG][NQ];
+#pragma unroll
+        for (int cc = 0; cc < SG; ++cc) {
+          const int c = cg + sg + cc;
 #pragma unroll
           for (int q = 0; q < NQ; ++q) {
             const int d = lane + 32 * q;
-            const Real t = d < sy ? __ldcs(row + (size_t)c * sy + d) : (Real)0;
-            x += t;
-            const Real y = t - rc[q];
+            t[cc][q] = (c < sy && d < sy) ? __ldcs(row + (size_t)c * sy + d) : (Real)0;
+          }
+        }
+#pragma unroll
+        for (int cc = 0; cc < SG; ++cc) {
+          Real x = 0;
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            x += t[cc][q];
+            const Real y = t[cc][q] - rc[q];
             const Real s2 = rs[q] + y;
             rc[q] = (s2 - rs[q]) - y;
             rs[q] = s2;
           }
+          xs[sg + cc] = x;
         }
-        xs[cc] = x;
       }
 #pragma unroll
       for (int o = 16; o >= 1; o >>= 1) {
@@ -161,16 +171,31 @@ __global__ void g2_marg(const Acc* __restrict__ Rc, const Acc* __restrict__ Rd, 
   if (idx < nM) {
     const int t = idx / (sx * sy), e = idx % (sx * sy), r = e / sy, col = e % sy;
     const Acc* src = (t == 0 || t == 2) ? Rc : Rd;
-    for (int o = 0; o < sx; ++o) {
-      const int i = (t < 2) ? r * sx + o : o * sx + r;
-      s = acc_add(s, src[(size_t)i * sy + col]);
+    const size_t base = (t < 2) ? (size_t)r * sx * sy + col : (size_t)r * sy + col;
+    const size_t step = (t < 2) ? (size_t)sy : (size_t)sx * sy;
+    int o = 0;
+    for (; o + 8 <= sx; o += 8) {
+      Acc x[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) x[e] = src[base + (size_t)(o + e) * step];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) s = acc_add(s, x[e]);
     }
+    for (; o < sx; ++o) s = acc_add(s, src[base + (size_t)o * step]);
     M[idx] = s;
   } else if (idx < nM + nR) {
     const int e = idx - nM;
-    if (exact)
-      for (int c = 0; c < sy; ++c) s = acc_add(s, Rc[(size_t)e * sy + c]);
-    else
+    if (exact) {
+      int c = 0;
+      for (; c + 8 <= sy; c += 8) {
+        Acc x[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) x[q] = Rc[(size_t)e * sy + c + q];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s = acc_add(s, x[q]);
+      }
+      for (; c < sy; ++c) s = acc_add(s, Rc[(size_t)e * sy + c]);
+    } else
       s = acc_add_d(s, u[e]);
     R[e] = s;
   } else if (idx < nM + nR + nC) {
@@ -183,24 +208,39 @@ __global__ void g2_marg(const Acc* __restrict__ Rc, const Acc* __restrict__ Rd, 
   }
 }
 
-// rA = R 1, rB = 1^T R, cA = C 1, cB = 1^T C.
+// rA = R 1, rB = 1^T R, cA = C 1, cB = 1^T C: one warp per output, lanes
+// over the summed index, then a fixed-order butterfly.
+__device__ __forceinline__ ff acc_shfl_xor(ff a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
+}
+__device__ __forceinline__ double acc_shfl_xor(double a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+
 template <typename Acc>
 __global__ void g2_vec(const Acc* __restrict__ R, const Acc* __restrict__ C, int sx, int sy, Acc* __restrict__ rA,
                        Acc* __restrict__ rB, Acc* __restrict__ cA, Acc* __restrict__ cB) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  Acc s = acc_zero((Acc*)nullptr);
-  if (idx < 2 * sx) {
-    const int j = idx % sx;
-    const bool rows = idx < sx;
-    for (int o = 0; o < sx; ++o) s = acc_add(s, rows ? R[j * sx + o] : R[o * sx + j]);
-    (rows ? rA : rB)[j] = s;
-  } else if (idx < 2 * sx + 2 * sy) {
-    const int e = idx - 2 * sx;
-    const int j = e % sy;
-    const bool rows = e < sy;
-    for (int o = 0; o < sy; ++o) s = acc_add(s, rows ? C[j * sy + o] : C[o * sy + j]);
-    (rows ? cA : cB)[j] = s;
+  const int wid = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  if (wid >= 2 * sx + 2 * sy) return;
+  const Acc* src;
+  Acc* dst;
+  int s, j, rows;
+  if (wid < 2 * sx) {
+    src = R;
+    s = sx;
+    j = wid % sx;
+    rows = wid < sx;
+    dst = rows ? rA : rB;
+  } else {
+    src = C;
+    s = sy;
+    j = (wid - 2 * sx) % sy;
+    rows = (wid - 2 * sx) < sy;
+    dst = rows ? cA : cB;
   }
+  Acc t = acc_zero((Acc*)nullptr);
+  for (int o = lane; o < s; o += 32) t = acc_add(t, rows ? src[j * s + o] : src[o * s + j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t = acc_add(t, acc_shfl_xor(t, o));
+  if (lane == 0) dst[j] = t;
 }
 
 // Small transforms by the axis matrix A (entries A(i - l)^pw):
@@ -230,104 +270,138 @@ __global__ void g2_tx(const __grid_constant__ TxJobs jobs) {
   const int per = J.rows * J.cols;
   const int b = e / per, i = (e % per) / J.cols, j = e % J.cols;
   const Acc* in = (const Acc*)J.in + (size_t)b * per;
-  Acc s0 = acc_zero((Acc*)nullptr), s1 = s0;
   const int len = J.right ? J.cols : J.rows;
-  int l = 0;
-  for (; l + 1 < len; l += 2) {
-    const float w0 = axis_w(J.right ? l - j : i - l, J.sq);
-    const float w1 = axis_w(J.right ? l + 1 - j : i - l - 1, J.sq);
-    Acc x0 = J.right ? in[i * J.cols + l] : in[l * J.cols + j];
-    Acc x1 = J.right ? in[i * J.cols + l + 1] : in[(l + 1) * J.cols + j];
-    x0 = acc_w(x0, w0);
-    x1 = acc_w(x1, w1);
-    if (J.pw == 2) {
-      x0 = acc_w(x0, w0);
-      x1 = acc_w(x1, w1);
-    }
-    s0 = acc_add(s0, x0);
-    s1 = acc_add(s1, x1);
-  }
-  if (l < len) {
-    const float w0 = axis_w(J.right ? l - j : i - l, J.sq);
-    Acc x0 = J.right ? in[i * J.cols + l] : in[l * J.cols + j];
-    x0 = acc_w(x0, w0);
-    if (J.pw == 2) x0 = acc_w(x0, w0);
-    s0 = acc_add(s0, x0);
-  }
-  ((Acc*)J.out)[e] = acc_add(s0, s1);
-}
-
-// Column constant: Cy[(c,d)] = scale_y (py[c] + 2 WY[c][d] + qy[d]), with
-// scale_y = out_scale s_Y^2, as hi/lo.
-template <typename Real>
-__global__ void g2_cy(const AccOf<Real>* __restrict__ py, const AccOf<Real>* __restrict__ qy,
-                      const AccOf<Real>* __restrict__ WY, int sy, double scale_y, Real* __restrict__ CyH,
-                      Real* __restrict__ CyL) {
-  using Acc = AccOf<Real>;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= sy * sy) return;
-  const int c = p / sy, d = p % sy;
-  Acc sc;
-  acc_from(&sc, scale_y);
-  const Acc w = WY[p];
-  Acc s = acc_add(acc_add(py[c], qy[d]), acc_add(w, w));
-  s = acc_mul(s, sc);
-  Real hi, lo;
-  acc_split(s, hi, lo);
-  CyH[p] = hi;
-  CyL[p] = lo;
-}
-
-// G rows.  For row (a,b):
-//   Ux[c] = out_scale (s_X^2 (px[a] + 2 WX[a][b] + qx[b]) - 2 s_X s_Y (Z1[a][c] + Z3[b][c]))
-//   Vx[d] = -out_scale 2 s_X s_Y (Z2[a][d] + Z4[b][d])
-//   G[(a,b),(c,d)] = Ux[c] + Vx[d] + Cy[(c,d)]   (hi parts, then lo parts).
-// The per-row tables are double-buffered in shared memory, so each row costs
-// one block barrier.
-template <typename Real, int NQ>
-__global__ void __launch_bounds__(512, 1)
-    g2_epi(Real* __restrict__ G, int sx, int sy, const AccOf<Real>* __restrict__ Z, const AccOf<Real>* __restrict__ px,
-           const AccOf<Real>* __restrict__ qx, const AccOf<Real>* __restrict__ WX, const Real* __restrict__ CyH,
-           const Real* __restrict__ CyL, double scale_x, double scale_z) {
-  using Acc = AccOf<Real>;
-  constexpr bool kLo = sizeof(Real) == 4;
-  __shared__ Real UH[2][256], UL[2][256], VH[2][256], VL[2][256];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int n = sx * sx;
-  const size_t m = (size_t)sy * sy;
-  const int per_mat = sx * sy;
-  Acc scx, scz;
-  acc_from(&scx, scale_x);
-  acc_from(&scz, scale_z);
-  int buf = 0;
-  for (int i = blockIdx.x; i < n; i += gridDim.x, buf ^= 1) {
-    const int a = i / sx, b = i % sx;
-    if (tid < sy) {
-      const int c = tid;
-      const Acc w = WX[a * sx + b];
-      Acc cx = acc_add(acc_add(px[a], qx[b]), acc_add(w, w));
-      cx = acc_mul(cx, scx);
-      const Acc zz = acc_mul(acc_add(Z[a * sy + c], Z[2 * per_mat + b * sy + c]), scz);
-      const Acc U = acc_sub(cx, zz);
-      acc_split(U, UH[buf][c], UL[buf][c]);
-    } else if (tid >= 256 && tid - 256 < sy) {
-      const int d = tid - 256;
-      const Acc zz = acc_mul(acc_add(Z[per_mat + a * sy + d], Z[3 * per_mat + b * sy + d]), scz);
-      const Acc V = acc_neg_of(zz);
-      acc_split(V, VH[buf][d], VL[buf][d]);
-    }
-    __syncthreads();
-    Real* grow = G + (size_t)i * m;
-    for (int c = warp; c < sy; c += 16) {
-      const Real uh = UH[buf][c], ul = UL[buf][c];
+  // Element l of the contracted line and the weight's offset from it.
+  const Acc* x0 = J.right ? in + (size_t)i * J.cols : in + j;
+  const int stride = J.right ? 1 : J.cols;
+  const int ref = J.right ? j : i;
+  constexpr int U = 8;
+  Acc s[4];
 #pragma unroll
-      for (int q = 0; q < NQ; ++q) {
-        const int d = lane + 32 * q;
-        if (d < sy) {
-          const int p = c * sy + d;
-          Real g = (uh + VH[buf][d]) + __ldg(CyH + p);
-          if (kLo) g += (ul + VL[buf][d]) + __ldg(CyL + p);
-          __stcs(grow + p, g);
+  for (int q = 0; q < 4; ++q) s[q] = acc_zero((Acc*)nullptr);
+  int l = 0;
+  for (; l + U <= len; l += U) {
+    Acc x[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) x[q] = x0[(size_t)(l + q) * stride];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const float w = axis_w(l + q - ref, J.sq);
+      Acc y = acc_w(x[q], w);
+      if (J.pw == 2) y = acc_w(y, w);
+      s[q & 3] = acc_add(s[q & 3], y);
+    }
+  }
+  for (; l < len; ++l) {
+    const float w = axis_w(l - ref, J.sq);
+    Acc y = acc_w(x0[(size_t)l * stride], w);
+    if (J.pw == 2) y = acc_w(y, w);
+    s[0] = acc_add(s[0], y);
+  }
+  ((Acc*)J.out)[e] = acc_add(acc_add(s[0], s[1]), acc_add(s[2], s[3]));
+}
+
+// Epilogue tables, all hi/lo (rounded once from the compensated values):
+//   Cy[(c,d)] = scale_y (py[c] + 2 WY[c][d] + qy[d]),   scale_y = out_scale s_Y^2
+//   Ux[i][c]  = scale_x (px[a] + 2 WX[a][b] + qx[b]) - scale_z (Z1[a][c] + Z3[b][c])
+//   Vx[i][d]  = -scale_z (Z2[a][d] + Z4[b][d])
+// for i = (a,b), with scale_x = out_scale s_X^2 and scale_z = 2 out_scale s_X s_Y,
+// so that G[(a,b),(c,d)] = Ux[i][c] + Vx[i][d] + Cy[(c,d)].  Layout: Cy as
+// [m] hi then [m] lo; UV as [n][sy] (Ux hi, Ux lo, Vx hi, Vx lo) per entry.
+template <typename Real>
+__global__ void g2_tab(const AccOf<Real>* __restrict__ Z, const AccOf<Real>* __restrict__ px,
+                       const AccOf<Real>* __restrict__ qx, const AccOf<Real>* __restrict__ WX,
+                       const AccOf<Real>* __restrict__ py, const AccOf<Real>* __restrict__ qy,
+                       const AccOf<Real>* __restrict__ WY, int sx, int sy, double scale_x, double scale_y,
+                       double scale_z, Real* __restrict__ Cy, Real* __restrict__ UV) {
+  using Acc = AccOf<Real>;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = sy * sy, n = sx * sx, per_mat = sx * sy;
+  if (idx < m) {
+    const int c = idx / sy, d = idx % sy;
+    Acc sc;
+    acc_from(&sc, scale_y);
+    const Acc w = WY[idx];
+    const Acc v = acc_mul(acc_add(acc_add(py[c], qy[d]), acc_add(w, w)), sc);
+    Real hi, lo;
+    acc_split(v, hi, lo);
+    Cy[idx] = hi;
+    Cy[m + idx] = lo;
+  } else if (idx < m + n * sy) {
+    const int e = idx - m;
+    const int i = e / sy, c = e % sy;  // c doubles as d for the V part
+    const int a = i / sx, b = i % sx;
+    Acc scx, scz;
+    acc_from(&scx, scale_x);
+    acc_from(&scz, scale_z);
+    const Acc w = WX[a * sx + b];
+    const Acc cx = acc_mul(acc_add(acc_add(px[a], qx[b]), acc_add(w, w)), scx);
+    const Acc U = acc_sub(cx, acc_mul(acc_add(Z[a * sy + c], Z[2 * per_mat + b * sy + c]), scz));
+    const Acc V = acc_neg_of(acc_mul(acc_add(Z[per_mat + a * sy + c], Z[3 * per_mat + b * sy + c]), scz));
+    Real* o = UV + (size_t)e * 4;
+    acc_split(U, o[0], o[1]);
+    acc_split(V, o[2], o[3]);
+  }
+}
+
+// G rows: one warp per row, lane l on d = l + 32q; no block barriers.  The
+// row's table entries (Ux, Vx) for index l + 32q sit in lane l's registers
+// (loaded one row ahead); Ux[c] reaches every lane by a shuffle.
+//   G[(a,b),(c,d)] = (Ux[c] + Vx[d] + Cy[(c,d)])_hi + (...)_lo
+template <typename Real>
+struct Quad {
+  Real uh, ul, vh, vl;
+};
+__device__ __forceinline__ Quad<float> load_quad(const float* p) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+  return {t.x, t.y, t.z, t.w};
+}
+__device__ __forceinline__ Quad<double> load_quad(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return {a.x, a.y, b.x, b.y};
+}
+
+template <typename Real, int NQ>
+__global__ void __launch_bounds__(256)
+    g2_epi(Real* __restrict__ G, int n, int sy, const Real* __restrict__ Cy, const Real* __restrict__ UV) {
+  constexpr bool kLo = sizeof(Real) == 4;
+  const int lane = threadIdx.x & 31;
+  const int w0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int m = sy * sy;
+  Quad<Real> nxt[NQ];
+  auto fetch = [&](int i) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int d = lane + 32 * q;
+      nxt[q] = (i < n && d < sy) ? load_quad(UV + ((size_t)i * sy + d) * 4) : Quad<Real>{0, 0, 0, 0};
+    }
+  };
+  fetch(w0);
+  for (int i = w0; i < n; i += nw) {
+    Quad<Real> cur[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) cur[q] = nxt[q];
+    fetch(i + nw);
+    Real* grow = G + (size_t)i * m;
+#pragma unroll
+    for (int qc = 0; qc < NQ; ++qc) {
+      const int cmax = min(32, sy - 32 * qc);
+#pragma unroll 4
+      for (int l = 0; l < cmax; ++l) {
+        const int c = 32 * qc + l;
+        const Real uh = __shfl_sync(0xffffffffu, cur[qc].uh, l);
+        const Real ul = __shfl_sync(0xffffffffu, cur[qc].ul, l);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int d = lane + 32 * q;
+          if (d < sy) {
+            const int p = c * sy + d;
+            Real g = (uh + cur[q].vh) + __ldg(Cy + p);
+            if (kLo) g += (ul + cur[q].vl) + __ldg(Cy + m + p);
+            __stcs(grow + p, g);
+          }
         }
       }
     }
@@ -338,7 +412,7 @@ __global__ void __launch_bounds__(512, 1)
 // Host side
 // ---------------------------------------------------------------------------
 struct G2Layout {
-  size_t Rc, Rd, M, R, C, rA, rB, cA, cB, Y, YR, YC, px, qx, py, qy, Z, WX, WY, CyH, CyL, part, Cm, total;
+  size_t Rc, Rd, M, R, C, rA, rB, cA, cB, Y, YR, YC, px, qx, py, qy, Z, WX, WY, Cy, UV, part, Cm, total;
   int nb;
 };
 
@@ -373,12 +447,23 @@ G2Layout g2_layout(int sx, int sy, int dtype) {
   L.Z = take(4 * (size_t)sx * sy * acc);
   L.WX = take(n * acc);
   L.WY = take(m * acc);
-  L.CyH = take(m * rb);
-  L.CyL = take(m * rb);
+  L.Cy = take(2 * m * rb);
+  L.UV = take(n * sy * 4 * rb);
   L.part = take((size_t)L.nb * m * acc);
   L.Cm = take(m * acc);
   L.total = off;
   return L;
+}
+
+// Blocks of `threads` threads that one SM holds at once for kernel f.
+template <typename F>
+int resident_blocks(F f, int threads) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, threads, 0) != cudaSuccess || b < 1) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return b;
 }
 
 template <typename Real, int NQ>
@@ -397,7 +482,7 @@ int grad2d_typed(const Grad2DArgs& A, void* wsv, size_t ws_bytes) {
   const double s_y = sq ? A.hy * A.hy : A.hy;
   {
     TraceScope ts(A.tracer, "g2_rows", st);
-    const int blocks = std::max(1, std::min((n + 7) / 8, 2 * A.num_sms));
+    const int blocks = std::max(1, std::min((n + 7) / 8, resident_blocks(g2_rows<Real, NQ>, 256) * A.num_sms));
     g2_rows<Real, NQ><<<blocks, 256, 0, st>>>(T, n, sy, P(L.Rc), P(L.Rd));
   }
   if (A.exact) {
@@ -408,12 +493,15 @@ int grad2d_typed(const Grad2DArgs& A, void* wsv, size_t ws_bytes) {
     g2_colsum_fin<Acc><<<(m + 255) / 256, 256, 0, st>>>(P(L.part), nb, m, P(L.Cm));
   }
   {
-    TraceScope ts(A.tracer, "g2_small", st);
+    TraceScope ts(A.tracer, "g2_marg", st);
     const int tot = 4 * sx * sy + n + m;
     g2_marg<Acc><<<(tot + 255) / 256, 256, 0, st>>>(P(L.Rc), P(L.Rd), sx, sy, A.u, A.v, P(L.Cm), A.exact, P(L.M),
                                                     P(L.R), P(L.C));
-    g2_vec<Acc><<<(2 * sx + 2 * sy + 255) / 256, 256, 0, st>>>(P(L.R), P(L.C), sx, sy, P(L.rA), P(L.rB), P(L.cA),
-                                                               P(L.cB));
+  }
+  {
+    TraceScope ts(A.tracer, "g2_tx", st);
+    g2_vec<Acc><<<(2 * sx + 2 * sy + 7) / 8, 256, 0, st>>>(P(L.R), P(L.C), sx, sy, P(L.rA), P(L.rB), P(L.cA),
+                                                           P(L.cB));
     TxJobs left{};
     int start = 0;
     auto add = [&](TxJobs& js, size_t in, size_t out, int batch, int rows, int cols, int right, int pw) {
@@ -446,15 +534,19 @@ int grad2d_typed(const Grad2DArgs& A, void* wsv, size_t ws_bytes) {
     add(right, L.YC, L.WY, 1, sy, sy, 1, 1);
     right.total = start;
     g2_tx<Acc><<<(right.total + 127) / 128, 128, 0, st>>>(right);
-    g2_cy<Real><<<(m + 255) / 256, 256, 0, st>>>(P(L.py), P(L.qy), P(L.WY), sy, A.out_scale * s_y * s_y,
-                                                  (Real*)(ws + L.CyH), (Real*)(ws + L.CyL));
+  }
+  {
+    TraceScope ts(A.tracer, "g2_tab", st);
+    const int tab = m + n * sy;
+    g2_tab<Real><<<(tab + 255) / 256, 256, 0, st>>>(P(L.Z), P(L.px), P(L.qx), P(L.WX), P(L.py), P(L.qy), P(L.WY),
+                                                     sx, sy, A.out_scale * s_x * s_x, A.out_scale * s_y * s_y,
+                                                     A.out_scale * 2.0 * s_x * s_y, (Real*)(ws + L.Cy),
+                                                     (Real*)(ws + L.UV));
   }
   {
     TraceScope ts(A.tracer, "g2_epi", st);
-    const int blocks = std::max(1, std::min(n, A.num_sms));
-    g2_epi<Real, NQ><<<blocks, 512, 0, st>>>((Real*)A.G, sx, sy, P(L.Z), P(L.px), P(L.qx), P(L.WX),
-                                             (const Real*)(ws + L.CyH), (const Real*)(ws + L.CyL),
-                                             A.out_scale * s_x * s_x, A.out_scale * 2.0 * s_x * s_y);
+    const int blocks = std::max(1, std::min((n + 7) / 8, resident_blocks(g2_epi<Real, NQ>, 256) * A.num_sms));
+    g2_epi<Real, NQ><<<blocks, 256, 0, st>>>((Real*)A.G, n, sy, (const Real*)(ws + L.Cy), (const Real*)(ws + L.UV));
   }
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }
