@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", dest="solve", action="store_false")
     ap.add_argument("--no-2d", dest="grid2d", action="store_false")
+    ap.add_argument("--no-batch", dest="batch", action="store_false")
+    ap.add_argument("--batch-count", type=int, default=256)
     return ap.parse_args()
 
 
@@ -252,6 +254,42 @@ def bench_2d(ctx, L, dev, stream, barrier, steps, with_solve):
     return out
 
 
+def bench_batch(ctx, L, dev, stream, barrier, count):
+    """`count` independent 1D problems, n and m log-uniform in [256, 8192], k in
+    {1, 2}, uniform marginals, eps = 1e-2, 20 x 100: one gw_solve_batch call
+    (one graph launch after the first call captures it)."""
+    import numpy as np
+    import torch
+    from paper_2404_08970_gb300 import inputs as I
+    ws = I.workload_batch(count, seed=0)
+    probs = [L.problem(dim=1, nx=w["nx"], ny=w["ny"], hx=w["hx"], hy=w["hy"], k=w["k"], eps=w["eps"],
+                       n_outer=w["n_outer"], n_inner=w["n_inner"], dtype=L.GW_F32) for w in ws]
+    u = [torch.from_numpy(w["u"]).to(dev) for w in ws]
+    v = [torch.from_numpy(w["v"]).to(dev) for w in ws]
+    T = [torch.empty(w["nx"], w["ny"], dtype=torch.float32, device=dev) for w in ws]
+    st = [torch.zeros(8, dtype=torch.float64, device=dev) for w in ws]
+    t0 = time.perf_counter()
+    ctx.gw_solve_batch(probs, u, v, T, st, stream=stream)  # builds and launches the graph
+    barrier()
+    t_first = time.perf_counter() - t0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.gw_solve_batch(probs, u, v, T, st, stream=stream)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    ctx.gw_ctx_check(stream)
+    nm = float(sum(w["nx"] * w["ny"] for w in ws))
+    passes = sum(w["n_outer"] * w["n_inner"] for w in ws) / count
+    vals = torch.stack(st)[:, 1].cpu().numpy()
+    return {"workload": f"{count} 1D problems, n,m log-uniform in [256, 8192], k in {{1,2}}, uniform marginals, "
+                        "eps=1e-2, 20 x 100, fp32; one gw_solve_batch call (one CUDA graph)",
+            "problems": count, "ms": ms, "problems_per_s": count / (ms / 1e3),
+            "sum_nm": nm, "sinkhorn_stream_gbs": 4.0 * nm * passes / (ms / 1e3) / 1e9,
+            "first_call_s_incl_capture": t_first, "all_values_finite": bool(np.all(np.isfinite(vals)))}
+
+
 # ---------------------------------------------------------------------------
 # Arms
 # ---------------------------------------------------------------------------
@@ -446,6 +484,7 @@ def run_ours(args):
                          "replaces only the 20 gradients by the best dense gradient time"}
 
     grid2d = bench_2d(ctx, L, dev, stream, barrier, min(args.steps, 20), args.solve) if args.grid2d else None
+    batch = bench_batch(ctx, L, dev, stream, barrier, args.batch_count) if args.batch else None
 
     clk = clocks.stop()
 
@@ -461,7 +500,7 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(n, k),
                 "roofline": roof, "whole_gradient_gbs": whole_gbs, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": launches, "kernels": prof, "dense": dense, "solve": solve,
-                "grid2d": grid2d}
+                "grid2d": grid2d, "batch": batch}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -216,6 +216,38 @@ gw_status gw_solve(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const
                    const double* d_phi, const double* d_psi, void* d_T, double* d_f, double* d_g,
                    double* d_stats, void* stream);
 
+/*
+ * gw_solve_batch - `count` independent solves (as gw_solve, without the
+ * potentials) in one call: the batched workload of many problems of mixed
+ * sizes (the paper solves one problem at a time; batching is a throughput
+ * mode of the same method).
+ *
+ *   probs[i]            descriptor of problem i (validated as for gw_solve).
+ *   d_u[i], d_v[i]      target marginals of problem i (device, double).
+ *   d_phi, d_psi        NULL, or arrays whose entry i is problem i's feature
+ *                       array (NULL where theta == 1).
+ *   d_T[i]              output plan of problem i (device, probs[i].dtype).
+ *   d_stats             NULL, or an array whose entry i is NULL or 8 device
+ *                       doubles (layout as for gw_solve).
+ *   The pointer arrays themselves are host memory, read during the call.
+ *
+ * Problems with the same row configuration (set by ny), dtype and schedule
+ * form groups of up to 32 that advance in lock step: each Sinkhorn pass is
+ * one launch over all row bands of the group's problems (bands of at least 32
+ * rows), the gradients run per problem.  Groups run concurrently on up to 32
+ * worker streams of the context, forked from and joined back into `stream`;
+ * each problem gets its own region of a batch workspace owned by the context.
+ * The whole batch is captured once into one CUDA graph and relaunched while
+ * the arguments are unchanged.  Results agree with gw_solve on each problem
+ * alone up to rounding (the batch's longer row bands group the partial sums
+ * differently).
+ * Errors: GW_ERR_INVALID naming the first bad problem; GW_ERR_OOM if the
+ * batch workspace cannot be allocated.
+ */
+gw_status gw_solve_batch(gw_ctx* ctx, int count, const gw_problem* probs, const double* const* d_u,
+                         const double* const* d_v, const double* const* d_phi, const double* const* d_psi,
+                         void* const* d_T, double* const* d_stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

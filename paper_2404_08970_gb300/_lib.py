@@ -93,6 +93,7 @@ def load() -> ctypes.CDLL:
         "gw_solve": (S, [P, prob, P, P, P, P, P, P, P, P, P]),
         "gw_grad_dense": (S, [P, prob, P, P, P, P, I, I, P]),
         "gw_grad_noalloc": (S, [prob, P, P, P, P, I, P]),
+        "gw_solve_batch": (S, [P, I, prob, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -193,6 +194,22 @@ class Context:
         st = self.lib.gw_solve(self.h, ctypes.byref(prob), _ptr(u), _ptr(v), _ptr(phi), _ptr(psi), _ptr(T),
                                _ptr(f), _ptr(g), _ptr(stats), _stream(stream))
         return self._check(st, "gw_solve")
+
+    def gw_solve_batch(self, probs, u, v, T, stats=None, phi=None, psi=None, stream=None) -> int:
+        """probs: list of gw_problem; u, v, T (and optionally stats, phi,
+        psi): lists of device tensors (entries may be None where allowed)."""
+        cnt = len(probs)
+        arr = (gw_problem * cnt)(*probs)
+
+        def ptrs(xs):
+            if xs is None:
+                return None
+            return (ctypes.c_void_p * cnt)(*[_ptr(x) for x in xs])
+
+        keep = [ptrs(u), ptrs(v), ptrs(phi), ptrs(psi), ptrs(T), ptrs(stats)]
+        st = self.lib.gw_solve_batch(self.h, cnt, arr, *[ctypes.cast(k, ctypes.c_void_p) if k is not None else None
+                                                         for k in keep], _stream(stream))
+        return self._check(st, "gw_solve_batch")
 
     def gw_grad_dense(self, prob: gw_problem, u, v, T, G, marginals=GW_MARG_TARGET, precision=GW_DENSE_BF16,
                       stream=None) -> int:

@@ -1,6 +1,7 @@
 // C ABI entry points: context, validation, workspace, dispatch.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -9,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "gw_internal.h"
@@ -86,6 +88,15 @@ struct gw_ctx {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t solve_exec = nullptr;
   std::string solve_key;
+  // Batched solves: worker streams (fork/join inside the captured graph), the
+  // batch workspace and the last batch graph.
+  std::vector<cudaStream_t> bstreams;
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join_ev;
+  void* bws = nullptr;
+  size_t bws_bytes = 0;
+  cudaGraphExec_t batch_exec = nullptr;
+  std::string batch_key;
   gw::Tracer* tr() { return tracer; }
 };
 
@@ -189,6 +200,11 @@ void gw_ctx_destroy(gw_ctx* c) {
   if (c->status) cudaFree(c->status);
   gw::dense_state_destroy(c->dense);
   if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+  if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
+  for (auto st : c->bstreams) cudaStreamDestroy(st);
+  for (auto ev : c->join_ev) cudaEventDestroy(ev);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->bws) cudaFree(c->bws);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c->tracer;
   delete c;
@@ -376,20 +392,27 @@ gw_status gw_grad_dense(gw_ctx* c, const gw_problem* p, const double* d_u, const
   return GW_OK;
 }
 
-gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const double* d_v, const double* d_phi,
-                   const double* d_psi, void* d_T, double* d_f, double* d_g, double* d_stats, void* stream) {
-  if (!c) return GW_ERR_INVALID;
-  std::lock_guard<std::mutex> lk(c->mu);
+}  // extern "C"
+
+namespace {
+
+gw_status check_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const double* d_v, const double* d_phi,
+                      const double* d_psi, const void* d_T, const char* who) {
   gw_status s = check_grid(c, p);
   if (s != GW_OK) return s;
-  if (!finite_pos(p->eps)) return fail(c, GW_ERR_INVALID, "gw_solve: eps must be finite and > 0");
+  if (!finite_pos(p->eps)) return fail(c, GW_ERR_INVALID, "%s: eps must be finite and > 0", who);
   if (p->n_outer < 0 || p->n_inner < 1)
-    return fail(c, GW_ERR_INVALID, "gw_solve: need n_outer >= 0 and n_inner >= 1");
-  if (!(p->theta >= 0.0 && p->theta <= 1.0)) return fail(c, GW_ERR_INVALID, "gw_solve: theta must be in [0, 1]");
+    return fail(c, GW_ERR_INVALID, "%s: need n_outer >= 0 and n_inner >= 1", who);
+  if (!(p->theta >= 0.0 && p->theta <= 1.0)) return fail(c, GW_ERR_INVALID, "%s: theta must be in [0, 1]", who);
   if (p->theta != 1.0 && (p->feat_dim < 1 || p->feat_dim > 64 || !d_phi || !d_psi))
-    return fail(c, GW_ERR_INVALID, "gw_solve: fused GW (theta < 1) needs 1 <= feat_dim <= 64 and both feature arrays");
-  if (!d_u || !d_v || !d_T) return fail(c, GW_ERR_INVALID, "gw_solve: d_u, d_v and d_T must not be NULL");
-  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
+    return fail(c, GW_ERR_INVALID, "%s: fused GW (theta < 1) needs 1 <= feat_dim <= 64 and both feature arrays",
+                who);
+  if (!d_u || !d_v || !d_T) return fail(c, GW_ERR_INVALID, "%s: d_u, d_v and d_T must not be NULL", who);
+  return GW_OK;
+}
+
+gw::SolveArgs solve_args(gw_ctx* c, const gw_problem* p, const double* d_u, const double* d_v, const double* d_phi,
+                         const double* d_psi, void* d_T, double* d_f, double* d_g, double* d_stats, void* stream) {
   gw::SolveArgs a{};
   a.dim = p->dim;
   a.cost = p->cost;
@@ -419,6 +442,21 @@ gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const doub
   a.num_sms = c->num_sms;
   a.tracer = c->tr();
   a.force_generic = c->force_generic;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const double* d_v, const double* d_phi,
+                   const double* d_psi, void* d_T, double* d_f, double* d_g, double* d_stats, void* stream) {
+  if (!c) return GW_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  gw_status s = check_solve(c, p, d_u, d_v, d_phi, d_psi, d_T, "gw_solve");
+  if (s != GW_OK) return s;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
+  gw::SolveArgs a = solve_args(c, p, d_u, d_v, d_phi, d_psi, d_T, d_f, d_g, d_stats, stream);
   s = ensure_ws(c, gw::solve_workspace_bytes(a));
   if (s != GW_OK) return s;
   int rc;
@@ -465,6 +503,147 @@ gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const doub
   if (rc != GW_OK) {
     cudaError_t e = cudaGetLastError();
     return fail(c, (gw_status)rc, "gw_solve launch failed: %s", cudaGetErrorString(e));
+  }
+  c->err.clear();
+  return GW_OK;
+}
+
+gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const double* const* d_u,
+                         const double* const* d_v, const double* const* d_phi, const double* const* d_psi,
+                         void* const* d_T, double* const* d_stats, void* stream) {
+  if (!c) return GW_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (count < 0 || (count > 0 && (!probs || !d_u || !d_v || !d_T)))
+    return fail(c, GW_ERR_INVALID, "gw_solve_batch: need count >= 0 and the problem and pointer arrays");
+  if (count == 0) return GW_OK;
+  std::vector<gw::SolveArgs> args(count);
+  std::vector<size_t> off(count);
+  size_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    const double* phi = d_phi ? d_phi[i] : nullptr;
+    const double* psi = d_psi ? d_psi[i] : nullptr;
+    char who[48];
+    snprintf(who, sizeof who, "gw_solve_batch[%d]", i);
+    gw_status s = check_solve(c, &probs[i], d_u[i], d_v[i], phi, psi, d_T[i], who);
+    if (s != GW_OK) return s;
+    args[i] = solve_args(c, &probs[i], d_u[i], d_v[i], phi, psi, d_T[i], nullptr, nullptr,
+                         d_stats ? d_stats[i] : nullptr, nullptr);
+    args[i].batch = 1;
+    off[i] = total;
+    total += (gw::solve_workspace_bytes(args[i]) + 4095) / 4096 * 4096;
+  }
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
+  if (total > c->bws_bytes) {
+    if (c->bws) {
+      cudaDeviceSynchronize();
+      cudaFree(c->bws);
+      c->bws = nullptr;
+      c->bws_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&c->bws, total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, GW_ERR_OOM, "gw_solve_batch: workspace of %zu bytes: %s", total, cudaGetErrorString(e));
+    }
+    c->bws_bytes = total;
+  }
+  // Groups: problems with the same row configuration, dtype and schedule run
+  // in lock step (one launch per Sinkhorn pass for the whole group).  Groups
+  // run concurrently, each on a worker stream; a group larger than 32
+  // problems is split so that its parts also run concurrently.
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
+  for (int i = 0; i < count; ++i)
+    groups[std::make_tuple(gw::solve_group_key(args[i]), args[i].dtype, args[i].n_outer, args[i].n_inner)]
+        .push_back(i);
+  std::vector<std::vector<int>> parts;
+  for (auto& g : groups) {
+    auto& v = g.second;
+    std::stable_sort(v.begin(), v.end(), [&](int x, int y) {
+      return (double)args[x].n * args[x].m > (double)args[y].n * args[y].m;
+    });
+    for (size_t b = 0; b < v.size(); b += 32) parts.emplace_back(v.begin() + b, v.begin() + std::min(v.size(), b + 32));
+  }
+  const int S = std::min<int>((int)parts.size(), 32);
+  while ((int)c->bstreams.size() < S) {
+    cudaStream_t st;
+    cudaEvent_t ev;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(c, cudaGetLastError(), "gw_solve_batch: worker streams");
+    c->bstreams.push_back(st);
+    c->join_ev.push_back(ev);
+  }
+  if (!c->fork_ev && cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess)
+    return cuda_fail(c, cudaGetLastError(), "gw_solve_batch: fork event");
+  auto enqueue = [&](cudaStream_t origin) -> int {
+    if (cudaEventRecord(c->fork_ev, origin) != cudaSuccess) return GW_ERR_CUDA;
+    for (int k = 0; k < S; ++k)
+      if (cudaStreamWaitEvent(c->bstreams[k], c->fork_ev, 0) != cudaSuccess) return GW_ERR_CUDA;
+    for (size_t g = 0; g < parts.size(); ++g) {
+      std::vector<gw::SolveArgs> ga;
+      std::vector<const gw::SolveArgs*> gp;
+      std::vector<void*> gws;
+      std::vector<size_t> gb;
+      for (int i : parts[g]) {
+        ga.push_back(args[i]);
+        gws.push_back((char*)c->bws + off[i]);
+        gb.push_back(gw::solve_workspace_bytes(args[i]));
+      }
+      for (auto& a : ga) gp.push_back(&a);
+      int rc = gw::solve_group_launch(gp.data(), gws.data(), gb.data(), (int)gp.size(), c->bstreams[g % S]);
+      if (rc != GW_OK) return rc;
+    }
+    for (int k = 0; k < S; ++k) {
+      if (cudaEventRecord(c->join_ev[k], c->bstreams[k]) != cudaSuccess) return GW_ERR_CUDA;
+      if (cudaStreamWaitEvent(origin, c->join_ev[k], 0) != cudaSuccess) return GW_ERR_CUDA;
+    }
+    return GW_OK;
+  };
+  int rc;
+  if (c->tracer) {
+    rc = enqueue((cudaStream_t)stream);
+  } else {
+    std::string key;
+    char buf[512];
+    snprintf(buf, sizeof buf, "%d %p %zu|", count, c->bws, c->bws_bytes);
+    key += buf;
+    for (int i = 0; i < count; ++i) {
+      const gw::SolveArgs& a = args[i];
+      snprintf(buf, sizeof buf, "%d %d %d %d %d %d %.17g %.17g %.17g %.17g %d %d %d %p %p %p %p %p %p|", a.dim,
+               a.cost, a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.theta, a.n_outer, a.n_inner, a.feat_dim,
+               (void*)a.u, (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.stats);
+      key += buf;
+    }
+    if (!c->batch_exec || c->batch_key != key) {
+      if (c->batch_exec) {
+        cudaGraphExecDestroy(c->batch_exec);
+        c->batch_exec = nullptr;
+      }
+      if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "capture stream");
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+      rc = enqueue(c->cap);
+      e = cudaStreamEndCapture(c->cap, &graph);
+      if (rc != GW_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(c, rc != GW_OK ? (gw_status)rc : GW_ERR_CUDA, "gw_solve_batch capture failed");
+      }
+      e = cudaGraphInstantiate(&c->batch_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        c->batch_exec = nullptr;
+        return cuda_fail(c, e, "batch graph instantiate");
+      }
+      c->batch_key = key;
+    }
+    rc = cudaGraphLaunch(c->batch_exec, (cudaStream_t)stream) == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+  }
+  if (rc != GW_OK) {
+    cudaError_t e = cudaGetLastError();
+    return fail(c, (gw_status)rc, "gw_solve_batch launch failed: %s", cudaGetErrorString(e));
   }
   c->err.clear();
   return GW_OK;

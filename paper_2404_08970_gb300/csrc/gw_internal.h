@@ -156,9 +156,16 @@ struct SolveArgs {
   int num_sms;
   Tracer* tracer;
   int force_generic;
+  int batch;  // 1: part of a batch (row bands of at least 32 rows)
 };
 
 size_t solve_workspace_bytes(const SolveArgs& a);
 int solve_launch(const SolveArgs& a, void* ws, size_t ws_bytes);
+// Batched solves: problems with equal solve_group_key, dtype and schedule
+// (n_outer, n_inner) form a group that solve_group_launch advances in lock
+// step on one stream (each Sinkhorn pass one launch per 32 problems).
+int solve_group_key(const SolveArgs& a);
+int solve_group_launch(const SolveArgs* const* a, void* const* ws, const size_t* ws_bytes, int count,
+                       cudaStream_t stream);
 
 }  // namespace gw

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "gw_common.cuh"
 #include "gw_internal.h"
@@ -87,8 +88,8 @@ template <> __device__ __forceinline__ double tiny_sum<double>() { return 1e-250
 
 // ---------------------------------------------------------------------------
 // Shared-memory layout of the row-streaming kernels (1024-aligned base):
-//   ring [stages][slot_bytes] | G (swizzled, vec_bytes) | red [2][NW] Real |
-//   Fband [Rmax] Real | bars [stages]
+//   ring [stages][slot_bytes] | G (swizzled, vec_bytes) | red [2][2][NW] Real |
+//   Fband, Fold, LU [Rmax] Real | bars [stages]
 // ---------------------------------------------------------------------------
 struct RowGeom {
   int slot_bytes, vec_bytes, stages, use_tma, box_cols;
@@ -96,7 +97,7 @@ struct RowGeom {
 
 template <int NW, typename Real>
 size_t rows_smem_bytes(const RowGeom& g, int Rmax) {
-  return 1024 + (size_t)g.stages * g.slot_bytes + g.vec_bytes + sizeof(Real) * (2 * NW + 3 * Rmax) + 16 +
+  return 1024 + (size_t)g.stages * g.slot_bytes + g.vec_bytes + sizeof(Real) * (4 * NW + 3 * Rmax) + 16 +
          8 * (size_t)g.stages + 64;
 }
 
@@ -130,6 +131,40 @@ struct RowRing {
     return dst;
   }
 };
+
+// One problem of a (possibly batched) launch: its cost matrix, potentials,
+// outputs and row-band layout.  Launches take up to MAXP of these as one
+// __grid_constant__ parameter block (the tensor maps stay in parameter space,
+// where the TMA unit reads them); blocks are numbered across the problems.
+template <typename Real>
+struct SkProb {
+  CUtensorMap tm;  // rows of Pi (64-byte aligned)
+  RowGeom geo;
+  const Real* Pi;
+  const Real* lu;  // log2 u
+  const Real* lv;  // log2 v
+  Real* F;
+  Real* G;
+  Real* part;           // [B][m] column partials of one Sinkhorn pass
+  Real* T;              // plan output
+  const double* u;      // row targets (plan statistics)
+  double* colpart;      // [B][m] plan column sums
+  double* cta_stats;    // [B][2] entropy and row-error partials
+  int n, m, R, B;
+  Real c;
+};
+template <typename Real, int MAXP>
+struct SkBatch {
+  SkProb<Real> p[MAXP];
+  int block0[MAXP + 1];  // first block of each problem; block0[count] = grid size
+  int count;
+};
+template <typename Real, int MAXP>
+__device__ __forceinline__ int batch_problem(const SkBatch<Real, MAXP>& P) {
+  int pi = 0;
+  while (pi + 1 < P.count && (int)blockIdx.x >= P.block0[pi + 1]) ++pi;
+  return pi;
+}
 
 __device__ __forceinline__ float u_or_exp(float lu) { return exp2f(lu); }
 __device__ __forceinline__ double u_or_exp(double lu) { return exp2(lu); }
@@ -180,29 +215,36 @@ __device__ __forceinline__ void row_fallback(RowRing<Real>& rr, int tl, int NT, 
 // ---------------------------------------------------------------------------
 // sk_pass
 // ---------------------------------------------------------------------------
-template <int NW, int VPT, typename Real>
-__global__ void __launch_bounds__(32 * NW, 1)
-    sk_pass(const __grid_constant__ CUtensorMap tmP, const Real* __restrict__ Pi, int n, int m, int R, Real c,
-            const Real* __restrict__ lu, Real* __restrict__ F, const Real* __restrict__ Gp, Real* __restrict__ part,
-            RowGeom geo, unsigned* status) {
+template <int NW, int VPT, typename Real, int MAXP>
+__global__ void __launch_bounds__(32 * NW, 1) sk_pass(const __grid_constant__ SkBatch<Real, MAXP> P, unsigned* status) {
   constexpr int NT = 32 * NW;
+  const int pi = batch_problem(P);
+  const SkProb<Real>& pr = P.p[pi];
+  const RowGeom geo = pr.geo;
+  const Real* __restrict__ Pi = pr.Pi;
+  const Real* __restrict__ lu = pr.lu;
+  Real* __restrict__ F = pr.F;
+  const Real* __restrict__ Gp = pr.G;
+  Real* __restrict__ part = pr.part;
+  const int n = pr.n, m = pr.m, R = pr.R;
+  const Real c = pr.c;
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   unsigned char* sm = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
   unsigned char* ring = sm;
   unsigned char* Gs = ring + (size_t)geo.stages * geo.slot_bytes;
-  Real* red = reinterpret_cast<Real*>(Gs + geo.vec_bytes);  // [2][NW]
-  Real* Fband = red + 2 * NW;  // new potentials of the band's rows
+  Real* red = reinterpret_cast<Real*>(Gs + geo.vec_bytes);  // [2][2][NW]
+  Real* Fband = red + 4 * NW;  // new potentials of the band's rows
   Real* Fold = Fband + R;      // previous potentials of the band's rows
   Real* LU = Fold + R;         // log2 u of the band's rows
   unsigned char* braw = reinterpret_cast<unsigned char*>(LU + R);
   uint64_t* bars = reinterpret_cast<uint64_t*>(braw + ((8u - (smem_u32(braw) & 7u)) & 7u));
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int a = blockIdx.x, s = a * R, Ra = min(R, n - s);
+  const int a = (int)blockIdx.x - P.block0[pi], s = a * R, Ra = min(R, n - s);
   const int c0 = tid * VPT;
   const int m_pad = geo.vec_bytes / (int)sizeof(Real);
 
-  RowRing<Real> rr{ring, bars, geo.stages, geo.slot_bytes, geo.use_tma, geo.box_cols, &tmP, Pi, m, s, Ra};
+  RowRing<Real> rr{ring, bars, geo.stages, geo.slot_bytes, geo.use_tma, geo.box_cols, &pr.tm, Pi, m, s, Ra};
   if (geo.use_tma && tid == 0) {
     for (int st = 0; st < geo.stages; ++st) mbar_init(&bars[st], 1);
     fence_mbar_init();
@@ -233,70 +275,100 @@ __global__ void __launch_bounds__(32 * NW, 1)
   // Row j: w_j,p = 2^(F_old,j + G_p - c Pi_jp) (every w <= v_p after a column
   // update), S_j = sum_p w_j,p.  The new potential is F_j + log2(u_j / S_j) and
   // the column sums need 2^(F_new,j + G_p - c Pi_jp) = (u_j / S_j) w_j,p, so one
-  // exp2 per element serves both halves.  Row j's column update runs after the
-  // row pass of row j + 1, so each block barrier has work on both sides.
-  Real wcur[VPT], wprev[VPT];
-#pragma unroll
-  for (int v = 0; v < VPT; ++v) wprev[v] = 0;
-  Real Fo_prev = 0;
-  for (int j = 0; j <= Ra; ++j) {
-    if (j < Ra) {
-      const unsigned char* xr = rr.get(j, NT, status);
-      Real x[VPT];
-      lds_swz<Real, VPT>(xr, c0, x);
-      const Real Fo = Fold[j];
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) wcur[v] = ex2(fma(-c, x[v], Gv[v] + Fo));
-      Real sum = tree_sum<VPT>(wcur);
-      sum = warp_sum(sum);
-      if (lane == 0) red[(j & 1) * NW + warp] = sum;
-      if (j >= 1) {
-        // Column update of row j - 1 (its row sum was posted before the last barrier).
-        const Real S = tree_sum_smem<NW>(red + ((j - 1) & 1) * NW);
-        const int ip = s + j - 1;
-        const Real lui = LU[j - 1];
-        if (S >= tiny_sum<Real>() && S <= (Real)1e30) {
-          const Real r = (Real)u_or_exp(lui) / S;
-#pragma unroll
-          for (int v = 0; v < VPT; ++v) acc[v] = fma(r, wprev[v], acc[v]);
-          if (tid == 0) {
-            const Real Fn = Fo_prev + lui - lg2(S);
-            F[ip] = Fn;
-            Fband[j - 1] = Fn;
-          }
-        } else {
-          row_fallback(rr, j - 1, NT, status, c, x, Gv, Fo_prev, lui, acc, F, Fband, ip, sfb, lane, warp, tid);
-        }
-      }
-      Fo_prev = Fo;
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) wprev[v] = wcur[v];
-    } else {
-      // Last row's column update.
-      const Real S = tree_sum_smem<NW>(red + ((j - 1) & 1) * NW);
-      const int ip = s + j - 1;
-      const Real lui = LU[j - 1];
-      Real x[VPT];
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) x[v] = 0;
-      if (S >= tiny_sum<Real>() && S <= (Real)1e30) {
-        const Real r = (Real)u_or_exp(lui) / S;
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) acc[v] = fma(r, wprev[v], acc[v]);
-        if (tid == 0) {
-          const Real Fn = Fo_prev + lui - lg2(S);
-          F[ip] = Fn;
-          Fband[j - 1] = Fn;
-        }
+  // exp2 per element serves both halves.  Rows go two at a time: both row
+  // passes, one block barrier for both row sums, both column updates.
+  for (int j = 0; j < Ra; j += 2) {
+    const bool two = j + 1 < Ra;
+    Real w0[VPT], w1[VPT];
+    const Real Fo0 = Fold[j], Fo1 = two ? Fold[j + 1] : (Real)0;
+    {
+      Real x0[VPT], x1[VPT];
+      lds_swz<Real, VPT>(rr.get(j, NT, status), c0, x0);
+      if (two) {
+        lds_swz<Real, VPT>(rr.get(j + 1, NT, status), c0, x1);
       } else {
-        row_fallback(rr, j - 1, NT, status, c, x, Gv, Fo_prev, lui, acc, F, Fband, ip, sfb, lane, warp, tid);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) x1[v] = 0;
+      }
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) {
+        w0[v] = ex2(fma(-c, x0[v], Gv[v] + Fo0));
+        w1[v] = two ? ex2(fma(-c, x1[v], Gv[v] + Fo1)) : (Real)0;
       }
     }
+    Real s0 = tree_sum<VPT>(w0), s1 = tree_sum<VPT>(w1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    Real* rb = red + ((j >> 1) & 1) * 2 * NW;  // [2 rows][NW], double-buffered by pair
+    if (lane == 0) {
+      rb[warp] = s0;
+      rb[NW + warp] = s1;
+    }
     __syncthreads();
-    // Rows <= j - 1 are done with their slots: refill the slot of row j - 1.
-    if (geo.use_tma && tid == 0 && j >= 1 && (j - 1) + geo.stages < Ra) {
-      fence_proxy_async_smem();
-      rr.issue(j - 1 + geo.stages);
+    const Real S0 = tree_sum_smem<NW>(rb), S1 = two ? tree_sum_smem<NW>(rb + NW) : (Real)1;
+    const bool ok0 = S0 >= tiny_sum<Real>() && S0 <= (Real)1e30;
+    const bool ok1 = S1 >= tiny_sum<Real>() && S1 <= (Real)1e30;
+    // Rows j, j + 1 are read: refill their slots now unless a row must be
+    // redone from its slot.
+    const bool refill_now = ok0 && ok1;
+    auto refill = [&]() {
+      if (geo.use_tma && tid == 0) {
+        fence_proxy_async_smem();
+        if (j + geo.stages < Ra) rr.issue(j + geo.stages);
+        if (j + 1 + geo.stages < Ra) rr.issue(j + 1 + geo.stages);
+      }
+    };
+    if (refill_now) refill();
+    const Real lu0 = LU[j], lu1 = two ? LU[j + 1] : (Real)0;
+    if (ok0 && ok1) {
+      const Real r0 = (Real)u_or_exp(lu0) / S0;
+      const Real r1 = two ? (Real)u_or_exp(lu1) / S1 : (Real)0;
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) acc[v] = fma(r1, w1[v], fma(r0, w0[v], acc[v]));
+      if (tid == 0) {
+        const Real Fn0 = Fo0 + lu0 - lg2(S0);
+        F[s + j] = Fn0;
+        Fband[j] = Fn0;
+        if (two) {
+          const Real Fn1 = Fo1 + lu1 - lg2(S1);
+          F[s + j + 1] = Fn1;
+          Fband[j + 1] = Fn1;
+        }
+      }
+    } else {
+      // Block-uniform: a row sum out of range is redone with a max shift.
+      Real x[VPT];
+      if (ok0) {
+        const Real r0 = (Real)u_or_exp(lu0) / S0;
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) acc[v] = fma(r0, w0[v], acc[v]);
+        if (tid == 0) {
+          const Real Fn0 = Fo0 + lu0 - lg2(S0);
+          F[s + j] = Fn0;
+          Fband[j] = Fn0;
+        }
+      } else {
+        row_fallback(rr, j, NT, status, c, x, Gv, Fo0, lu0, acc, F, Fband, s + j, sfb, lane, warp, tid);
+      }
+      if (two) {
+        if (ok1) {
+          const Real r1 = (Real)u_or_exp(lu1) / S1;
+#pragma unroll
+          for (int v = 0; v < VPT; ++v) acc[v] = fma(r1, w1[v], acc[v]);
+          if (tid == 0) {
+            const Real Fn1 = Fo1 + lu1 - lg2(S1);
+            F[s + j + 1] = Fn1;
+            Fband[j + 1] = Fn1;
+          }
+        } else {
+          row_fallback(rr, j + 1, NT, status, c, x, Gv, Fo1, lu1, acc, F, Fband, s + j + 1, sfb, lane, warp, tid);
+        }
+      }
+      __syncthreads();
+      refill();
     }
   }
   // Band partials of the column sums (relative to the current G).
@@ -310,14 +382,21 @@ __global__ void __launch_bounds__(32 * NW, 1)
 // columns.  If any of them has S_p out of range, the block recomputes its 32
 // columns from Pi and the new F with a running max (8 warps over the rows,
 // one lane per column).
-template <typename Real>
-__global__ void __launch_bounds__(256) sk_cols(const Real* __restrict__ part, int B, int n, int m,
-                                               const Real* __restrict__ lv, Real* __restrict__ G,
-                                               const Real* __restrict__ Pi, const Real* __restrict__ F, Real c) {
+template <typename Real, int MAXP>
+__global__ void __launch_bounds__(256) sk_cols(const __grid_constant__ SkBatch<Real, MAXP> P) {
+  const int pi = batch_problem(P);
+  const SkProb<Real>& pr = P.p[pi];
+  const Real* __restrict__ part = pr.part;
+  const Real* __restrict__ lv = pr.lv;
+  Real* __restrict__ G = pr.G;
+  const Real* __restrict__ Pi = pr.Pi;
+  const Real* __restrict__ F = pr.F;
+  const int B = pr.B, n = pr.n, m = pr.m;
+  const Real c = pr.c;
   __shared__ double sS[8][32];
   __shared__ Real sM[8][32];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  const int p = blockIdx.x * 32 + lane;
+  const int p = ((int)blockIdx.x - P.block0[pi]) * 32 + lane;
   const int per = (B + 7) / 8;
   const int b0 = min(B, grp * per), b1 = min(B, b0 + per);
   Real S = 0, C = 0;
@@ -383,13 +462,21 @@ __global__ void __launch_bounds__(256) sk_cols(const Real* __restrict__ part, in
 // partial sum_ip T (ln T - 1), the row-marginal error sum_i |T_i. - u_i| and
 // the band's column sums.
 // ---------------------------------------------------------------------------
-template <int NW, int VPT, typename Real>
-__global__ void __launch_bounds__(32 * NW, 1)
-    sk_plan(const __grid_constant__ CUtensorMap tmP, const Real* __restrict__ Pi, int n, int m, int R, Real c,
-            const Real* __restrict__ F, const Real* __restrict__ Gp, const double* __restrict__ u,
-            Real* __restrict__ T, double* __restrict__ colpart, double* __restrict__ cta_stats, RowGeom geo,
-            unsigned* status) {
+template <int NW, int VPT, typename Real, int MAXP>
+__global__ void __launch_bounds__(32 * NW, 1) sk_plan(const __grid_constant__ SkBatch<Real, MAXP> P, unsigned* status) {
   constexpr int NT = 32 * NW;
+  const int pi = batch_problem(P);
+  const SkProb<Real>& pr = P.p[pi];
+  const RowGeom geo = pr.geo;
+  const Real* __restrict__ Pi = pr.Pi;
+  const Real* __restrict__ F = pr.F;
+  const Real* __restrict__ Gp = pr.G;
+  const double* __restrict__ u = pr.u;
+  Real* __restrict__ T = pr.T;
+  double* __restrict__ colpart = pr.colpart;
+  double* __restrict__ cta_stats = pr.cta_stats;
+  const int n = pr.n, m = pr.m, R = pr.R;
+  const Real c = pr.c;
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   unsigned char* sm = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
   unsigned char* ring = sm;
@@ -401,10 +488,10 @@ __global__ void __launch_bounds__(32 * NW, 1)
   __shared__ double dred[2][32];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int a = blockIdx.x, s = a * R, Ra = min(R, n - s);
+  const int a = (int)blockIdx.x - P.block0[pi], s = a * R, Ra = min(R, n - s);
   const int c0 = tid * VPT;
   const int m_pad = geo.vec_bytes / (int)sizeof(Real);
-  RowRing<Real> rr{ring, bars, geo.stages, geo.slot_bytes, geo.use_tma, geo.box_cols, &tmP, Pi, m, s, Ra};
+  RowRing<Real> rr{ring, bars, geo.stages, geo.slot_bytes, geo.use_tma, geo.box_cols, &pr.tm, Pi, m, s, Ra};
   if (geo.use_tma && tid == 0) {
     for (int st = 0; st < geo.stages; ++st) mbar_init(&bars[st], 1);
     fence_mbar_init();
@@ -617,13 +704,33 @@ RowGeom row_geom(const void* Pi, int n, int m, CUtensorMap* tm, int Rmax) {
   return g;
 }
 
+// Row bands of the Sinkhorn kernels.  A single solve spreads its rows over
+// all SMs; in a batch, problems share the GPU, so bands are at least 32 rows
+// (fewer blocks and fewer column partials per problem).
+Bands solve_bands(const SolveArgs& A) {
+  if (!A.batch) return choose_bands(A.n, A.num_sms);
+  const int target = std::max(1, std::min(A.num_sms, A.n / 32));
+  return choose_bands(A.n, target);
+}
+
+constexpr int kDots = 256;
+
+// One problem's state inside its workspace:
+//   Pi | F | G | lu | lv | part | colpart | cta_stats | dots | gradient workspace
+template <typename Real>
+struct SolveState {
+  const SolveArgs* A;
+  SkProb<Real> sk;
+  double *dotE, *dotC;
+  char* gws;
+  size_t gws_bytes;
+  size_t smem;
+};
+
 template <int NW, int VPT, typename Real>
-int solve_typed(const SolveArgs& A, void* wsv, size_t ws_bytes) {
+int prepare(const SolveArgs& A, void* wsv, size_t ws_bytes, SolveState<Real>* S) {
   const int n = A.n, m = A.m;
-  cudaStream_t st = A.stream;
-  const Bands bands = choose_bands(n, A.num_sms);
-  const int B = bands.B, R = bands.R;
-  // Workspace: Pi | F | G | lu | lv | part | colpart | cta_stats | dots | gradient workspace
+  const Bands bands = solve_bands(A);
   char* ws = (char*)wsv;
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -631,132 +738,263 @@ int solve_typed(const SolveArgs& A, void* wsv, size_t ws_bytes) {
     off = (off + bytes + 255) / 256 * 256;
     return p;
   };
-  Real* Pi = (Real*)take((size_t)n * m * sizeof(Real));
-  Real* F = (Real*)take((size_t)n * sizeof(Real));
-  Real* G = (Real*)take((size_t)m * sizeof(Real));
-  Real* lu = (Real*)take((size_t)n * sizeof(Real));
-  Real* lv = (Real*)take((size_t)m * sizeof(Real));
-  Real* part = (Real*)take((size_t)B * m * sizeof(Real));
-  double* colpart = (double*)take((size_t)B * m * sizeof(double));
-  double* cta_stats = (double*)take((size_t)2 * B * sizeof(double));
-  const int ndot = 256;
-  double* dotE = (double*)take((size_t)ndot * sizeof(double));
-  double* dotC = (double*)take((size_t)ndot * sizeof(double));
-  char* gws = take(0);
+  SkProb<Real>& k = S->sk;
+  memset(&k, 0, sizeof(k));
+  k.n = n;
+  k.m = m;
+  k.B = bands.B;
+  k.R = bands.R;
+  k.c = (Real)(1.4426950408889634 / A.eps);
+  k.Pi = (Real*)take((size_t)n * m * sizeof(Real));
+  k.F = (Real*)take((size_t)n * sizeof(Real));
+  k.G = (Real*)take((size_t)m * sizeof(Real));
+  k.lu = (Real*)take((size_t)n * sizeof(Real));
+  k.lv = (Real*)take((size_t)m * sizeof(Real));
+  k.part = (Real*)take((size_t)bands.B * m * sizeof(Real));
+  k.colpart = (double*)take((size_t)bands.B * m * sizeof(double));
+  k.cta_stats = (double*)take((size_t)2 * bands.B * sizeof(double));
+  S->dotE = (double*)take((size_t)kDots * sizeof(double));
+  S->dotC = (double*)take((size_t)kDots * sizeof(double));
+  S->gws = take(0);
   if (off > ws_bytes) return GW_ERR_OOM;
-  const size_t gws_bytes = ws_bytes - off;
+  S->gws_bytes = ws_bytes - off;
+  k.T = (Real*)A.T;
+  k.u = A.u;
+  k.geo = row_geom<NW, VPT, Real>(k.Pi, n, m, &k.tm, k.R);
+  S->smem = rows_smem_bytes<NW, Real>(k.geo, k.R);
+  S->A = &A;
+  return GW_OK;
+}
 
-  const Real c = (Real)(1.4426950408889634 / A.eps);
-  CUtensorMap tm;
-  const RowGeom geo = row_geom<NW, VPT, Real>(Pi, n, m, &tm, R);
-  const size_t smem = rows_smem_bytes<NW, Real>(geo, R);
-  if (cudaFuncSetAttribute(sk_pass<NW, VPT, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(sk_plan<NW, VPT, Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-          cudaSuccess)
-    return GW_ERR_CUDA;
-
-  {
-    TraceScope ts(A.tracer, "solve_setup", st);
-    log2_scaled<Real><<<(n + 255) / 256, 256, 0, st>>>(A.u, n, lu);
-    log2_scaled<Real><<<(m + 255) / 256, 256, 0, st>>>(A.v, m, lv);
-    fill_product<Real><<<4 * A.num_sms, 256, 0, st>>>(A.u, A.v, n, m, (Real*)A.T);
+// Pi = out_scale * G(T) with target marginals (out_scale = 2 theta), or,
+// for the value, G(T) with T's own marginals.
+template <typename Real>
+int gradient(const SolveState<Real>& S, int exact, double out_scale, cudaStream_t st) {
+  const SolveArgs& A = *S.A;
+  if (A.dim == 2) {
+    Grad2DArgs g2{};
+    g2.sx = A.nx;
+    g2.sy = A.ny;
+    g2.cost = A.cost;
+    g2.hx = A.hx;
+    g2.hy = A.hy;
+    g2.dtype = A.dtype;
+    g2.T = A.T;
+    g2.G = (void*)S.sk.Pi;
+    g2.u = A.u;
+    g2.v = A.v;
+    g2.exact = exact;
+    g2.out_scale = out_scale;
+    g2.stream = st;
+    g2.status = A.status;
+    g2.num_sms = A.num_sms;
+    g2.tracer = A.tracer;
+    return grad2d_launch(g2, S.gws, S.gws_bytes);
   }
-  // Pi = out_scale * G(T) with target marginals (out_scale = 2 theta), or,
-  // for the value, G(T) with T's own marginals.
-  auto gradient = [&](int exact, double out_scale) -> int {
-    if (A.dim == 2) {
-      Grad2DArgs g2{};
-      g2.sx = A.nx;
-      g2.sy = A.ny;
-      g2.cost = A.cost;
-      g2.hx = A.hx;
-      g2.hy = A.hy;
-      g2.dtype = A.dtype;
-      g2.T = A.T;
-      g2.G = Pi;
-      g2.u = A.u;
-      g2.v = A.v;
-      g2.exact = exact;
-      g2.out_scale = out_scale;
-      g2.stream = st;
-      g2.status = A.status;
-      g2.num_sms = A.num_sms;
-      g2.tracer = A.tracer;
-      return grad2d_launch(g2, gws, gws_bytes);
-    }
-    Grad1DArgs ga{};
-    ga.n = n;
-    ga.m = m;
-    ga.k = A.k;
-    ga.hx = A.hx;
-    ga.hy = A.hy;
-    ga.dtype = A.dtype;
-    ga.T = A.T;
-    ga.G = Pi;
-    ga.u = A.u;
-    ga.v = A.v;
-    ga.exact = exact;
-    ga.out_scale = out_scale;
-    ga.stream = st;
-    ga.status = A.status;
-    ga.num_sms = A.num_sms;
-    ga.tracer = A.tracer;
-    ga.force_generic = A.force_generic;
-    return grad1d_launch(ga, gws, gws_bytes);
-  };
-  const bool fgw = A.theta != 1.0 && A.feat_dim > 0 && A.phi && A.psi;
+  Grad1DArgs ga{};
+  ga.n = A.n;
+  ga.m = A.m;
+  ga.k = A.k;
+  ga.hx = A.hx;
+  ga.hy = A.hy;
+  ga.dtype = A.dtype;
+  ga.T = A.T;
+  ga.G = (void*)S.sk.Pi;
+  ga.u = A.u;
+  ga.v = A.v;
+  ga.exact = exact;
+  ga.out_scale = out_scale;
+  ga.stream = st;
+  ga.status = A.status;
+  ga.num_sms = A.num_sms;
+  ga.tracer = A.tracer;
+  ga.force_generic = A.force_generic;
+  return grad1d_launch(ga, S.gws, S.gws_bytes);
+}
 
-  for (int l = 0; l < A.n_outer; ++l) {
-    int rc = gradient(0, 2.0 * A.theta);
-    if (rc != GW_OK) return rc;
-    if (fgw) {
-      TraceScope ts(A.tracer, "add_feature_cost", st);
-      add_feature_cost<Real><<<n, 256, 0, st>>>(Pi, n, m, A.feat_dim, A.phi, A.psi, 1.0 - A.theta);
-    }
-    {
-      TraceScope ts(A.tracer, "solve_setup", st);
-      fill_val<Real><<<(n + 255) / 256, 256, 0, st>>>(F, n, (Real)0);
-      fill_val<Real><<<(m + 255) / 256, 256, 0, st>>>(G, m, (Real)0);
-    }
-    for (int it = 0; it < A.n_inner; ++it) {
-      {
-        TraceScope ts(A.tracer, "sk_pass", st);
-        sk_pass<NW, VPT, Real><<<B, 32 * NW, smem, st>>>(tm, Pi, n, m, R, c, lu, F, G, part, geo, A.status);
-      }
-      {
-        TraceScope ts(A.tracer, "sk_cols", st);
-        sk_cols<Real><<<(m + 31) / 32, 256, 0, st>>>(part, B, n, m, lv, G, Pi, F, c);
-      }
-    }
-    {
-      TraceScope ts(A.tracer, "sk_plan", st);
-      sk_plan<NW, VPT, Real><<<B, 32 * NW, smem, st>>>(tm, Pi, n, m, R, c, F, G, A.u, (Real*)A.T, colpart,
-                                                       cta_stats, geo, A.status);
-    }
+template <typename Real>
+bool fused(const SolveArgs& A) {
+  return A.theta != 1.0 && A.feat_dim > 0 && A.phi && A.psi;
+}
+
+// T^0 = u v^T and the log-marginals.
+template <typename Real>
+void step_setup(const SolveState<Real>& S, cudaStream_t st) {
+  const SolveArgs& A = *S.A;
+  TraceScope ts(A.tracer, "solve_setup", st);
+  log2_scaled<Real><<<(A.n + 255) / 256, 256, 0, st>>>(A.u, A.n, (Real*)S.sk.lu);
+  log2_scaled<Real><<<(A.m + 255) / 256, 256, 0, st>>>(A.v, A.m, (Real*)S.sk.lv);
+  fill_product<Real><<<4 * A.num_sms, 256, 0, st>>>(A.u, A.v, A.n, A.m, (Real*)A.T);
+}
+
+// Pi for one mirror-descent step, then f = g = 0.
+template <typename Real>
+int step_cost(const SolveState<Real>& S, cudaStream_t st) {
+  const SolveArgs& A = *S.A;
+  int rc = gradient(S, 0, 2.0 * A.theta, st);
+  if (rc != GW_OK) return rc;
+  if (fused<Real>(A)) {
+    TraceScope ts(A.tracer, "add_feature_cost", st);
+    add_feature_cost<Real><<<A.n, 256, 0, st>>>((Real*)S.sk.Pi, A.n, A.m, A.feat_dim, A.phi, A.psi, 1.0 - A.theta);
   }
-  if (A.f) potentials_out<Real><<<(n + 255) / 256, 256, 0, st>>>(F, n, A.eps / 1.4426950408889634, A.f);
-  if (A.g) potentials_out<Real><<<(m + 255) / 256, 256, 0, st>>>(G, m, A.eps / 1.4426950408889634, A.g);
-  if (A.stats) {
-    TraceScope ts(A.tracer, "solve_stats", st);
-    // E(T) = <G(T; T's marginals), T>; the gradient overwrites Pi.
-    int rc = gradient(1, 1.0);
-    if (rc != GW_OK) return rc;
-    dot_partial<Real><<<ndot, 256, 0, st>>>(Pi, (const Real*)A.T, (size_t)n * m, dotE);
-    if (fgw)
-      feature_dot_partial<Real><<<ndot, 256, 0, st>>>((const Real*)A.T, n, m, A.feat_dim, A.phi, A.psi, dotC);
-    else
-      fill_val<double><<<1, 256, 0, st>>>(dotC, ndot, 0.0);
-    finish_stats<<<1, 256, 0, st>>>(dotE, ndot, dotC, ndot, cta_stats, B, colpart, m, A.v, A.eps, A.theta,
-                                    A.n_outer, A.stats);
+  TraceScope ts(A.tracer, "solve_setup", st);
+  fill_val<Real><<<(A.n + 255) / 256, 256, 0, st>>>(S.sk.F, A.n, (Real)0);
+  fill_val<Real><<<(A.m + 255) / 256, 256, 0, st>>>(S.sk.G, A.m, (Real)0);
+  return GW_OK;
+}
+
+// Potentials out and the statistics of the final plan.
+template <typename Real>
+int step_finish(const SolveState<Real>& S, cudaStream_t st) {
+  const SolveArgs& A = *S.A;
+  const int n = A.n, m = A.m;
+  if (A.f) potentials_out<Real><<<(n + 255) / 256, 256, 0, st>>>(S.sk.F, n, A.eps / 1.4426950408889634, A.f);
+  if (A.g) potentials_out<Real><<<(m + 255) / 256, 256, 0, st>>>(S.sk.G, m, A.eps / 1.4426950408889634, A.g);
+  if (!A.stats) return GW_OK;
+  TraceScope ts(A.tracer, "solve_stats", st);
+  // E(T) = <G(T; T's marginals), T>; the gradient overwrites Pi.
+  int rc = gradient(S, 1, 1.0, st);
+  if (rc != GW_OK) return rc;
+  dot_partial<Real><<<kDots, 256, 0, st>>>(S.sk.Pi, (const Real*)A.T, (size_t)n * m, S.dotE);
+  if (fused<Real>(A))
+    feature_dot_partial<Real><<<kDots, 256, 0, st>>>((const Real*)A.T, n, m, A.feat_dim, A.phi, A.psi, S.dotC);
+  else
+    fill_val<double><<<1, 256, 0, st>>>(S.dotC, kDots, 0.0);
+  finish_stats<<<1, 256, 0, st>>>(S.dotE, kDots, S.dotC, kDots, S.sk.cta_stats, S.sk.B, S.sk.colpart, m, A.v, A.eps,
+                                  A.theta, A.n_outer, A.stats);
+  return GW_OK;
+}
+
+// Launches one Sinkhorn pass (rows, then columns), or the plan, over a list
+// of problems in parameter blocks of up to MAXP problems each.
+template <int NW, int VPT, typename Real, int MAXP>
+int launch_rows(SolveState<Real>* const* S, int count, bool plan, cudaStream_t st, unsigned* status,
+                Tracer* tracer) {
+  for (int base = 0; base < count; base += MAXP) {
+    const int cnt = std::min(MAXP, count - base);
+    SkBatch<Real, MAXP> P;
+    memset(&P, 0, sizeof(P));
+    P.count = cnt;
+    size_t smem = 0;
+    int blocks = 0;
+    for (int q = 0; q < cnt; ++q) {
+      P.p[q] = S[base + q]->sk;
+      P.block0[q] = blocks;
+      blocks += P.p[q].B;
+      smem = std::max(smem, S[base + q]->smem);
+    }
+    P.block0[cnt] = blocks;
+    auto kern = plan ? sk_plan<NW, VPT, Real, MAXP> : sk_pass<NW, VPT, Real, MAXP>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return GW_ERR_CUDA;
+    {
+      TraceScope ts(tracer, plan ? "sk_plan" : "sk_pass", st);
+      kern<<<blocks, 32 * NW, smem, st>>>(P, status);
+    }
+    if (plan) continue;
+    // Column update: blocks of 32 columns.
+    blocks = 0;
+    for (int q = 0; q < cnt; ++q) {
+      P.block0[q] = blocks;
+      blocks += (P.p[q].m + 31) / 32;
+    }
+    P.block0[cnt] = blocks;
+    TraceScope ts(tracer, "sk_cols", st);
+    sk_cols<Real, MAXP><<<blocks, 256, 0, st>>>(P);
   }
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+}
+
+template <int NW, int VPT, typename Real>
+int solve_typed(const SolveArgs& A, void* ws, size_t ws_bytes) {
+  cudaStream_t st = A.stream;
+  SolveState<Real> S;
+  int rc = prepare<NW, VPT, Real>(A, ws, ws_bytes, &S);
+  if (rc != GW_OK) return rc;
+  SolveState<Real>* list[1] = {&S};
+  step_setup(S, st);
+  for (int l = 0; l < A.n_outer; ++l) {
+    rc = step_cost(S, st);
+    if (rc != GW_OK) return rc;
+    for (int it = 0; it < A.n_inner; ++it) {
+      rc = launch_rows<NW, VPT, Real, 1>(list, 1, false, st, A.status, A.tracer);
+      if (rc != GW_OK) return rc;
+    }
+    rc = launch_rows<NW, VPT, Real, 1>(list, 1, true, st, A.status, A.tracer);
+    if (rc != GW_OK) return rc;
+  }
+  rc = step_finish(S, st);
+  if (rc != GW_OK) return rc;
+  return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+}
+
+// A group of problems with the same row configuration and schedule, advanced
+// in lock step on one stream: each Sinkhorn pass is one launch (per 32
+// problems) over all of the group's row bands.
+template <int NW, int VPT, typename Real>
+int solve_group(const SolveArgs* const* A, void* const* ws, const size_t* ws_bytes, int count, cudaStream_t st) {
+  std::vector<SolveState<Real>> S(count);
+  std::vector<SolveState<Real>*> list(count);
+  for (int i = 0; i < count; ++i) {
+    int rc = prepare<NW, VPT, Real>(*A[i], ws[i], ws_bytes[i], &S[i]);
+    if (rc != GW_OK) return rc;
+    list[i] = &S[i];
+  }
+  unsigned* status = A[0]->status;
+  Tracer* tracer = A[0]->tracer;
+  for (auto& s : S) step_setup(s, st);
+  for (int l = 0; l < A[0]->n_outer; ++l) {
+    for (auto& s : S) {
+      int rc = step_cost(s, st);
+      if (rc != GW_OK) return rc;
+    }
+    for (int it = 0; it < A[0]->n_inner; ++it) {
+      int rc = launch_rows<NW, VPT, Real, 32>(list.data(), count, false, st, status, tracer);
+      if (rc != GW_OK) return rc;
+    }
+    int rc = launch_rows<NW, VPT, Real, 32>(list.data(), count, true, st, status, tracer);
+    if (rc != GW_OK) return rc;
+  }
+  for (auto& s : S) {
+    int rc = step_finish(s, st);
+    if (rc != GW_OK) return rc;
+  }
+  return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+}
+
+// Row configuration (warps, values per thread) of the Sinkhorn kernels for m
+// columns; the configuration index groups batched problems.
+int row_config(int m, int dtype) {
+  if (dtype == GW_F32) {
+    if (m <= 1024) return 0;
+    if (m <= 4096) return 1;
+    if (m <= 8192) return 2;
+    if (m <= 9216) return 3;
+    return 4;
+  }
+  if (m <= 1024) return 10;
+  if (m <= 4096) return 11;
+  return 12;
+}
+
+template <typename F>
+int with_config(int cfg, F&& f) {
+  switch (cfg) {
+    case 0: return f.template run<8, 4, float>();
+    case 1: return f.template run<16, 8, float>();
+    case 2: return f.template run<16, 16, float>();
+    case 3: return f.template run<18, 16, float>();
+    case 4: return f.template run<32, 16, float>();
+    case 10: return f.template run<8, 4, double>();
+    case 11: return f.template run<16, 8, double>();
+    default: return f.template run<32, 16, double>();
+  }
 }
 
 size_t solve_workspace_bytes(const SolveArgs& A) {
   const int n = A.n, m = A.m;
   const size_t rb = A.dtype == GW_F32 ? 4 : 8;
-  const Bands bands = choose_bands(n, A.num_sms);
+  const Bands bands = solve_bands(A);
   size_t b = 0;
   auto add = [&](size_t x) { b = (b + x + 255) / 256 * 256; };
   add((size_t)n * m * rb);
@@ -767,25 +1005,48 @@ size_t solve_workspace_bytes(const SolveArgs& A) {
   add((size_t)bands.B * m * rb);
   add((size_t)bands.B * m * 8);
   add((size_t)2 * bands.B * 8);
-  add(256 * 8);
-  add(256 * 8);
+  add(kDots * 8);
+  add(kDots * 8);
   const size_t g = A.dim == 2 ? grad2d_workspace_bytes(A.nx, A.ny, A.dtype)
                               : grad1d_workspace_bytes(n, m, A.k, A.dtype, A.num_sms);
   return b + g + 4096;
 }
 
-int solve_launch(const SolveArgs& A, void* ws, size_t ws_bytes) {
-  const int m = A.m;
-  if (A.dtype == GW_F32) {
-    if (m <= 1024) return solve_typed<8, 4, float>(A, ws, ws_bytes);
-    if (m <= 4096) return solve_typed<16, 8, float>(A, ws, ws_bytes);
-    if (m <= 8192) return solve_typed<16, 16, float>(A, ws, ws_bytes);
-    if (m <= 9216) return solve_typed<18, 16, float>(A, ws, ws_bytes);
-    return solve_typed<32, 16, float>(A, ws, ws_bytes);
+namespace {
+struct SingleRun {
+  const SolveArgs& A;
+  void* ws;
+  size_t bytes;
+  template <int NW, int VPT, typename Real>
+  int run() {
+    return solve_typed<NW, VPT, Real>(A, ws, bytes);
   }
-  if (m <= 1024) return solve_typed<8, 4, double>(A, ws, ws_bytes);
-  if (m <= 4096) return solve_typed<16, 8, double>(A, ws, ws_bytes);
-  return solve_typed<32, 16, double>(A, ws, ws_bytes);
+};
+struct GroupRun {
+  const SolveArgs* const* A;
+  void* const* ws;
+  const size_t* bytes;
+  int count;
+  cudaStream_t st;
+  template <int NW, int VPT, typename Real>
+  int run() {
+    return solve_group<NW, VPT, Real>(A, ws, bytes, count, st);
+  }
+};
+}  // namespace
+
+int solve_launch(const SolveArgs& A, void* ws, size_t ws_bytes) {
+  SingleRun r{A, ws, ws_bytes};
+  return with_config(row_config(A.m, A.dtype), r);
+}
+
+int solve_group_key(const SolveArgs& A) { return row_config(A.m, A.dtype); }
+
+int solve_group_launch(const SolveArgs* const* A, void* const* ws, const size_t* ws_bytes, int count,
+                       cudaStream_t stream) {
+  if (count <= 0) return GW_OK;
+  GroupRun r{A, ws, ws_bytes, count, stream};
+  return with_config(row_config(A[0]->m, A[0]->dtype), r);
 }
 
 }  // namespace gw

@@ -127,3 +127,19 @@ def workload_2d(side_x: int = 64, side_y: int = 96, cost: str = "sqeuclid",
     return dict(dim=2, nx=side_x, ny=side_y, hx=1.0 / (side_x - 1),
                 hy=1.0 / (side_y - 1), k=1, cost=cost, eps=5e-3,
                 n_outer=20, n_inner=100, u=u, v=v)
+
+
+def workload_batch(count: int = 256, seed: int = 0, lo: int = 256, hi: int = 8192,
+                   n_outer: int = 20, n_inner: int = 100):
+    """`count` independent 1D problems: n and m drawn independently as
+    round(exp(U(ln lo, ln hi))), k uniform in {1, 2}, uniform marginals,
+    h = 1/n and 1/m, eps = 1e-2."""
+    rng = rng_for(seed)
+    out = []
+    for _ in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        m = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        k = int(rng.integers(1, 3))
+        out.append(dict(dim=1, nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=k, eps=1e-2, n_outer=n_outer,
+                        n_inner=n_inner, u=uniform_weights(n), v=uniform_weights(m)))
+    return out

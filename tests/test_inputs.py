@@ -1,0 +1,26 @@
+"""The seeded workload generators: shapes, ranges and determinism (CPU)."""
+import numpy as np
+
+from paper_2404_08970_gb300 import inputs as I
+
+
+def test_batch_workload_generator():
+    ws = I.workload_batch(256, seed=0)
+    assert len(ws) == 256
+    ns = np.array([w["nx"] for w in ws] + [w["ny"] for w in ws])
+    assert ns.min() >= 256 and ns.max() <= 8192
+    # log-uniform: about half the sizes below the geometric midpoint 1448
+    assert 0.4 < np.mean(ns < 1448) < 0.6
+    assert set(w["k"] for w in ws) == {1, 2}
+    for w in ws[:5]:
+        assert abs(w["u"].sum() - 1) < 1e-12 and abs(w["v"].sum() - 1) < 1e-12
+    again = I.workload_batch(256, seed=0)
+    assert [(w["nx"], w["ny"], w["k"]) for w in ws] == [(w["nx"], w["ny"], w["k"]) for w in again]
+
+
+def test_random_coupling_is_positive_with_marginals():
+    rng = I.rng_for(0)
+    u, v = I.dirichlet(30, 0.5, rng), I.dirichlet(40, 0.5, rng)
+    T = I.random_coupling(u, v, rng)
+    assert np.all(T > 0)
+    assert np.max(np.abs(T.sum(1) - u)) < 1e-15 and np.max(np.abs(T.sum(0) - v)) < 1e-15
