@@ -194,7 +194,8 @@ gw_status gw_grad_dense(gw_ctx* ctx, const gw_problem* prob, const double* d_u, 
  * and runs prob->n_inner log-domain Sinkhorn iterations from f = g = 0
  * (f then g each iteration), then sets T_ip = exp((f_i + g_p - Pi_ip) / eps).
  *
- *   prob         dim 1 or 2; nx, ny, hx, hy, k, cost as for gw_grad; eps > 0;
+ *   prob         dim 1 or 2; nx, ny, hx, hy, k, cost as for gw_grad, with at
+ *                most 16384 points in Y (ny, or ny^2 in 2D); eps > 0;
  *                n_outer >= 0; n_inner >= 1; theta in [0, 1]; feat_dim in
  *                [1, 64] when theta < 1; dtype GW_F32 or GW_F64 (the
  *                arithmetic precision of the whole solve).

@@ -408,6 +408,8 @@ gw_status check_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const d
     return fail(c, GW_ERR_INVALID, "%s: fused GW (theta < 1) needs 1 <= feat_dim <= 64 and both feature arrays",
                 who);
   if (!d_u || !d_v || !d_T) return fail(c, GW_ERR_INVALID, "%s: d_u, d_v and d_T must not be NULL", who);
+  if (points_y(p) > 16384)
+    return fail(c, GW_ERR_INVALID, "%s: the solver takes at most 16384 points in Y (got %zu)", who, points_y(p));
   return GW_OK;
 }
 

@@ -165,13 +165,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 // Bounded wait on an mbarrier phase.  Returns false (and sets ERR_TIMEOUT)
 // if the phase did not complete within kWaitLimit polls.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, unsigned* status) {
-  if (mbar_try_wait(bar, parity)) return true;
-  // Once any wait has given up, the results are already invalid: later waits
-  // return at once so that the launch finishes quickly and reports.
-  if (status && (*(volatile unsigned*)status & ERR_TIMEOUT)) return false;
   for (unsigned it = 0; it < kWaitLimit; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (it > 64) __nanosleep(64);
+    // Once any wait has given up, the results are already invalid: later
+    // waits give up too (checked every 256 polls, so that short waits never
+    // pay a global load) and the launch finishes quickly and reports.
+    if ((it & 255u) == 255u && status && (*(volatile unsigned*)status & ERR_TIMEOUT)) return false;
+    if (it >= 1024) __nanosleep(64);
   }
   set_status(status, ERR_TIMEOUT);
   return false;

@@ -29,7 +29,6 @@
 
 #include "gw_common.cuh"
 #include "gw_internal.h"
-#include "gw_tma.cuh"
 
 namespace gw {
 
@@ -71,11 +70,23 @@ __device__ __forceinline__ Real tree_sum(const Real (&x)[N]) {
     for (int v = 0; v + w < N; v += 2 * w) t[v] += t[v + w];
   return t[0];
 }
+// p 16-byte aligned (shared memory): read with 16-byte loads.
 template <int N, typename Real>
 __device__ __forceinline__ Real tree_sum_smem(const Real* p) {
+  constexpr int PER = 16 / sizeof(Real);
   Real t[N];
+  if constexpr (N % PER == 0) {
 #pragma unroll
-  for (int v = 0; v < N; ++v) t[v] = p[v];
+    for (int j = 0; j < N / PER; ++j) {
+      const float4 q = reinterpret_cast<const float4*>(p)[j];
+      const Real* e = reinterpret_cast<const Real*>(&q);
+#pragma unroll
+      for (int w = 0; w < PER; ++w) t[j * PER + w] = e[w];
+    }
+  } else {
+#pragma unroll
+    for (int v = 0; v < N; ++v) t[v] = p[v];
+  }
   return tree_sum<N>(t);
 }
 
@@ -87,58 +98,72 @@ template <> __device__ __forceinline__ float tiny_sum<float>() { return 1e-24f; 
 template <> __device__ __forceinline__ double tiny_sum<double>() { return 1e-250; }
 
 // ---------------------------------------------------------------------------
-// Shared-memory layout of the row-streaming kernels (1024-aligned base):
-//   ring [stages][slot_bytes] | G (swizzled, vec_bytes) | red [2][2][NW] Real |
-//   Fband, Fold, LU [Rmax] Real | bars [stages]
+// Row streaming.  Rows of Pi are brought into a shared-memory ring with 1D
+// bulk copies (cp.async.bulk) completing on mbarriers.  A copy must start and
+// end on 16-byte boundaries, so row i is copied from the 16-byte boundary at
+// or below its first byte to the boundary at or above its end, and its
+// element p sits at index off + p of the slot (off < 16 / sizeof(Real)); any
+// row length works.  The copies may read up to 15 bytes past the end of Pi,
+// which lies inside the workspace.
 // ---------------------------------------------------------------------------
 struct RowGeom {
-  int slot_bytes, vec_bytes, stages, use_tma, box_cols;
+  int slot_bytes, stages;
 };
-
-template <int NW, typename Real>
-size_t rows_smem_bytes(const RowGeom& g, int Rmax) {
-  return 1024 + (size_t)g.stages * g.slot_bytes + g.vec_bytes + sizeof(Real) * (4 * NW + 3 * Rmax) + 16 +
-         8 * (size_t)g.stages + 64;
-}
 
 template <typename Real>
-struct RowRing {
-  unsigned char* ring;
-  uint64_t* bars;
-  int stages, slot_bytes, use_tma, box_cols;
-  const CUtensorMap* tm;
-  const Real* src;
-  int m, s, Ra;
+__device__ __forceinline__ void row_span(const Real* Pi, int m, int row, const char** src, unsigned* bytes,
+                                         int* off) {
+  const size_t start = (size_t)row * (size_t)m * sizeof(Real);
+  const size_t a0 = start & ~(size_t)15;
+  const size_t a1 = (start + (size_t)m * sizeof(Real) + 15) & ~(size_t)15;
+  *src = reinterpret_cast<const char*>(Pi) + a0;
+  *bytes = (unsigned)(a1 - a0);
+  *off = (int)((start - a0) / sizeof(Real));
+}
 
-  __device__ void issue(int tl) {  // row s + tl into slot tl % stages, in boxes of box_cols 128-byte lines
-    const int slot = tl % stages;
-    const int lines = (int)(m * sizeof(Real) / 128);
-    mbar_arrive_expect_tx(&bars[slot], (unsigned)(m * sizeof(Real)));
-    for (int y = 0; y < lines; y += box_cols)
-      tma_load_3d(ring + (size_t)slot * slot_bytes + (size_t)y * 128, tm, 0, y, s + tl, &bars[slot]);
-  }
-  // Returns the slot holding row tl; all NT threads call it.
-  __device__ const unsigned char* get(int tl, int NT, unsigned* status) {
-    if (use_tma) {
-      const int slot = tl % stages;
-      mbar_wait_bounded(&bars[slot], (unsigned)((tl / stages) & 1), status);
-      return ring + (size_t)slot * slot_bytes;
+// Column ownership in the row kernels: value v = j * PER + e of thread t
+// (PER = 16 / sizeof(Real)) is column col_of(t, v) = PER * (j * NT + t) + e,
+// so the j-th 16-byte load of a warp reads 512 contiguous bytes (no bank
+// conflicts without a swizzle) and every thread's columns are interleaved
+// across the row.
+template <typename Real>
+__host__ __device__ __forceinline__ int col_of(int t, int v, int NT) {
+  constexpr int PER = 16 / sizeof(Real);
+  return PER * ((v / PER) * NT + t) + v % PER;
+}
+
+// x[v] = row[col_of(t, v)]: 16-byte loads when the row's start is 16-byte
+// aligned, else scalar loads.  A 16-byte group that starts at or past column
+// m is not read (zeros); the group straddling m reads up to PER - 1 values
+// past the row, inside the slot's slack (finite, see sk_pass).  `row` is
+// derived from the shared array.
+template <int VPT, int NT, typename Real>
+__device__ __forceinline__ void load_vals(const Real* row, int tid, int m, Real (&x)[VPT]) {
+  constexpr int PER = 16 / sizeof(Real);
+  static_assert(VPT % PER == 0, "VPT must be a multiple of the 16-byte vector");
+  if ((smem_u32(row) & 15u) == 0) {
+#pragma unroll
+    for (int j = 0; j < VPT / PER; ++j) {
+      const bool in = PER * (j * NT + tid) < m;
+      const float4 q = in ? reinterpret_cast<const float4*>(row)[j * NT + tid] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const Real* e = reinterpret_cast<const Real*>(&q);
+#pragma unroll
+      for (int w = 0; w < PER; ++w) x[j * PER + w] = e[w];
     }
-    unsigned char* dst = ring + (size_t)(tl & 1) * slot_bytes;
-    const Real* row = src + (size_t)(s + tl) * m;
-    for (int p = threadIdx.x; p < m; p += NT) sts_swz<Real>(dst, p, row[p]);
-    __syncthreads();
-    return dst;
+  } else {
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) {
+      const int p = col_of<Real>(tid, v, NT);
+      x[v] = p < m + PER ? row[p] : (Real)0;
+    }
   }
-};
+}
 
 // One problem of a (possibly batched) launch: its cost matrix, potentials,
 // outputs and row-band layout.  Launches take up to MAXP of these as one
-// __grid_constant__ parameter block (the tensor maps stay in parameter space,
-// where the TMA unit reads them); blocks are numbered across the problems.
+// __grid_constant__ parameter block; blocks are numbered across the problems.
 template <typename Real>
 struct SkProb {
-  CUtensorMap tm;  // rows of Pi (64-byte aligned)
   RowGeom geo;
   const Real* Pi;
   const Real* lu;  // log2 u
@@ -166,19 +191,34 @@ __device__ __forceinline__ int batch_problem(const SkBatch<Real, MAXP>& P) {
   return pi;
 }
 
-__device__ __forceinline__ float u_or_exp(float lu) { return exp2f(lu); }
-__device__ __forceinline__ double u_or_exp(double lu) { return exp2(lu); }
+// r = 2^lu / S: the factor that turns the row pass's exponentials into the
+// new plan's entries (float: hardware exp2 and a correctly rounded
+// reciprocal, about 2 ulp in all; double: exact library operations).
+__device__ __forceinline__ float scale_of(float lu, float S) { return ex2(lu) * __frcp_rn(S); }
+__device__ __forceinline__ double scale_of(double lu, double S) { return exp2(lu) / S; }
 
-// Row sum out of range: redo row `tl` with a max shift from the ring slot
-// (block-uniform branch; sfb holds 32 scratch reals).
-template <int VPT, typename Real>
-__device__ __forceinline__ void row_fallback(RowRing<Real>& rr, int tl, int NT, unsigned* status, Real c, Real (&x)[VPT],
-                                          const Real (&Gv)[VPT], Real Fo, Real lui, Real (&acc)[VPT], Real* F,
-                                          Real* Fband, int ip, Real* sfb, int lane, int warp, int tid) {
-  const int slot = tl % rr.stages;
-  const unsigned char* xr = rr.use_tma ? rr.ring + (size_t)slot * rr.slot_bytes : rr.ring + (size_t)(tl & 1) * rr.slot_bytes;
-  lds_swz<Real, VPT>(xr, tid * VPT, x);
-  const int NW = NT / 32;
+// Shared memory of sk_pass (128-byte aligned base):
+//   ring [stages][slot_bytes] | red [2][NW] Real | Fold, LU [R] Real |
+//   full [stages] mbarriers
+template <int NW, typename Real>
+size_t pass_smem_bytes(const RowGeom& g, int R) {
+  return 128 + (size_t)g.stages * g.slot_bytes + sizeof(Real) * (2 * NW + 2 * (size_t)R) + 16 + 8 * (size_t)g.stages;
+}
+// Shared memory of sk_plan: ring | full [stages] mbarriers.
+inline size_t plan_smem_bytes(const RowGeom& g) { return 128 + (size_t)g.stages * g.slot_bytes + 8 * g.stages + 16; }
+
+// Row sum out of range: redo the row from the ring with a max shift,
+// M = max_p e_p, S2 = sum_p 2^(e_p - M), e = F_old + G - c Pi (all threads of
+// the block call it for the same row; padded columns have G = -inf).
+// Returns the new potential and adds the row's plan entries to acc.  The
+// row is read again from the ring, so nothing of the row pass stays live
+// across the block barrier.
+template <int NW, int VPT, typename Real>
+__device__ __forceinline__ Real row_redo(const Real* row, int m, Real c, const Real (&Gv)[VPT], Real Fo, Real lut,
+                                         Real (&acc)[VPT], Real* sfb) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Real x[VPT];
+  load_vals<VPT, 32 * NW>(row, threadIdx.x, m, x);
   Real e[VPT];
   Real lm = -INFINITY;
 #pragma unroll
@@ -187,11 +227,11 @@ __device__ __forceinline__ void row_fallback(RowRing<Real>& rr, int tl, int NT, 
     lm = fmax(lm, e[v]);
   }
   lm = warp_max(lm);
-  __syncthreads();
   if (lane == 0) sfb[warp] = lm;
   __syncthreads();
   Real M = -INFINITY;
-  for (int w = 0; w < NW; ++w) M = fmax(M, sfb[w]);
+#pragma unroll
+  for (int q = 0; q < NW; ++q) M = fmax(M, sfb[q]);
   Real s2 = 0;
 #pragma unroll
   for (int v = 0; v < VPT; ++v) s2 += ex2(e[v] - M);
@@ -200,181 +240,131 @@ __device__ __forceinline__ void row_fallback(RowRing<Real>& rr, int tl, int NT, 
   if (lane == 0) sfb[warp] = s2;
   __syncthreads();
   Real S2 = 0;
-  for (int w = 0; w < NW; ++w) S2 += sfb[w];
-  const Real Fn = Fo + lui - (M + lg2(S2));
-  // Column terms 2^(Fn + G - c Pi) directly.
+#pragma unroll
+  for (int q = 0; q < NW; ++q) S2 += sfb[q];
+  const Real Fn = Fo + lut - (M + lg2(S2));
 #pragma unroll
   for (int v = 0; v < VPT; ++v) acc[v] += ex2(Fn + e[v] - Fo);
-  if (tid == 0) {
-    F[ip] = Fn;
-    Fband[tl] = Fn;
-  }
   __syncthreads();
+  return Fn;
 }
 
 // ---------------------------------------------------------------------------
-// sk_pass
+// sk_pass: one Sinkhorn iteration over one row band of one problem.
+//
+// Row j: w_j,p = 2^(F_old,j + G_p - c Pi_jp) (every w <= v_p after a column
+// update), S_j = sum_p w_j,p.  The new potential is F_j + log2(u_j / S_j) and
+// the column sums need 2^(F_new,j + G_p - c Pi_jp) = (u_j / S_j) w_j,p, so one
+// exp2 per element serves both.  Thread t owns columns t*VPT .. t*VPT+VPT-1;
+// per row: the row pass, one block barrier (the row sum needs every warp),
+// then thread 0 refills the ring slot and every thread adds r_j w_j to its
+// column sums.  A row sum out of range is redone from the ring with a max
+// shift (block-uniform branch).
 // ---------------------------------------------------------------------------
 template <int NW, int VPT, typename Real, int MAXP>
-__global__ void __launch_bounds__(32 * NW, 1) sk_pass(const __grid_constant__ SkBatch<Real, MAXP> P, unsigned* status) {
+__global__ void __launch_bounds__(32 * NW, 1)
+    sk_pass(const __grid_constant__ SkBatch<Real, MAXP> P, unsigned* status) {
   constexpr int NT = 32 * NW;
   const int pi = batch_problem(P);
   const SkProb<Real>& pr = P.p[pi];
-  const RowGeom geo = pr.geo;
+  const int S = pr.geo.stages, slot_bytes = pr.geo.slot_bytes;
   const Real* __restrict__ Pi = pr.Pi;
-  const Real* __restrict__ lu = pr.lu;
   Real* __restrict__ F = pr.F;
-  const Real* __restrict__ Gp = pr.G;
   Real* __restrict__ part = pr.part;
   const int n = pr.n, m = pr.m, R = pr.R;
   const Real c = pr.c;
+
   extern __shared__ __align__(16) unsigned char smem_dyn[];
-  unsigned char* sm = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+  unsigned char* sm = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
   unsigned char* ring = sm;
-  unsigned char* Gs = ring + (size_t)geo.stages * geo.slot_bytes;
-  Real* red = reinterpret_cast<Real*>(Gs + geo.vec_bytes);  // [2][2][NW]
-  Real* Fband = red + 4 * NW;  // new potentials of the band's rows
-  Real* Fold = Fband + R;      // previous potentials of the band's rows
-  Real* LU = Fold + R;         // log2 u of the band's rows
+  Real* red = reinterpret_cast<Real*>(ring + (size_t)S * slot_bytes);  // 16-byte aligned
+  Real* Fold = red + 2 * NW;
+  Real* LU = Fold + R;
   unsigned char* braw = reinterpret_cast<unsigned char*>(LU + R);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(braw + ((8u - (smem_u32(braw) & 7u)) & 7u));
+  uint64_t* full = reinterpret_cast<uint64_t*>(braw + ((8u - (smem_u32(braw) & 7u)) & 7u));
+  __shared__ Real sfb[32];  // fallback reductions
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int a = (int)blockIdx.x - P.block0[pi], s = a * R, Ra = min(R, n - s);
-  const int c0 = tid * VPT;
-  const int m_pad = geo.vec_bytes / (int)sizeof(Real);
-
-  RowRing<Real> rr{ring, bars, geo.stages, geo.slot_bytes, geo.use_tma, geo.box_cols, &pr.tm, Pi, m, s, Ra};
-  if (geo.use_tma && tid == 0) {
-    for (int st = 0; st < geo.stages; ++st) mbar_init(&bars[st], 1);
+  auto issue = [&](int t) {
+    const char* src;
+    unsigned bytes;
+    int off;
+    row_span(Pi, m, s + t, &src, &bytes, &off);
+    mbar_arrive_expect_tx(&full[t % S], bytes);
+    bulk_g2s(ring + (size_t)(t % S) * slot_bytes, src, bytes, &full[t % S]);
+  };
+  // Past the row's end a slot holds up to 24 bytes of what follows the row in
+  // Pi (finite), or the zeros written here: finite values that the -inf of the
+  // padded columns' G turns into exact zeros, with no per-element masks.
+  const size_t row_bytes = (size_t)m * sizeof(Real);
+  for (int q = 0; q < S; ++q)
+    for (size_t b = row_bytes + 4 * (size_t)tid; b + 4 <= (size_t)slot_bytes; b += 4 * (size_t)NT)
+      *reinterpret_cast<unsigned*>(ring + (size_t)q * slot_bytes + b) = 0u;
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) mbar_init(&full[i], 1);
     fence_mbar_init();
+    for (int t = 0; t < S && t < Ra; ++t) issue(t);
   }
-  // The band's previous potentials and log2 u, staged once so that no row
-  // waits on a dependent global load.
   for (int t = tid; t < Ra; t += NT) {
     Fold[t] = F[s + t];
-    LU[t] = lu[s + t];
+    LU[t] = pr.lu[s + t];
   }
-  // Padded columns get G = -inf, so their terms are exactly zero.
-  for (int p = tid; p < m_pad; p += NT) sts_swz<Real>(Gs, p, p < m ? Gp[p] : (Real)-INFINITY);
-  for (int st = 0; st < geo.stages; ++st)
-    for (int p = m + tid; p < m_pad; p += NT) sts_swz<Real>(ring + (size_t)st * geo.slot_bytes, p, (Real)0);
+  Real Gv[VPT], acc[VPT];
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    const int p = col_of<Real>(tid, v, NT);
+    Gv[v] = p < m ? pr.G[p] : (Real)-INFINITY;
+    acc[v] = 0;
+  }
   __syncthreads();
-  // Every slot is free at the start: rows 0 .. stages-1.  Later, the slot of
-  // row j-1 is refilled (with row j-1+stages) after iteration j.
-  if (geo.use_tma && tid == 0)
-    for (int tl = 0; tl < geo.stages && tl < Ra; ++tl) rr.issue(tl);
+  auto row_ptr = [&](int t) {
+    const int off = (int)((((size_t)(s + t) * (size_t)m * sizeof(Real)) & 15) / sizeof(Real));
+    return reinterpret_cast<const Real*>(ring + (size_t)(t % S) * slot_bytes) + off;
+  };
 
-  Real Gv[VPT];
-  lds_swz<Real, VPT>(Gs, c0, Gv);
-  Real acc[VPT];
+  for (int t = 0; t < Ra; ++t) {
+    mbar_wait_bounded(&full[t % S], (unsigned)((t / S) & 1), status);
+    Real x[VPT], w[VPT];
+    load_vals<VPT, NT>(row_ptr(t), tid, m, x);
+    const Real Fo = Fold[t];
 #pragma unroll
-  for (int v = 0; v < VPT; ++v) acc[v] = 0;
-  __shared__ Real sfb[32];  // fallback reductions
-
-  // Row j: w_j,p = 2^(F_old,j + G_p - c Pi_jp) (every w <= v_p after a column
-  // update), S_j = sum_p w_j,p.  The new potential is F_j + log2(u_j / S_j) and
-  // the column sums need 2^(F_new,j + G_p - c Pi_jp) = (u_j / S_j) w_j,p, so one
-  // exp2 per element serves both halves.  Rows go two at a time: both row
-  // passes, one block barrier for both row sums, both column updates.
-  for (int j = 0; j < Ra; j += 2) {
-    const bool two = j + 1 < Ra;
-    Real w0[VPT], w1[VPT];
-    const Real Fo0 = Fold[j], Fo1 = two ? Fold[j + 1] : (Real)0;
-    {
-      Real x0[VPT], x1[VPT];
-      lds_swz<Real, VPT>(rr.get(j, NT, status), c0, x0);
-      if (two) {
-        lds_swz<Real, VPT>(rr.get(j + 1, NT, status), c0, x1);
-      } else {
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) x1[v] = 0;
-      }
-#pragma unroll
-      for (int v = 0; v < VPT; ++v) {
-        w0[v] = ex2(fma(-c, x0[v], Gv[v] + Fo0));
-        w1[v] = two ? ex2(fma(-c, x1[v], Gv[v] + Fo1)) : (Real)0;
-      }
-    }
-    Real s0 = tree_sum<VPT>(w0), s1 = tree_sum<VPT>(w1);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-    }
-    Real* rb = red + ((j >> 1) & 1) * 2 * NW;  // [2 rows][NW], double-buffered by pair
-    if (lane == 0) {
-      rb[warp] = s0;
-      rb[NW + warp] = s1;
-    }
+    for (int v = 0; v < VPT; ++v) w[v] = ex2(fma(-c, x[v], Gv[v] + Fo));
+    const Real sum = warp_sum(tree_sum<VPT>(w));
+    Real* rb = red + (t & 1) * NW;
+    if (lane == 0) rb[warp] = sum;
     __syncthreads();
-    const Real S0 = tree_sum_smem<NW>(rb), S1 = two ? tree_sum_smem<NW>(rb + NW) : (Real)1;
-    const bool ok0 = S0 >= tiny_sum<Real>() && S0 <= (Real)1e30;
-    const bool ok1 = S1 >= tiny_sum<Real>() && S1 <= (Real)1e30;
-    // Rows j, j + 1 are read: refill their slots now unless a row must be
-    // redone from its slot.
-    const bool refill_now = ok0 && ok1;
-    auto refill = [&]() {
-      if (geo.use_tma && tid == 0) {
+    const Real St = tree_sum_smem<NW>(rb);
+    const Real lut = LU[t];
+    if (St >= tiny_sum<Real>() && St <= (Real)1e30) {
+      // Every thread has read row t: its slot takes row t + S.
+      if (tid == 0 && t + S < Ra) {
         fence_proxy_async_smem();
-        if (j + geo.stages < Ra) rr.issue(j + geo.stages);
-        if (j + 1 + geo.stages < Ra) rr.issue(j + 1 + geo.stages);
+        issue(t + S);
       }
-    };
-    if (refill_now) refill();
-    const Real lu0 = LU[j], lu1 = two ? LU[j + 1] : (Real)0;
-    if (ok0 && ok1) {
-      const Real r0 = (Real)u_or_exp(lu0) / S0;
-      const Real r1 = two ? (Real)u_or_exp(lu1) / S1 : (Real)0;
+      const Real r = scale_of(lut, St);
 #pragma unroll
-      for (int v = 0; v < VPT; ++v) acc[v] = fma(r1, w1[v], fma(r0, w0[v], acc[v]));
-      if (tid == 0) {
-        const Real Fn0 = Fo0 + lu0 - lg2(S0);
-        F[s + j] = Fn0;
-        Fband[j] = Fn0;
-        if (two) {
-          const Real Fn1 = Fo1 + lu1 - lg2(S1);
-          F[s + j + 1] = Fn1;
-          Fband[j + 1] = Fn1;
-        }
-      }
+      for (int v = 0; v < VPT; ++v) acc[v] = fma(r, w[v], acc[v]);
+      if (tid == 0) F[s + t] = Fo + lut - lg2(St);
     } else {
-      // Block-uniform: a row sum out of range is redone with a max shift.
-      Real x[VPT];
-      if (ok0) {
-        const Real r0 = (Real)u_or_exp(lu0) / S0;
-#pragma unroll
-        for (int v = 0; v < VPT; ++v) acc[v] = fma(r0, w0[v], acc[v]);
-        if (tid == 0) {
-          const Real Fn0 = Fo0 + lu0 - lg2(S0);
-          F[s + j] = Fn0;
-          Fband[j] = Fn0;
-        }
-      } else {
-        row_fallback(rr, j, NT, status, c, x, Gv, Fo0, lu0, acc, F, Fband, s + j, sfb, lane, warp, tid);
-      }
-      if (two) {
-        if (ok1) {
-          const Real r1 = (Real)u_or_exp(lu1) / S1;
-#pragma unroll
-          for (int v = 0; v < VPT; ++v) acc[v] = fma(r1, w1[v], acc[v]);
-          if (tid == 0) {
-            const Real Fn1 = Fo1 + lu1 - lg2(S1);
-            F[s + j + 1] = Fn1;
-            Fband[j + 1] = Fn1;
-          }
-        } else {
-          row_fallback(rr, j + 1, NT, status, c, x, Gv, Fo1, lu1, acc, F, Fband, s + j + 1, sfb, lane, warp, tid);
+      const Real Fn = row_redo<NW, VPT, Real>(row_ptr(t), m, c, Gv, Fo, lut, acc, sfb);
+      if (tid == 0) {
+        F[s + t] = Fn;
+        if (t + S < Ra) {
+          fence_proxy_async_smem();
+          issue(t + S);
         }
       }
-      __syncthreads();
-      refill();
     }
   }
   // Band partials of the column sums (relative to the current G).
 #pragma unroll
-  for (int v = 0; v < VPT; ++v)
-    if (c0 + v < m) part[(size_t)a * m + c0 + v] = acc[v];
+  for (int v = 0; v < VPT; ++v) {
+    const int p = col_of<Real>(tid, v, NT);
+    if (p < m) part[(size_t)a * m + p] = acc[v];
+  }
 }
 
 // Per column: S_p = sum_b part_bp (FP32 compensated sums over 8 band groups,
@@ -464,46 +454,45 @@ __global__ void __launch_bounds__(256) sk_cols(const __grid_constant__ SkBatch<R
 // ---------------------------------------------------------------------------
 template <int NW, int VPT, typename Real, int MAXP>
 __global__ void __launch_bounds__(32 * NW, 1) sk_plan(const __grid_constant__ SkBatch<Real, MAXP> P, unsigned* status) {
-  constexpr int NT = 32 * NW;
   const int pi = batch_problem(P);
   const SkProb<Real>& pr = P.p[pi];
-  const RowGeom geo = pr.geo;
+  const int S = pr.geo.stages, slot_bytes = pr.geo.slot_bytes;
   const Real* __restrict__ Pi = pr.Pi;
   const Real* __restrict__ F = pr.F;
-  const Real* __restrict__ Gp = pr.G;
   const double* __restrict__ u = pr.u;
   Real* __restrict__ T = pr.T;
-  double* __restrict__ colpart = pr.colpart;
-  double* __restrict__ cta_stats = pr.cta_stats;
   const int n = pr.n, m = pr.m, R = pr.R;
   const Real c = pr.c;
   extern __shared__ __align__(16) unsigned char smem_dyn[];
-  unsigned char* sm = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+  unsigned char* sm = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
   unsigned char* ring = sm;
-  unsigned char* Gs = ring + (size_t)geo.stages * geo.slot_bytes;
-  Real* red = reinterpret_cast<Real*>(Gs + geo.vec_bytes);
-  Real* Fband = red + 2 * NW;
-  unsigned char* braw = reinterpret_cast<unsigned char*>(Fband + R);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(braw + ((8u - (smem_u32(braw) & 7u)) & 7u));
+  unsigned char* braw = ring + (size_t)S * slot_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(braw);
   __shared__ double dred[2][32];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int a = (int)blockIdx.x - P.block0[pi], s = a * R, Ra = min(R, n - s);
-  const int c0 = tid * VPT;
-  const int m_pad = geo.vec_bytes / (int)sizeof(Real);
-  RowRing<Real> rr{ring, bars, geo.stages, geo.slot_bytes, geo.use_tma, geo.box_cols, &pr.tm, Pi, m, s, Ra};
-  if (geo.use_tma && tid == 0) {
-    for (int st = 0; st < geo.stages; ++st) mbar_init(&bars[st], 1);
+  constexpr int NT = 32 * NW;
+  auto issue = [&](int t) {
+    const char* src;
+    unsigned bytes;
+    int off;
+    row_span(Pi, m, s + t, &src, &bytes, &off);
+    mbar_arrive_expect_tx(&full[t % S], bytes);
+    bulk_g2s(ring + (size_t)(t % S) * slot_bytes, src, bytes, &full[t % S]);
+  };
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) mbar_init(&full[i], 1);
     fence_mbar_init();
+    for (int t = 0; t < S && t < Ra; ++t) issue(t);
   }
-  for (int p = tid; p < m_pad; p += NT) sts_swz<Real>(Gs, p, p < m ? Gp[p] : (Real)0);
-  for (int st = 0; st < geo.stages; ++st)
-    for (int p = m + tid; p < m_pad; p += NT) sts_swz<Real>(ring + (size_t)st * geo.slot_bytes, p, (Real)0);
   __syncthreads();
-  if (geo.use_tma && tid == 0)
-    for (int tl = 0; tl < geo.stages - 1 && tl < Ra; ++tl) rr.issue(tl);
   Real Gv[VPT];
-  lds_swz<Real, VPT>(Gs, c0, Gv);
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) {
+    const int p = col_of<Real>(tid, v, NT);
+    Gv[v] = p < m ? pr.G[p] : (Real)0;
+  }
   double csum[VPT];
 #pragma unroll
   for (int v = 0; v < VPT; ++v) csum[v] = 0.0;
@@ -511,15 +500,16 @@ __global__ void __launch_bounds__(32 * NW, 1) sk_plan(const __grid_constant__ Sk
   const Real ln2 = (Real)0.69314718055994530942;
   for (int t = 0; t < Ra; ++t) {
     const int i = s + t;
-    const unsigned char* xr = rr.get(t, NT, status);
+    mbar_wait_bounded(&full[t % S], (unsigned)((t / S) & 1), status);
+    const int off = (int)((((size_t)i * (size_t)m * sizeof(Real)) & 15) / sizeof(Real));
     Real x[VPT];
-    lds_swz<Real, VPT>(xr, c0, x);
+    load_vals<VPT, NT>(reinterpret_cast<const Real*>(ring + (size_t)(t % S) * slot_bytes) + off, tid, m, x);
     const Real Fi = F[i];
     Real rs = 0, en = 0;
     Real* trow = T + (size_t)i * m;
 #pragma unroll
     for (int v = 0; v < VPT; ++v) {
-      const int p = c0 + v;
+      const int p = col_of<Real>(tid, v, NT);
       if (p < m) {
         const Real lt = fma(-c, x[v], Gv[v] + Fi);  // log2 T
         const Real tv = ex2(lt);
@@ -533,9 +523,9 @@ __global__ void __launch_bounds__(32 * NW, 1) sk_plan(const __grid_constant__ Sk
     ent += (double)en;
     if (lane == 0) dred[t & 1][warp] = rsd;
     __syncthreads();
-    if (geo.use_tma && tid == 0 && t + geo.stages - 1 < Ra) {
+    if (tid == 0 && t + S < Ra) {
       fence_proxy_async_smem();
-      rr.issue(t + geo.stages - 1);
+      issue(t + S);
     }
     if (tid == 0) {
       double r = 0.0;
@@ -544,8 +534,10 @@ __global__ void __launch_bounds__(32 * NW, 1) sk_plan(const __grid_constant__ Sk
     }
   }
 #pragma unroll
-  for (int v = 0; v < VPT; ++v)
-    if (c0 + v < m) colpart[(size_t)a * m + c0 + v] = csum[v];
+  for (int v = 0; v < VPT; ++v) {
+    const int p = col_of<Real>(tid, v, NT);
+    if (p < m) pr.colpart[(size_t)a * m + p] = csum[v];
+  }
   ent = warp_sum(ent);
   __syncthreads();
   if (lane == 0) dred[0][warp] = ent;
@@ -553,8 +545,8 @@ __global__ void __launch_bounds__(32 * NW, 1) sk_plan(const __grid_constant__ Sk
   if (tid == 0) {
     double e = 0.0;
     for (int w = 0; w < NW; ++w) e += dred[0][w];
-    cta_stats[2 * a + 0] = e;
-    cta_stats[2 * a + 1] = rowerr;
+    pr.cta_stats[2 * a + 0] = e;
+    pr.cta_stats[2 * a + 1] = rowerr;
   }
 }
 
@@ -690,17 +682,16 @@ __global__ void potentials_out(const Real* __restrict__ F, int len, double scale
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
+// Ring slots hold one row, its alignment offset (< 16 bytes) and the VPT
+// elements a thread straddling the row's end reads past it; as many slots as
+// fit in about 200 KB next to the small arrays, from 2 to 6.
 template <int NW, int VPT, typename Real>
-RowGeom row_geom(const void* Pi, int n, int m, CUtensorMap* tm, int Rmax) {
+RowGeom row_geom(int m, int R) {
   RowGeom g{};
-  const int cover = 32 * NW * VPT;
-  g.vec_bytes = (int)(((size_t)cover * sizeof(Real) + 1023) / 1024 * 1024);
-  g.slot_bytes = g.vec_bytes;
-  memset(tm, 0, sizeof(*tm));
-  g.use_tma = ((((uintptr_t)Pi) & 15) == 0) && encode_rows_tmap(tm, Pi, n, m, sizeof(Real), &g.box_cols) &&
-              g.box_cols >= 8;
-  const size_t fixed = 1024 + g.vec_bytes + sizeof(Real) * (2 * NW + Rmax) + 128;
-  g.stages = g.use_tma ? (int)std::max<size_t>(2, std::min<size_t>(4, (200 * 1024 - fixed) / g.slot_bytes)) : 2;
+  g.slot_bytes = (int)((((size_t)m + VPT + 8) * sizeof(Real) + 127) / 128 * 128);
+  const size_t fixed = pass_smem_bytes<NW, Real>(RowGeom{0, 0}, R);
+  g.stages = (int)std::max<size_t>(2, std::min<size_t>(6, (200 * 1024 - std::min<size_t>(fixed, 100 * 1024)) /
+                                                             g.slot_bytes));
   return g;
 }
 
@@ -724,7 +715,7 @@ struct SolveState {
   double *dotE, *dotC;
   char* gws;
   size_t gws_bytes;
-  size_t smem;
+  size_t smem_pass, smem_plan;
 };
 
 template <int NW, int VPT, typename Real>
@@ -760,8 +751,9 @@ int prepare(const SolveArgs& A, void* wsv, size_t ws_bytes, SolveState<Real>* S)
   S->gws_bytes = ws_bytes - off;
   k.T = (Real*)A.T;
   k.u = A.u;
-  k.geo = row_geom<NW, VPT, Real>(k.Pi, n, m, &k.tm, k.R);
-  S->smem = rows_smem_bytes<NW, Real>(k.geo, k.R);
+  k.geo = row_geom<NW, VPT, Real>(m, k.R);
+  S->smem_pass = pass_smem_bytes<NW, Real>(k.geo, k.R);
+  S->smem_plan = plan_smem_bytes(k.geo);
   S->A = &A;
   return GW_OK;
 }
@@ -822,6 +814,8 @@ template <typename Real>
 void step_setup(const SolveState<Real>& S, cudaStream_t st) {
   const SolveArgs& A = *S.A;
   TraceScope ts(A.tracer, "solve_setup", st);
+  // The row copies may read up to 15 bytes past Pi: keep them finite.
+  cudaMemsetAsync((char*)S.sk.Pi + (size_t)A.n * A.m * sizeof(Real), 0, 16, st);
   log2_scaled<Real><<<(A.n + 255) / 256, 256, 0, st>>>(A.u, A.n, (Real*)S.sk.lu);
   log2_scaled<Real><<<(A.m + 255) / 256, 256, 0, st>>>(A.v, A.m, (Real*)S.sk.lv);
   fill_product<Real><<<4 * A.num_sms, 256, 0, st>>>(A.u, A.v, A.n, A.m, (Real*)A.T);
@@ -881,7 +875,7 @@ int launch_rows(SolveState<Real>* const* S, int count, bool plan, cudaStream_t s
       P.p[q] = S[base + q]->sk;
       P.block0[q] = blocks;
       blocks += P.p[q].B;
-      smem = std::max(smem, S[base + q]->smem);
+      smem = std::max(smem, plan ? S[base + q]->smem_plan : S[base + q]->smem_pass);
     }
     P.block0[cnt] = blocks;
     auto kern = plan ? sk_plan<NW, VPT, Real, MAXP> : sk_pass<NW, VPT, Real, MAXP>;
