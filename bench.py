@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-2d", dest="grid2d", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--no-serve", dest="serve", action="store_false")
+    ap.add_argument("--serve-count", type=int, default=1500)
     return ap.parse_args()
 
 
@@ -290,6 +292,72 @@ def bench_batch(ctx, L, dev, stream, barrier, count):
             "first_call_s_incl_capture": t_first, "all_values_finite": bool(np.all(np.isfinite(vals)))}
 
 
+def bench_serve(L, device, count):
+    """Serving: requests of four kinds (1D/2D, GW/fused GW), N per space
+    log-uniform in [128, 16384], eps = 1e-2, 10 x 50, through gw_submit /
+    gw_poll with a 40 GB budget and 8 slots.  Saturated throughput (all
+    submitted at once), then latency with Poisson arrivals at 2000/s and at
+    0.8 x the measured throughput; the first 100 requests of each phase are
+    warm-up and excluded from the percentiles."""
+    import numpy as np
+    from paper_2404_08970_gb300 import inputs as I
+    reqs = I.workload_serve(count, rate=2000.0, seed=0)
+    srv = L.Server(device, hbm_budget_bytes=40 << 30, max_slots=8)
+
+    def prob(r):
+        return L.problem(dim=r["dim"], nx=r["nx"], ny=r["ny"], hx=r["hx"], hy=r["hy"], k=r["k"],
+                         cost=L.GW_COST_SQEUCLID if r["cost"] == "sqeuclid" else L.GW_COST_POW, eps=r["eps"],
+                         n_outer=r["n_outer"], n_inner=r["n_inner"], theta=r["theta"],
+                         feat_dim=0 if r.get("phi") is None else r["phi"].shape[1], dtype=L.GW_F32)
+
+    probs = [prob(r) for r in reqs]
+
+    def run(arrivals):
+        t0 = time.perf_counter()
+        tickets = []
+        for r, p, a in zip(reqs, probs, arrivals):
+            if a is not None:
+                while time.perf_counter() - t0 < a:
+                    pass
+            tickets.append(srv.submit(p, r["u"], r["v"], r.get("phi"), r.get("psi")))
+        lat, bad = {}, 0
+        while len(lat) < len(tickets):
+            for i, t in enumerate(tickets):
+                if i in lat:
+                    continue
+                res = srv.poll(t)
+                if res is not None:
+                    lat[i] = res[2]
+                    bad += res[0] != L.GW_OK
+            time.sleep(0.001)
+        wall = time.perf_counter() - t0
+        la = np.array([lat[i] for i in range(100, len(tickets))]) if len(tickets) > 100 else np.array(list(lat.values()))
+        return wall, la, bad
+
+    try:
+        run([None] * min(64, count))  # warm-up: allocator pool, module loads
+        wall, la, bad = run([None] * count)
+        cap = count / wall
+        out = {"workload": f"{count} requests: 1D GW, 1D FGW, 2D GW, 2D FGW (1/4 each), N per space log-uniform in "
+                           "[128, 16384], 2D side round(sqrt(N)), FGW theta=0.5 with 16-dim N(0,1) features, "
+                           "eps=1e-2, 10 x 50, fp32; budget 40 GB, 8 slots",
+               "saturated_solves_per_s": cap, "saturated_wall_s": wall, "errors": int(bad),
+               "mean_nm": float(np.mean([(r["nx"] ** 2 if r["dim"] == 2 else r["nx"]) *
+                                         (r["ny"] ** 2 if r["dim"] == 2 else r["ny"]) for r in reqs]))}
+        arr = [r["arrival"] for r in reqs]
+        wall, la, bad = run(arr)
+        out["at_2000_per_s"] = {"p50_s": float(np.percentile(la, 50)), "p99_s": float(np.percentile(la, 99)),
+                                "errors": int(bad), "note": "offered load above capacity: the queue grows"}
+        rate = 0.8 * cap
+        gaps = np.random.default_rng(1).exponential(1.0 / rate, size=count)
+        wall, la, bad = run(list(np.cumsum(gaps)))
+        out["at_0.8_capacity"] = {"rate_per_s": rate, "p50_s": float(np.percentile(la, 50)),
+                                  "p99_s": float(np.percentile(la, 99)), "errors": int(bad)}
+        return out
+    finally:
+        srv.close()
+
+
 # ---------------------------------------------------------------------------
 # Arms
 # ---------------------------------------------------------------------------
@@ -485,6 +553,7 @@ def run_ours(args):
 
     grid2d = bench_2d(ctx, L, dev, stream, barrier, min(args.steps, 20), args.solve) if args.grid2d else None
     batch = bench_batch(ctx, L, dev, stream, barrier, args.batch_count) if args.batch else None
+    serve = bench_serve(L, local, args.serve_count) if args.serve else None
 
     clk = clocks.stop()
 
@@ -500,7 +569,7 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(n, k),
                 "roofline": roof, "whole_gradient_gbs": whole_gbs, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": launches, "kernels": prof, "dense": dense, "solve": solve,
-                "grid2d": grid2d, "batch": batch}
+                "grid2d": grid2d, "batch": batch, "serve": serve}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -249,6 +249,57 @@ gw_status gw_solve_batch(gw_ctx* ctx, int count, const gw_problem* probs, const 
                          const double* const* d_v, const double* const* d_phi, const double* const* d_psi,
                          void* const* d_T, double* const* d_stats, void* stream);
 
+/*
+ * Serving: independent (fused) GW solves arriving over time (a deployment
+ * mode of the same method; the paper has no counterpart).
+ *
+ * gw_server_create starts `max_slots` (1..64) worker threads on CUDA device
+ * `device`, each with its own stream.  Requests run in arrival order as soon
+ * as the device-memory budget `hbm_budget_bytes` has room for them (inputs,
+ * plan, statistics and solve workspace); a finished request frees its memory
+ * and slot for the next one.  Up to max_slots requests run concurrently.
+ */
+typedef struct gw_server gw_server;
+
+gw_status gw_server_create(gw_server** server, int device, size_t hbm_budget_bytes, int max_slots);
+
+/* Stops the workers after their running requests; queued requests end with
+ * GW_ERR_SHUTDOWN.  Frees the server. */
+void gw_server_destroy(gw_server* server);
+
+/*
+ * gw_submit - queues one solve (as gw_solve) and returns at once.
+ *   prob                 validated as for gw_solve.
+ *   h_u, h_v             host marginals (double, n and m); copied.
+ *   h_phi, h_psi         host features (double, n x feat_dim, m x feat_dim)
+ *                        when theta < 1, else may be NULL; copied.
+ *   h_T                  NULL, or a host buffer of n*m reals (prob->dtype)
+ *                        that receives the plan; it must stay valid until
+ *                        gw_poll reports the request finished.
+ *   *ticket              receives the request's ticket.
+ * GW_ERR_INVALID for a bad descriptor or a request larger than the budget
+ * (it could never run); GW_ERR_SHUTDOWN after gw_server_destroy began.
+ */
+gw_status gw_submit(gw_server* server, const gw_problem* prob, const double* h_u, const double* h_v,
+                    const double* h_phi, const double* h_psi, void* h_T, uint64_t* ticket);
+
+/*
+ * gw_poll - GW_NOT_READY while the request is queued or running.  Once it
+ * has finished: its status (GW_OK, or the error of its solve), the 8
+ * statistics of gw_solve in stats (if not NULL) and the seconds from
+ * gw_submit to completion in *latency_s (if not NULL).  A finished ticket
+ * is reported once; afterwards (or for an unknown ticket) GW_ERR_INVALID.
+ */
+gw_status gw_poll(gw_server* server, uint64_t ticket, double* stats, double* latency_s);
+
+/* Text of the last failed request ("" if none); valid until the calling
+ * thread's next call of this function. */
+const char* gw_server_last_error(gw_server* server);
+
+/* Queued requests, requests completed so far, device bytes held by running
+ * requests (any pointer may be NULL). */
+gw_status gw_server_info(gw_server* server, long* queued, long* completed, size_t* bytes_in_use);
+
 #ifdef __cplusplus
 }
 #endif

@@ -94,6 +94,13 @@ def load() -> ctypes.CDLL:
         "gw_grad_dense": (S, [P, prob, P, P, P, P, I, I, P]),
         "gw_grad_noalloc": (S, [prob, P, P, P, P, I, P]),
         "gw_solve_batch": (S, [P, I, prob, P, P, P, P, P, P, P]),
+        "gw_server_create": (S, [ctypes.POINTER(P), I, ctypes.c_size_t, I]),
+        "gw_server_destroy": (None, [P]),
+        "gw_submit": (S, [P, prob, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint64)]),
+        "gw_poll": (S, [P, ctypes.c_uint64, P, ctypes.POINTER(ctypes.c_double)]),
+        "gw_server_info": (S, [P, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
+                               ctypes.POINTER(ctypes.c_size_t)]),
+        "gw_server_last_error": (ctypes.c_char_p, [P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -216,3 +223,69 @@ class Context:
         st = self.lib.gw_grad_dense(self.h, ctypes.byref(prob), _ptr(u), _ptr(v), _ptr(T), _ptr(G), marginals,
                                     precision, _stream(stream))
         return self._check(st, "gw_grad_dense")
+
+
+def _host_ptr(a):
+    """Address of a C-contiguous numpy array (or None)."""
+    if a is None:
+        return None
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host arrays must be C-contiguous")
+    return a.ctypes.data
+
+
+class Server:
+    """Owns a gw_server*: submit/poll of independent solves (host arrays)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 40 << 30, max_slots: int = 8):
+        lib = load()
+        h = ctypes.c_void_p()
+        st = lib.gw_server_create(ctypes.byref(h), device, hbm_budget_bytes, max_slots)
+        if st != GW_OK:
+            raise GWError(st, "gw_server_create failed")
+        self.h = h
+        self.lib = lib
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gw_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, prob: gw_problem, u, v, phi=None, psi=None, T_out=None) -> int:
+        """u, v (and phi, psi) float64 numpy arrays; T_out an optional numpy
+        array of n*m reals of the problem's dtype that receives the plan."""
+        t = ctypes.c_uint64()
+        st = self.lib.gw_submit(self.h, ctypes.byref(prob), _host_ptr(u), _host_ptr(v), _host_ptr(phi),
+                                _host_ptr(psi), _host_ptr(T_out), ctypes.byref(t))
+        if st != GW_OK:
+            raise GWError(st, "gw_submit")
+        if T_out is not None:
+            self._keep[t.value] = T_out
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while not finished; else (status, stats (8 floats), latency_s)."""
+        stats = (ctypes.c_double * 8)()
+        lat = ctypes.c_double()
+        st = self.lib.gw_poll(self.h, ticket, ctypes.cast(stats, ctypes.c_void_p), ctypes.byref(lat))
+        if st == GW_NOT_READY:
+            return None
+        self._keep.pop(ticket, None)
+        if st == GW_ERR_INVALID:
+            raise GWError(st, f"gw_poll: unknown or already reported ticket {ticket}")
+        return st, list(stats), lat.value
+
+    def last_error(self) -> str:
+        return self.lib.gw_server_last_error(self.h).decode()
+
+    def info(self):
+        q, c, b = ctypes.c_long(), ctypes.c_long(), ctypes.c_size_t()
+        self.lib.gw_server_info(self.h, ctypes.byref(q), ctypes.byref(c), ctypes.byref(b))
+        return q.value, c.value, b.value

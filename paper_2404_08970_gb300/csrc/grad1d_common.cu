@@ -1,5 +1,6 @@
 // Host dispatch of the structured 1D gradient and the constant-term kernels.
 #include <algorithm>
+#include <cstdio>
 #include <cmath>
 
 #include <cuda.h>
@@ -240,6 +241,43 @@ bool encode_rows_tmap(void* tmap, const void* base, int n, int m, int elem_bytes
                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   *box_cols = bc;
   return r == CUDA_SUCCESS;
+}
+
+namespace {
+thread_local char g_failure[256] = "";
+}
+void note_failure(const char* what) { snprintf(g_failure, sizeof g_failure, "%s", what); }
+const char* last_failure() { return g_failure; }
+
+bool allow_dynamic_smem(const void* func, size_t need) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(g_failure, sizeof g_failure, "shared-memory limit query: %s", cudaGetErrorString(e));
+    return false;
+  }
+  // The limit covers static and dynamic shared memory together.
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, func);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(g_failure, sizeof g_failure, "cudaFuncGetAttributes: %s", cudaGetErrorString(e));
+    return false;
+  }
+  const int dyn_max = optin - (int)fa.sharedSizeBytes;
+  if (need > (size_t)dyn_max) {
+    snprintf(g_failure, sizeof g_failure, "kernel needs %zu bytes of dynamic shared memory, limit %d", need, dyn_max);
+    return false;
+  }
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    snprintf(g_failure, sizeof g_failure, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    return false;
+  }
+  return true;
 }
 
 size_t grad1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms) {

@@ -774,7 +774,7 @@ int launch_k1c(const Grad1DArgs& g, const K1Layout& L, char* ws, int use_tma, cu
   const size_t smem = K1cSmem<K, NT, VPT, Real>::bytes(m_pad, stages);
   auto kern = k1c_grad_rows<K, NT, VPT, Real>;
   TraceScope ts(g.tracer, "k1c_grad_rows", st);
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (!allow_dynamic_smem((const void*)kern, smem))
     return GW_ERR_CUDA;
   const Real scale = (Real)(2.0 * g.out_scale * std::pow(g.hx, g.k) * std::pow(g.hy, g.k));
   const Real* cx = (const Real*)(ws + L.cx_off);
@@ -800,7 +800,7 @@ int launch_k1c_fast(const Grad1DArgs& g, const K1Layout& L, char* ws, cudaStream
   const size_t smem = FastSmem<K, NW, VPT, Real>::bytes(slot_bytes, vec_bytes, stages);
   auto kern = k1c_fast_rows<K, NW, VPT, Real>;
   TraceScope ts(g.tracer, "k1c_fast_rows", st);
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (!allow_dynamic_smem((const void*)kern, smem))
     return GW_ERR_CUDA;
   const Real scale = (Real)(2.0 * g.out_scale * std::pow(g.hx, g.k) * std::pow(g.hy, g.k));
   const Real* cx = (const Real*)(ws + L.cx_off);

@@ -74,6 +74,17 @@ struct Grad1DArgs {
   int force_generic;    // 1: use the block-scan row kernel even where the warp-specialised one applies
 };
 
+// Host-side failure notes (per thread): the launch helpers record what
+// failed before returning an error status, for the callers' messages.
+void note_failure(const char* what);
+const char* last_failure();
+
+// Lets `func` use the device's largest opt-in dynamic shared memory.  Every
+// caller sets the same value, so threads launching concurrently with
+// different shared-memory sizes do not undo each other's setting.  Returns
+// false if the attribute cannot be set or `need` exceeds the limit.
+bool allow_dynamic_smem(const void* func, size_t need);
+
 // Encodes a TMA tensor map over the rows of an n x m row-major array of
 // elem_bytes-sized reals, viewed as [n][m / E][E] with E*elem_bytes = 128,
 // 128-byte swizzle, box {E, box_cols, 1}, box_cols the largest divisor of

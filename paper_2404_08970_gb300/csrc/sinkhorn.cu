@@ -879,7 +879,7 @@ int launch_rows(SolveState<Real>* const* S, int count, bool plan, cudaStream_t s
     }
     P.block0[cnt] = blocks;
     auto kern = plan ? sk_plan<NW, VPT, Real, MAXP> : sk_pass<NW, VPT, Real, MAXP>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (!allow_dynamic_smem((const void*)kern, smem))
       return GW_ERR_CUDA;
     {
       TraceScope ts(tracer, plan ? "sk_plan" : "sk_pass", st);

@@ -143,3 +143,38 @@ def workload_batch(count: int = 256, seed: int = 0, lo: int = 256, hi: int = 819
         out.append(dict(dim=1, nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=k, eps=1e-2, n_outer=n_outer,
                         n_inner=n_inner, u=uniform_weights(n), v=uniform_weights(m)))
     return out
+
+
+SERVE_KINDS = ("1d", "1d_fgw", "2d", "2d_fgw")
+
+
+def workload_serve(count: int, rate: float, seed: int = 0, lo: int = 128, hi: int = 16384,
+                   n_outer: int = 10, n_inner: int = 50, feat_dim: int = 16):
+    """A stream of `count` requests with Poisson arrivals at `rate` per second:
+    each of the kinds 1D GW, 1D fused GW, 2D GW, 2D fused GW with probability
+    1/4; the point count of each space N log-uniform in [lo, hi] (2D: side
+    round(sqrt(N)), squared Euclidean on the unit square, |N(0,1)| image
+    marginals; 1D: k = 1, h = 1/N, uniform marginals); fused GW with
+    theta = 0.5 and feat_dim-dimensional N(0,1) features; eps = 1e-2."""
+    rng = rng_for(seed)
+    t = 0.0
+    out = []
+    for _ in range(count):
+        t += rng.exponential(1.0 / rate)
+        kind = SERVE_KINDS[int(rng.integers(0, 4))]
+        nx = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        ny = int(round(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+        r = dict(arrival=t, kind=kind, eps=1e-2, n_outer=n_outer, n_inner=n_inner, k=1, theta=1.0)
+        if kind.startswith("2d"):
+            sx, sy = int(round(np.sqrt(nx))), int(round(np.sqrt(ny)))
+            r.update(dim=2, nx=sx, ny=sy, hx=1.0 / (sx - 1), hy=1.0 / (sy - 1), cost="sqeuclid",
+                     u=abs_normal_image(sx, rng), v=abs_normal_image(sy, rng))
+            n, m = sx * sx, sy * sy
+        else:
+            r.update(dim=1, nx=nx, ny=ny, hx=1.0 / nx, hy=1.0 / ny, cost="pow",
+                     u=uniform_weights(nx), v=uniform_weights(ny))
+            n, m = nx, ny
+        if kind.endswith("fgw"):
+            r.update(theta=0.5, phi=features(n, feat_dim, rng), psi=features(m, feat_dim, rng))
+        out.append(r)
+    return out

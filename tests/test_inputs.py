@@ -24,3 +24,19 @@ def test_random_coupling_is_positive_with_marginals():
     T = I.random_coupling(u, v, rng)
     assert np.all(T > 0)
     assert np.max(np.abs(T.sum(1) - u)) < 1e-15 and np.max(np.abs(T.sum(0) - v)) < 1e-15
+
+
+def test_serve_workload_generator():
+    reqs = I.workload_serve(400, rate=2000.0, seed=0)
+    kinds = [r["kind"] for r in reqs]
+    for k in I.SERVE_KINDS:
+        assert 0.15 < kinds.count(k) / len(kinds) < 0.35
+    gaps = np.diff([0.0] + [r["arrival"] for r in reqs])
+    assert np.all(gaps > 0) and 0.5 / 2000 < gaps.mean() < 1.5 / 2000
+    for r in reqs:
+        n = r["nx"] ** 2 if r["dim"] == 2 else r["nx"]
+        m = r["ny"] ** 2 if r["dim"] == 2 else r["ny"]
+        assert 100 <= n <= 16384 + 300 and 100 <= m <= 16384 + 300
+        assert abs(r["u"].sum() - 1) < 1e-12 and r["u"].size == n
+        if r["kind"].endswith("fgw"):
+            assert r["phi"].shape == (n, 16) and r["psi"].shape == (m, 16) and r["theta"] == 0.5
