@@ -1,6 +1,7 @@
 // Host dispatch of the structured 1D gradient and the constant-term kernels.
 #include <algorithm>
 #include <cstdio>
+#include <vector>
 #include <cmath>
 
 #include <cuda.h>
@@ -249,10 +250,34 @@ thread_local char g_failure[256] = "";
 void note_failure(const char* what) { snprintf(g_failure, sizeof g_failure, "%s", what); }
 const char* last_failure() { return g_failure; }
 
+namespace {
+// Functions whose attribute is already set, per device, with their limit.
+struct SmemGrant {
+  const void* func;
+  int dev, limit;
+};
+std::mutex g_grant_mu;
+std::vector<SmemGrant> g_grants;
+}  // namespace
+
 bool allow_dynamic_smem(const void* func, size_t need) {
   int dev = 0, optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    note_failure("cudaGetDevice failed");
+    return false;
+  }
+  {
+    std::lock_guard<std::mutex> lk(g_grant_mu);
+    for (const auto& gr : g_grants)
+      if (gr.func == func && gr.dev == dev) {
+        if (need <= (size_t)gr.limit) return true;
+        snprintf(g_failure, sizeof g_failure, "kernel needs %zu bytes of dynamic shared memory, limit %d", need,
+                 gr.limit);
+        return false;
+      }
+  }
+  cudaError_t e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) {
     cudaGetLastError();
     snprintf(g_failure, sizeof g_failure, "shared-memory limit query: %s", cudaGetErrorString(e));
@@ -277,6 +302,8 @@ bool allow_dynamic_smem(const void* func, size_t need) {
     snprintf(g_failure, sizeof g_failure, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
     return false;
   }
+  std::lock_guard<std::mutex> lk(g_grant_mu);
+  g_grants.push_back({func, dev, dyn_max});
   return true;
 }
 

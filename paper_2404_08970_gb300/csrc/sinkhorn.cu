@@ -198,27 +198,40 @@ __device__ __forceinline__ float scale_of(float lu, float S) { return ex2(lu) * 
 __device__ __forceinline__ double scale_of(double lu, double S) { return exp2(lu) / S; }
 
 // Shared memory of sk_pass (128-byte aligned base):
-//   ring [stages][slot_bytes] | red [2][NW] Real | Fold, LU [R] Real |
-//   full [stages] mbarriers
-template <int NW, typename Real>
+//   ring [NG][stages][slot_bytes] (reused at the end for the groups' column
+//   sums, [NG][cover] Real) | red [NG][2][NW] Real | sfb [NG][NW] Real |
+//   Fold, LU [R] Real | full [NG][stages] mbarriers
+template <int NW, int VPT, int NG, typename Real>
 size_t pass_smem_bytes(const RowGeom& g, int R) {
-  return 128 + (size_t)g.stages * g.slot_bytes + sizeof(Real) * (2 * NW + 2 * (size_t)R) + 16 + 8 * (size_t)g.stages;
+  const size_t ring = std::max((size_t)NG * g.stages * g.slot_bytes, (size_t)NG * 32 * NW * VPT * sizeof(Real));
+  return 128 + ring + sizeof(Real) * (3 * NG * NW + 2 * (size_t)R) + 16 + 8 * (size_t)NG * g.stages;
 }
 // Shared memory of sk_plan: ring | full [stages] mbarriers.
 inline size_t plan_smem_bytes(const RowGeom& g) { return 128 + (size_t)g.stages * g.slot_bytes + 8 * g.stages + 16; }
 
+// Barrier of the NW warps of row group g (named barrier 1 + g; a group of
+// one warp needs only a warp barrier).
+template <int NW>
+__device__ __forceinline__ void group_sync(int g) {
+  if constexpr (NW == 1) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(1 + g), "r"(32 * NW) : "memory");
+  }
+}
+
 // Row sum out of range: redo the row from the ring with a max shift,
 // M = max_p e_p, S2 = sum_p 2^(e_p - M), e = F_old + G - c Pi (all threads of
-// the block call it for the same row; padded columns have G = -inf).
+// the row group call it for the same row; padded columns have G = -inf).
 // Returns the new potential and adds the row's plan entries to acc.  The
 // row is read again from the ring, so nothing of the row pass stays live
-// across the block barrier.
+// across the group barrier.
 template <int NW, int VPT, typename Real>
-__device__ __forceinline__ Real row_redo(const Real* row, int m, Real c, const Real (&Gv)[VPT], Real Fo, Real lut,
-                                         Real (&acc)[VPT], Real* sfb) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ Real row_redo(const Real* row, int gt, int g, int m, Real c, const Real (&Gv)[VPT],
+                                         Real Fo, Real lut, Real (&acc)[VPT], Real* sfb) {
+  const int lane = gt & 31, wig = gt >> 5;
   Real x[VPT];
-  load_vals<VPT, 32 * NW>(row, threadIdx.x, m, x);
+  load_vals<VPT, 32 * NW>(row, gt, m, x);
   Real e[VPT];
   Real lm = -INFINITY;
 #pragma unroll
@@ -227,8 +240,8 @@ __device__ __forceinline__ Real row_redo(const Real* row, int m, Real c, const R
     lm = fmax(lm, e[v]);
   }
   lm = warp_max(lm);
-  if (lane == 0) sfb[warp] = lm;
-  __syncthreads();
+  if (lane == 0) sfb[wig] = lm;
+  group_sync<NW>(g);
   Real M = -INFINITY;
 #pragma unroll
   for (int q = 0; q < NW; ++q) M = fmax(M, sfb[q]);
@@ -236,16 +249,16 @@ __device__ __forceinline__ Real row_redo(const Real* row, int m, Real c, const R
 #pragma unroll
   for (int v = 0; v < VPT; ++v) s2 += ex2(e[v] - M);
   s2 = warp_sum(s2);
-  __syncthreads();
-  if (lane == 0) sfb[warp] = s2;
-  __syncthreads();
+  group_sync<NW>(g);
+  if (lane == 0) sfb[wig] = s2;
+  group_sync<NW>(g);
   Real S2 = 0;
 #pragma unroll
   for (int q = 0; q < NW; ++q) S2 += sfb[q];
   const Real Fn = Fo + lut - (M + lg2(S2));
 #pragma unroll
   for (int v = 0; v < VPT; ++v) acc[v] += ex2(Fn + e[v] - Fo);
-  __syncthreads();
+  group_sync<NW>(g);
   return Fn;
 }
 
@@ -255,16 +268,24 @@ __device__ __forceinline__ Real row_redo(const Real* row, int m, Real c, const R
 // Row j: w_j,p = 2^(F_old,j + G_p - c Pi_jp) (every w <= v_p after a column
 // update), S_j = sum_p w_j,p.  The new potential is F_j + log2(u_j / S_j) and
 // the column sums need 2^(F_new,j + G_p - c Pi_jp) = (u_j / S_j) w_j,p, so one
-// exp2 per element serves both.  Thread t owns columns t*VPT .. t*VPT+VPT-1;
-// per row: the row pass, one block barrier (the row sum needs every warp),
-// then thread 0 refills the ring slot and every thread adds r_j w_j to its
-// column sums.  A row sum out of range is redone from the ring with a max
-// shift (block-uniform branch).
+// exp2 per element serves both.
+//
+// The block holds NG row groups of NW warps; group g takes the band's rows
+// g, g + NG, g + 2 NG, ... through its own ring of bulk-copied rows, so short
+// rows do not leave the block idle behind one barrier per row.  In a group,
+// thread t owns the columns col_of(t, v); per row: the row pass, one group
+// barrier (the row sum needs every warp of the group; none for a one-warp
+// group), then the group's first thread refills the slot and every thread
+// adds r_j w_j to its column sums.  At the end the groups' column sums are
+// added in shared memory.  A row sum out of range is redone from the ring
+// with a max shift (group-uniform branch).
 // ---------------------------------------------------------------------------
-template <int NW, int VPT, typename Real, int MAXP>
-__global__ void __launch_bounds__(32 * NW, 1)
+template <int NW, int VPT, int NG, typename Real, int MAXP>
+__global__ void __launch_bounds__(32 * NW * NG, 1)
     sk_pass(const __grid_constant__ SkBatch<Real, MAXP> P, unsigned* status) {
-  constexpr int NT = 32 * NW;
+  constexpr int GT = 32 * NW;  // threads of a row group
+  constexpr int NT = GT * NG;
+  constexpr int COVER = GT * VPT;
   const int pi = batch_problem(P);
   const SkProb<Real>& pr = P.p[pi];
   const int S = pr.geo.stages, slot_bytes = pr.geo.slot_bytes;
@@ -277,93 +298,119 @@ __global__ void __launch_bounds__(32 * NW, 1)
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   unsigned char* sm = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
   unsigned char* ring = sm;
-  Real* red = reinterpret_cast<Real*>(ring + (size_t)S * slot_bytes);  // 16-byte aligned
-  Real* Fold = red + 2 * NW;
+  const size_t ring_bytes = (size_t)NG * S * slot_bytes > (size_t)NG * COVER * sizeof(Real)
+                                ? (size_t)NG * S * slot_bytes
+                                : (size_t)NG * COVER * sizeof(Real);
+  Real* red = reinterpret_cast<Real*>(ring + ring_bytes);  // 16-byte aligned
+  Real* sfb = red + 2 * NG * NW;
+  Real* Fold = sfb + NG * NW;
   Real* LU = Fold + R;
   unsigned char* braw = reinterpret_cast<unsigned char*>(LU + R);
   uint64_t* full = reinterpret_cast<uint64_t*>(braw + ((8u - (smem_u32(braw) & 7u)) & 7u));
-  __shared__ Real sfb[32];  // fallback reductions
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, g = tid / GT, gt = tid % GT, lane = tid & 31, wig = gt >> 5;
   const int a = (int)blockIdx.x - P.block0[pi], s = a * R, Ra = min(R, n - s);
-  auto issue = [&](int t) {
+  unsigned char* gring = ring + (size_t)g * S * slot_bytes;
+  uint64_t* gfull = full + g * S;
+  // Row k of group g is band row g + k NG, in slot k mod S.
+  auto issue = [&](int k) {
+    const int t = g + k * NG;
     const char* src;
     unsigned bytes;
     int off;
     row_span(Pi, m, s + t, &src, &bytes, &off);
-    mbar_arrive_expect_tx(&full[t % S], bytes);
-    bulk_g2s(ring + (size_t)(t % S) * slot_bytes, src, bytes, &full[t % S]);
+    mbar_arrive_expect_tx(&gfull[k % S], bytes);
+    bulk_g2s(gring + (size_t)(k % S) * slot_bytes, src, bytes, &gfull[k % S]);
   };
   // Past the row's end a slot holds up to 24 bytes of what follows the row in
   // Pi (finite), or the zeros written here: finite values that the -inf of the
   // padded columns' G turns into exact zeros, with no per-element masks.
   const size_t row_bytes = (size_t)m * sizeof(Real);
-  for (int q = 0; q < S; ++q)
+  for (int q = 0; q < NG * S; ++q)
     for (size_t b = row_bytes + 4 * (size_t)tid; b + 4 <= (size_t)slot_bytes; b += 4 * (size_t)NT)
       *reinterpret_cast<unsigned*>(ring + (size_t)q * slot_bytes + b) = 0u;
   fence_proxy_async_smem();
-  __syncthreads();
   if (tid == 0) {
-    for (int i = 0; i < S; ++i) mbar_init(&full[i], 1);
+    for (int i = 0; i < NG * S; ++i) mbar_init(&full[i], 1);
     fence_mbar_init();
-    for (int t = 0; t < S && t < Ra; ++t) issue(t);
   }
   for (int t = tid; t < Ra; t += NT) {
     Fold[t] = F[s + t];
     LU[t] = pr.lu[s + t];
   }
+  __syncthreads();
+  if (gt == 0)
+    for (int k = 0; k < S && g + k * NG < Ra; ++k) issue(k);
   Real Gv[VPT], acc[VPT];
 #pragma unroll
   for (int v = 0; v < VPT; ++v) {
-    const int p = col_of<Real>(tid, v, NT);
+    const int p = col_of<Real>(gt, v, GT);
     Gv[v] = p < m ? pr.G[p] : (Real)-INFINITY;
     acc[v] = 0;
   }
-  __syncthreads();
-  auto row_ptr = [&](int t) {
+  Real* gred = red + g * 2 * NW;
+  Real* gsfb = sfb + g * NW;
+  for (int k = 0;; ++k) {
+    const int t = g + k * NG;
+    if (t >= Ra) break;
+    mbar_wait_bounded(&gfull[k % S], (unsigned)((k / S) & 1), status);
     const int off = (int)((((size_t)(s + t) * (size_t)m * sizeof(Real)) & 15) / sizeof(Real));
-    return reinterpret_cast<const Real*>(ring + (size_t)(t % S) * slot_bytes) + off;
-  };
-
-  for (int t = 0; t < Ra; ++t) {
-    mbar_wait_bounded(&full[t % S], (unsigned)((t / S) & 1), status);
+    const Real* row = reinterpret_cast<const Real*>(gring + (size_t)(k % S) * slot_bytes) + off;
     Real x[VPT], w[VPT];
-    load_vals<VPT, NT>(row_ptr(t), tid, m, x);
+    load_vals<VPT, GT>(row, gt, m, x);
     const Real Fo = Fold[t];
 #pragma unroll
     for (int v = 0; v < VPT; ++v) w[v] = ex2(fma(-c, x[v], Gv[v] + Fo));
-    const Real sum = warp_sum(tree_sum<VPT>(w));
-    Real* rb = red + (t & 1) * NW;
-    if (lane == 0) rb[warp] = sum;
-    __syncthreads();
-    const Real St = tree_sum_smem<NW>(rb);
+    Real St = warp_sum(tree_sum<VPT>(w));
+    if constexpr (NW > 1) {
+      Real* rb = gred + (k & 1) * NW;
+      if (lane == 0) rb[wig] = St;
+      group_sync<NW>(g);
+      St = tree_sum_smem<NW>(rb);
+    }
     const Real lut = LU[t];
+    const bool more = t + S * NG < Ra;
     if (St >= tiny_sum<Real>() && St <= (Real)1e30) {
-      // Every thread has read row t: its slot takes row t + S.
-      if (tid == 0 && t + S < Ra) {
+      // Every thread of the group has read row t: its slot takes row k + S.
+      if (gt == 0 && more) {
         fence_proxy_async_smem();
-        issue(t + S);
+        issue(k + S);
       }
       const Real r = scale_of(lut, St);
 #pragma unroll
       for (int v = 0; v < VPT; ++v) acc[v] = fma(r, w[v], acc[v]);
-      if (tid == 0) F[s + t] = Fo + lut - lg2(St);
+      if (gt == 0) F[s + t] = Fo + lut - lg2(St);
     } else {
-      const Real Fn = row_redo<NW, VPT, Real>(row_ptr(t), m, c, Gv, Fo, lut, acc, sfb);
-      if (tid == 0) {
+      const Real Fn = row_redo<NW, VPT, Real>(row, gt, g, m, c, Gv, Fo, lut, acc, gsfb);
+      if (gt == 0) {
         F[s + t] = Fn;
-        if (t + S < Ra) {
+        if (more) {
           fence_proxy_async_smem();
-          issue(t + S);
+          issue(k + S);
         }
       }
     }
   }
   // Band partials of the column sums (relative to the current G).
+  if constexpr (NG == 1) {
 #pragma unroll
-  for (int v = 0; v < VPT; ++v) {
-    const int p = col_of<Real>(tid, v, NT);
-    if (p < m) part[(size_t)a * m + p] = acc[v];
+    for (int v = 0; v < VPT; ++v) {
+      const int p = col_of<Real>(gt, v, GT);
+      if (p < m) part[(size_t)a * m + p] = acc[v];
+    }
+  } else {
+    // Every copy was consumed, so the ring is free: add the groups' sums.
+    __syncthreads();
+    Real* cs = reinterpret_cast<Real*>(ring);
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) cs[(size_t)g * COVER + col_of<Real>(gt, v, GT)] = acc[v];
+    __syncthreads();
+    for (int p = tid; p < m; p += NT) {
+      Real sum = 0;
+#pragma unroll
+      for (int q = 0; q < NG; ++q) sum += cs[(size_t)q * COVER + p];
+      part[(size_t)a * m + p] = sum;
+    }
   }
 }
 
@@ -573,22 +620,97 @@ __global__ void fill_val(Real* __restrict__ x, int len, Real val) {
   if (i < len) x[i] = val;
 }
 
-// Pi += (1 - theta) ||phi_i - psi_p||^2, features as doubles (row-major,
-// n x D and m x D).  One block per row, psi read through L1/L2.
+// Pi += w ||phi_i - psi_p||^2 (w = 1 - theta), features as doubles (row-major
+// n x D and m x D, D <= 64).  A block covers 256 columns x 16 rows: each
+// thread keeps its column's features in registers (in the arithmetic type:
+// D squared differences of order-one features add up without cancellation),
+// the block's 16 rows of features sit in shared memory.
+constexpr int kFeatRows = 16;
 template <typename Real>
-__global__ void add_feature_cost(Real* __restrict__ Pi, int n, int m, int D, const double* __restrict__ phi,
-                                 const double* __restrict__ psi, double w) {
-  __shared__ double ph[64];
-  const int i = blockIdx.x;
-  if (threadIdx.x < D) ph[threadIdx.x] = phi[(size_t)i * D + threadIdx.x];
+__global__ void __launch_bounds__(256) add_feature_cost(Real* __restrict__ Pi, int n, int m, int D,
+                                                        const double* __restrict__ phi,
+                                                        const double* __restrict__ psi, double w) {
+  __shared__ Real ph[kFeatRows][64];
+  const int p = blockIdx.x * 256 + threadIdx.x;
+  const int i0 = blockIdx.y * kFeatRows;
+  for (int e = threadIdx.x; e < kFeatRows * D; e += 256) {
+    const int r = e / D, d = e % D;
+    ph[r][d] = i0 + r < n ? (Real)phi[(size_t)(i0 + r) * D + d] : (Real)0;
+  }
   __syncthreads();
-  for (int p = threadIdx.x; p < m; p += blockDim.x) {
-    double acc = 0.0;
-    for (int d = 0; d < D; ++d) {
-      const double diff = ph[d] - psi[(size_t)p * D + d];
-      acc += diff * diff;
+  if (p >= m) return;
+  Real ps[64];
+#pragma unroll
+  for (int d = 0; d < 64; ++d) ps[d] = d < D ? (Real)psi[(size_t)p * D + d] : (Real)0;
+  const Real wr = (Real)w;
+  for (int r = 0; r < kFeatRows && i0 + r < n; ++r) {
+    Real acc = 0;
+#pragma unroll
+    for (int d = 0; d < 64; ++d) {
+      if (d < D) {
+        const Real diff = ph[r][d] - ps[d];
+        acc = fma(diff, diff, acc);
+      }
     }
-    Pi[(size_t)i * m + p] += (Real)(w * acc);
+    Real* q = Pi + (size_t)(i0 + r) * m + p;
+    *q = fma(wr, acc, *q);
+  }
+}
+
+// Partial sums of <CC, T>, CC_ip = ||phi_i - psi_p||^2, over the same tiles
+// (FP64 accumulation per thread, one partial per block).
+template <typename Real>
+__global__ void __launch_bounds__(256) feature_dot_tiles(const Real* __restrict__ T, int n, int m, int D,
+                                                         const double* __restrict__ phi,
+                                                         const double* __restrict__ psi, double* __restrict__ part) {
+  __shared__ double ph[kFeatRows][64];
+  __shared__ double sm[8];
+  const int p = blockIdx.x * 256 + threadIdx.x;
+  const int i0 = blockIdx.y * kFeatRows;
+  for (int e = threadIdx.x; e < kFeatRows * D; e += 256) {
+    const int r = e / D, d = e % D;
+    ph[r][d] = i0 + r < n ? phi[(size_t)(i0 + r) * D + d] : 0.0;
+  }
+  __syncthreads();
+  double tot = 0.0;
+  if (p < m) {
+    double ps[64];
+#pragma unroll
+    for (int d = 0; d < 64; ++d) ps[d] = d < D ? psi[(size_t)p * D + d] : 0.0;
+    for (int r = 0; r < kFeatRows && i0 + r < n; ++r) {
+      double cc = 0.0;
+#pragma unroll
+      for (int d = 0; d < 64; ++d) {
+        if (d < D) {
+          const double diff = ph[r][d] - ps[d];
+          cc = fma(diff, diff, cc);
+        }
+      }
+      tot += cc * (double)T[(size_t)(i0 + r) * m + p];
+    }
+  }
+  tot = warp_sum(tot);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = tot;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < 8; ++q) t += sm[q];
+    part[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Sums `count` partials into out[0] (one block, fixed order).
+__global__ void sum_partials(const double* __restrict__ part, int count, double* __restrict__ out) {
+  __shared__ double sm[32];
+  double t = 0.0;
+  for (int k = threadIdx.x; k < count; k += blockDim.x) t += part[k];
+  t = warp_sum(t);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += sm[w];
+    out[0] = r;
   }
 }
 
@@ -598,32 +720,6 @@ __global__ void dot_partial(const Real* __restrict__ A, const Real* __restrict__
   double acc = 0.0;
   for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x)
     acc += (double)A[k] * (double)B[k];
-  __shared__ double sm[32];
-  acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w];
-    part[blockIdx.x] = s;
-  }
-}
-
-// <CC, T> with CC_ip = ||phi_i - psi_p||^2 computed on the fly.
-template <typename Real>
-__global__ void feature_dot_partial(const Real* __restrict__ T, int n, int m, int D, const double* __restrict__ phi,
-                                    const double* __restrict__ psi, double* __restrict__ part) {
-  double acc = 0.0;
-  const size_t N = (size_t)n * m;
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = k / m, p = k % m;
-    double cc = 0.0;
-    for (int d = 0; d < D; ++d) {
-      const double diff = phi[i * D + d] - psi[p * D + d];
-      cc += diff * diff;
-    }
-    acc += cc * (double)T[k];
-  }
   __shared__ double sm[32];
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = acc;
@@ -682,16 +778,15 @@ __global__ void potentials_out(const Real* __restrict__ F, int len, double scale
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-// Ring slots hold one row, its alignment offset (< 16 bytes) and the VPT
-// elements a thread straddling the row's end reads past it; as many slots as
-// fit in about 200 KB next to the small arrays, from 2 to 6.
-template <int NW, int VPT, typename Real>
-RowGeom row_geom(int m, int R) {
+// Ring slots hold one row, its alignment offset (< 16 bytes) and the few
+// elements a thread straddling the row's end reads past it.  Each of the NG
+// row groups gets `stages` slots: as many as fit in about 150 KB, from 2 to
+// 6.
+template <int NW, int VPT, int NG, typename Real>
+RowGeom row_geom(int m) {
   RowGeom g{};
-  g.slot_bytes = (int)((((size_t)m + VPT + 8) * sizeof(Real) + 127) / 128 * 128);
-  const size_t fixed = pass_smem_bytes<NW, Real>(RowGeom{0, 0}, R);
-  g.stages = (int)std::max<size_t>(2, std::min<size_t>(6, (200 * 1024 - std::min<size_t>(fixed, 100 * 1024)) /
-                                                             g.slot_bytes));
+  g.slot_bytes = (int)((((size_t)m + 16 + 8) * sizeof(Real) + 127) / 128 * 128);
+  g.stages = (int)std::max<size_t>(2, std::min<size_t>(6, (150 * 1024) / ((size_t)NG * g.slot_bytes)));
   return g;
 }
 
@@ -718,7 +813,7 @@ struct SolveState {
   size_t smem_pass, smem_plan;
 };
 
-template <int NW, int VPT, typename Real>
+template <int NW, int VPT, int NG, typename Real>
 int prepare(const SolveArgs& A, void* wsv, size_t ws_bytes, SolveState<Real>* S) {
   const int n = A.n, m = A.m;
   const Bands bands = solve_bands(A);
@@ -751,8 +846,8 @@ int prepare(const SolveArgs& A, void* wsv, size_t ws_bytes, SolveState<Real>* S)
   S->gws_bytes = ws_bytes - off;
   k.T = (Real*)A.T;
   k.u = A.u;
-  k.geo = row_geom<NW, VPT, Real>(m, k.R);
-  S->smem_pass = pass_smem_bytes<NW, Real>(k.geo, k.R);
+  k.geo = row_geom<NW, VPT, NG, Real>(m);
+  S->smem_pass = pass_smem_bytes<NW, VPT, NG, Real>(k.geo, k.R);
   S->smem_plan = plan_smem_bytes(k.geo);
   S->A = &A;
   return GW_OK;
@@ -829,7 +924,8 @@ int step_cost(const SolveState<Real>& S, cudaStream_t st) {
   if (rc != GW_OK) return rc;
   if (fused<Real>(A)) {
     TraceScope ts(A.tracer, "add_feature_cost", st);
-    add_feature_cost<Real><<<A.n, 256, 0, st>>>((Real*)S.sk.Pi, A.n, A.m, A.feat_dim, A.phi, A.psi, 1.0 - A.theta);
+    const dim3 grid((A.m + 255) / 256, (A.n + kFeatRows - 1) / kFeatRows);
+    add_feature_cost<Real><<<grid, 256, 0, st>>>((Real*)S.sk.Pi, A.n, A.m, A.feat_dim, A.phi, A.psi, 1.0 - A.theta);
   }
   TraceScope ts(A.tracer, "solve_setup", st);
   fill_val<Real><<<(A.n + 255) / 256, 256, 0, st>>>(S.sk.F, A.n, (Real)0);
@@ -851,8 +947,15 @@ int step_finish(const SolveState<Real>& S, cudaStream_t st) {
   if (rc != GW_OK) return rc;
   dot_partial<Real><<<kDots, 256, 0, st>>>(S.sk.Pi, (const Real*)A.T, (size_t)n * m, S.dotE);
   if (fused<Real>(A))
-    feature_dot_partial<Real><<<kDots, 256, 0, st>>>((const Real*)A.T, n, m, A.feat_dim, A.phi, A.psi, S.dotC);
-  else
+  {
+    // <CC, T>: tile partials in Pi's storage (free after the dot above), summed
+    // into dotC[0]; the other kDots - 1 entries are zero.
+    const dim3 grid((m + 255) / 256, (n + kFeatRows - 1) / kFeatRows);
+    double* tiles = reinterpret_cast<double*>(const_cast<Real*>(S.sk.Pi));
+    feature_dot_tiles<Real><<<grid, 256, 0, st>>>((const Real*)A.T, n, m, A.feat_dim, A.phi, A.psi, tiles);
+    fill_val<double><<<1, 256, 0, st>>>(S.dotC, kDots, 0.0);
+    sum_partials<<<1, 256, 0, st>>>(tiles, (int)(grid.x * grid.y), S.dotC);
+  } else
     fill_val<double><<<1, 256, 0, st>>>(S.dotC, kDots, 0.0);
   finish_stats<<<1, 256, 0, st>>>(S.dotE, kDots, S.dotC, kDots, S.sk.cta_stats, S.sk.B, S.sk.colpart, m, A.v, A.eps,
                                   A.theta, A.n_outer, A.stats);
@@ -861,7 +964,7 @@ int step_finish(const SolveState<Real>& S, cudaStream_t st) {
 
 // Launches one Sinkhorn pass (rows, then columns), or the plan, over a list
 // of problems in parameter blocks of up to MAXP problems each.
-template <int NW, int VPT, typename Real, int MAXP>
+template <int NW, int VPT, int NG, typename Real, int MAXP>
 int launch_rows(SolveState<Real>* const* S, int count, bool plan, cudaStream_t st, unsigned* status,
                 Tracer* tracer) {
   for (int base = 0; base < count; base += MAXP) {
@@ -878,12 +981,12 @@ int launch_rows(SolveState<Real>* const* S, int count, bool plan, cudaStream_t s
       smem = std::max(smem, plan ? S[base + q]->smem_plan : S[base + q]->smem_pass);
     }
     P.block0[cnt] = blocks;
-    auto kern = plan ? sk_plan<NW, VPT, Real, MAXP> : sk_pass<NW, VPT, Real, MAXP>;
+    auto kern = plan ? sk_plan<NW, VPT, Real, MAXP> : sk_pass<NW, VPT, NG, Real, MAXP>;
     if (!allow_dynamic_smem((const void*)kern, smem))
       return GW_ERR_CUDA;
     {
       TraceScope ts(tracer, plan ? "sk_plan" : "sk_pass", st);
-      kern<<<blocks, 32 * NW, smem, st>>>(P, status);
+      kern<<<blocks, plan ? 32 * NW : 32 * NW * NG, smem, st>>>(P, status);
     }
     if (plan) continue;
     // Column update: blocks of 32 columns.
@@ -899,11 +1002,11 @@ int launch_rows(SolveState<Real>* const* S, int count, bool plan, cudaStream_t s
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }
 
-template <int NW, int VPT, typename Real>
+template <int NW, int VPT, int NG, typename Real>
 int solve_typed(const SolveArgs& A, void* ws, size_t ws_bytes) {
   cudaStream_t st = A.stream;
   SolveState<Real> S;
-  int rc = prepare<NW, VPT, Real>(A, ws, ws_bytes, &S);
+  int rc = prepare<NW, VPT, NG, Real>(A, ws, ws_bytes, &S);
   if (rc != GW_OK) return rc;
   SolveState<Real>* list[1] = {&S};
   step_setup(S, st);
@@ -911,10 +1014,10 @@ int solve_typed(const SolveArgs& A, void* ws, size_t ws_bytes) {
     rc = step_cost(S, st);
     if (rc != GW_OK) return rc;
     for (int it = 0; it < A.n_inner; ++it) {
-      rc = launch_rows<NW, VPT, Real, 1>(list, 1, false, st, A.status, A.tracer);
+      rc = launch_rows<NW, VPT, NG, Real, 1>(list, 1, false, st, A.status, A.tracer);
       if (rc != GW_OK) return rc;
     }
-    rc = launch_rows<NW, VPT, Real, 1>(list, 1, true, st, A.status, A.tracer);
+    rc = launch_rows<NW, VPT, NG, Real, 1>(list, 1, true, st, A.status, A.tracer);
     if (rc != GW_OK) return rc;
   }
   rc = step_finish(S, st);
@@ -925,12 +1028,12 @@ int solve_typed(const SolveArgs& A, void* ws, size_t ws_bytes) {
 // A group of problems with the same row configuration and schedule, advanced
 // in lock step on one stream: each Sinkhorn pass is one launch (per 32
 // problems) over all of the group's row bands.
-template <int NW, int VPT, typename Real>
+template <int NW, int VPT, int NG, typename Real>
 int solve_group(const SolveArgs* const* A, void* const* ws, const size_t* ws_bytes, int count, cudaStream_t st) {
   std::vector<SolveState<Real>> S(count);
   std::vector<SolveState<Real>*> list(count);
   for (int i = 0; i < count; ++i) {
-    int rc = prepare<NW, VPT, Real>(*A[i], ws[i], ws_bytes[i], &S[i]);
+    int rc = prepare<NW, VPT, NG, Real>(*A[i], ws[i], ws_bytes[i], &S[i]);
     if (rc != GW_OK) return rc;
     list[i] = &S[i];
   }
@@ -943,10 +1046,10 @@ int solve_group(const SolveArgs* const* A, void* const* ws, const size_t* ws_byt
       if (rc != GW_OK) return rc;
     }
     for (int it = 0; it < A[0]->n_inner; ++it) {
-      int rc = launch_rows<NW, VPT, Real, 32>(list.data(), count, false, st, status, tracer);
+      int rc = launch_rows<NW, VPT, NG, Real, 32>(list.data(), count, false, st, status, tracer);
       if (rc != GW_OK) return rc;
     }
-    int rc = launch_rows<NW, VPT, Real, 32>(list.data(), count, true, st, status, tracer);
+    int rc = launch_rows<NW, VPT, NG, Real, 32>(list.data(), count, true, st, status, tracer);
     if (rc != GW_OK) return rc;
   }
   for (auto& s : S) {
@@ -956,32 +1059,39 @@ int solve_group(const SolveArgs* const* A, void* const* ws, const size_t* ws_byt
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }
 
-// Row configuration (warps, values per thread) of the Sinkhorn kernels for m
-// columns; the configuration index groups batched problems.
+// Row configuration of the Sinkhorn kernels for m columns: warps per row
+// group NW, values per thread VPT (32 NW VPT >= m), row groups per block NG.
+// The configuration index also groups batched problems.
 int row_config(int m, int dtype) {
   if (dtype == GW_F32) {
-    if (m <= 1024) return 0;
-    if (m <= 4096) return 1;
-    if (m <= 8192) return 2;
-    if (m <= 9216) return 3;
-    return 4;
+    if (m <= 512) return 0;
+    if (m <= 1024) return 1;
+    if (m <= 2048) return 2;
+    if (m <= 4096) return 3;
+    if (m <= 8192) return 4;
+    if (m <= 9216) return 5;
+    return 6;
   }
-  if (m <= 1024) return 10;
-  if (m <= 4096) return 11;
-  return 12;
+  if (m <= 256) return 10;
+  if (m <= 1024) return 11;
+  if (m <= 4096) return 12;
+  return 13;
 }
 
 template <typename F>
 int with_config(int cfg, F&& f) {
   switch (cfg) {
-    case 0: return f.template run<8, 4, float>();
-    case 1: return f.template run<16, 8, float>();
-    case 2: return f.template run<16, 16, float>();
-    case 3: return f.template run<18, 16, float>();
-    case 4: return f.template run<32, 16, float>();
-    case 10: return f.template run<8, 4, double>();
-    case 11: return f.template run<16, 8, double>();
-    default: return f.template run<32, 16, double>();
+    case 0: return f.template run<1, 16, 16, float>();
+    case 1: return f.template run<2, 16, 8, float>();
+    case 2: return f.template run<4, 16, 4, float>();
+    case 3: return f.template run<8, 16, 2, float>();
+    case 4: return f.template run<16, 16, 1, float>();
+    case 5: return f.template run<18, 16, 1, float>();
+    case 6: return f.template run<32, 16, 1, float>();
+    case 10: return f.template run<1, 8, 16, double>();
+    case 11: return f.template run<4, 8, 4, double>();
+    case 12: return f.template run<16, 8, 1, double>();
+    default: return f.template run<32, 16, 1, double>();
   }
 }
 
@@ -1011,9 +1121,9 @@ struct SingleRun {
   const SolveArgs& A;
   void* ws;
   size_t bytes;
-  template <int NW, int VPT, typename Real>
+  template <int NW, int VPT, int NG, typename Real>
   int run() {
-    return solve_typed<NW, VPT, Real>(A, ws, bytes);
+    return solve_typed<NW, VPT, NG, Real>(A, ws, bytes);
   }
 };
 struct GroupRun {
@@ -1022,9 +1132,9 @@ struct GroupRun {
   const size_t* bytes;
   int count;
   cudaStream_t st;
-  template <int NW, int VPT, typename Real>
+  template <int NW, int VPT, int NG, typename Real>
   int run() {
-    return solve_group<NW, VPT, Real>(A, ws, bytes, count, st);
+    return solve_group<NW, VPT, NG, Real>(A, ws, bytes, count, st);
   }
 };
 }  // namespace
