@@ -6,6 +6,7 @@
 #include <cublas_v2.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "gw_common.cuh"
@@ -34,19 +35,39 @@ __global__ void build_dist(Out* __restrict__ D, int n, double hk, int k, int sid
   }
 }
 
-__global__ void to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, size_t N) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+// Four floats -> four bfloat16 per thread (16-byte loads, 8-byte stores);
+// N a multiple of 4, both arrays 16-byte aligned.
+__global__ void to_bf16(const float4* __restrict__ x, __nv_bfloat162* __restrict__ y, size_t N4) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = x[i];
+    y[2 * i] = __floats2bfloat162_rn(v.x, v.y);
+    y[2 * i + 1] = __floats2bfloat162_rn(v.z, v.w);
+  }
+}
+__global__ void to_bf16_tail(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, size_t from, size_t N) {
+  for (size_t i = from + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
     y[i] = __float2bfloat16_rn(x[i]);
 }
 
 // G = cx_i + cy_p - s * Z_ip, in place on Z (= G).  cx, cy hold hi parts first.
+// One block per matrix row, 16-byte accesses when the rows allow them.
 template <typename Real>
 __global__ void dense_epilogue(Real* __restrict__ G, int n, int m, const Real* __restrict__ cx,
                                const Real* __restrict__ cy, Real s) {
-  const size_t N = (size_t)n * m;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = idx / m, p = idx % m;
-    G[idx] = fma(-s, G[idx], cx[i] + cy[p]);
+  constexpr int PER = 16 / sizeof(Real);
+  const int i = blockIdx.x;
+  Real* row = G + (size_t)i * m;
+  const Real ci = cx[i];
+  if (m % PER == 0 && ((reinterpret_cast<uintptr_t>(G) & 15) == 0)) {
+    for (int q = threadIdx.x; q < m / PER; q += blockDim.x) {
+      float4 z = reinterpret_cast<float4*>(row)[q];
+      Real* e = reinterpret_cast<Real*>(&z);
+#pragma unroll
+      for (int w = 0; w < PER; ++w) e[w] = fma(-s, e[w], ci + cy[q * PER + w]);
+      reinterpret_cast<float4*>(row)[q] = z;
+    }
+  } else {
+    for (int p = threadIdx.x; p < m; p += blockDim.x) row[p] = fma(-s, row[p], ci + cy[p]);
   }
 }
 
@@ -233,7 +254,12 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
   {
     TraceScope ts(a.tracer, "dense_gemm", st);
     if (a.prec == GW_DENSE_BF16) {
-      to_bf16<<<4 * 152, 256, 0, st>>>((const float*)a.T, (__nv_bfloat16*)Tin, nm);
+      if ((reinterpret_cast<uintptr_t>(a.T) & 15) == 0) {
+        to_bf16<<<8 * 152, 256, 0, st>>>((const float4*)a.T, (__nv_bfloat162*)Tin, nm / 4);
+        if (nm % 4) to_bf16_tail<<<1, 256, 0, st>>>((const float*)a.T, (__nv_bfloat16*)Tin, nm / 4 * 4, nm);
+      } else {
+        to_bf16_tail<<<8 * 152, 256, 0, st>>>((const float*)a.T, (__nv_bfloat16*)Tin, 0, nm);
+      }
       const float one = 1.f, zero = 0.f;
       cs = cublasGemmEx(S->handle, CUBLAS_OP_N, CUBLAS_OP_N, m, n, n, &one, Tin, CUDA_R_16BF, m, S->X.D,
                         CUDA_R_16BF, n, &zero, Y, CUDA_R_16BF, m, CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
@@ -261,9 +287,9 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
   {
     TraceScope ts(a.tracer, "dense_epilogue", st);
     if (dbl)
-      dense_epilogue<double><<<4 * 152, 256, 0, st>>>((double*)a.G, n, m, (const double*)cx, (const double*)cy, 2.0);
+      dense_epilogue<double><<<n, 256, 0, st>>>((double*)a.G, n, m, (const double*)cx, (const double*)cy, 2.0);
     else
-      dense_epilogue<float><<<4 * 152, 256, 0, st>>>((float*)a.G, n, m, (const float*)cx, (const float*)cy, 2.f);
+      dense_epilogue<float><<<n, 256, 0, st>>>((float*)a.G, n, m, (const float*)cx, (const float*)cy, 2.f);
   }
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }

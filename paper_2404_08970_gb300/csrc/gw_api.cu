@@ -86,8 +86,9 @@ struct gw_ctx {
   // Graph of the last solve (the whole mirror descent), relaunched while the
   // arguments stay the same.
   cudaStream_t cap = nullptr;
-  cudaGraphExec_t solve_exec = nullptr;
-  std::string solve_key;
+  // Graphs of recent calls (gradients, solves), keyed by their arguments and
+  // relaunched while the arguments match; at most kGraphCache, oldest dropped.
+  std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
   // Batched solves: worker streams (fork/join inside the captured graph), the
   // batch workspace and the last batch graph.
   std::vector<cudaStream_t> bstreams;
@@ -134,6 +135,57 @@ gw_status ensure_ws(gw_ctx* c, size_t bytes) {
     return fail(c, GW_ERR_OOM, "workspace allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
   }
   c->ws_bytes = want;
+  return GW_OK;
+}
+
+constexpr size_t kGraphCache = 8;
+
+// Runs `enqueue` (a sequence of launches on the stream it is given) on
+// `stream` as a CUDA graph: captured on the context's side stream the first
+// time a key is seen, relaunched from the cache afterwards.  With profiling on
+// the launches go straight to `stream` (per-kernel events need them eager).
+template <typename F>
+gw_status run_graph(gw_ctx* c, const std::string& key, cudaStream_t stream, F&& enqueue, const char* what) {
+  int rc;
+  if (c->tracer) {
+    rc = enqueue(stream);
+  } else {
+    cudaGraphExec_t exec = nullptr;
+    for (size_t i = 0; i < c->graphs.size(); ++i)
+      if (c->graphs[i].first == key) {
+        exec = c->graphs[i].second;
+        break;
+      }
+    if (!exec) {
+      if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "capture stream");
+      cudaGraph_t graph = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+      rc = enqueue(c->cap);
+      e = cudaStreamEndCapture(c->cap, &graph);
+      if (rc != GW_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(c, rc != GW_OK ? (gw_status)rc : GW_ERR_CUDA, "%s: capture failed (%s)", what,
+                    gw::last_failure());
+      }
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+      if (c->graphs.size() >= kGraphCache) {
+        cudaGraphExecDestroy(c->graphs.front().second);
+        c->graphs.erase(c->graphs.begin());
+      }
+      c->graphs.emplace_back(key, exec);
+    }
+    rc = cudaGraphLaunch(exec, stream) == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+  }
+  if (rc != GW_OK) {
+    cudaError_t e = cudaGetLastError();
+    return fail(c, (gw_status)rc, "%s launch failed: %s (%s)", what, cudaGetErrorString(e), gw::last_failure());
+  }
+  c->err.clear();
   return GW_OK;
 }
 
@@ -199,7 +251,7 @@ void gw_ctx_destroy(gw_ctx* c) {
   if (c->ws) cudaFree(c->ws);
   if (c->status) cudaFree(c->status);
   gw::dense_state_destroy(c->dense);
-  if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
   if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
   for (auto st : c->bstreams) cudaStreamDestroy(st);
   for (auto ev : c->join_ev) cudaEventDestroy(ev);
@@ -303,13 +355,17 @@ gw_status gw_grad(gw_ctx* c, const gw_problem* p, const double* d_u, const doubl
     a.tracer = c->tr();
     s = ensure_ws(c, gw::grad2d_workspace_bytes(a.sx, a.sy, a.dtype));
     if (s != GW_OK) return s;
-    int rc = gw::grad2d_launch(a, c->ws, c->ws_bytes);
-    if (rc != GW_OK) {
-      cudaError_t e = cudaGetLastError();
-      return fail(c, (gw_status)rc, "gw_grad (2D) launch failed: %s", cudaGetErrorString(e));
-    }
-    c->err.clear();
-    return GW_OK;
+    char key[384];
+    snprintf(key, sizeof key, "grad2 %d %d %d %.17g %.17g %d %p %p %p %p %d %p %zu", a.sx, a.sy, a.cost, a.hx, a.hy,
+             a.dtype, a.T, a.G, (void*)a.u, (void*)a.v, a.exact, c->ws, c->ws_bytes);
+    return run_graph(
+        c, key, a.stream,
+        [&](cudaStream_t st) {
+          gw::Grad2DArgs ac = a;
+          ac.stream = st;
+          return gw::grad2d_launch(ac, c->ws, c->ws_bytes);
+        },
+        "gw_grad (2D)");
   }
 
   gw::Grad1DArgs a{};
@@ -332,13 +388,17 @@ gw_status gw_grad(gw_ctx* c, const gw_problem* p, const double* d_u, const doubl
   a.force_generic = c->force_generic;
   s = ensure_ws(c, gw::grad1d_workspace_bytes(a.n, a.m, a.k, a.dtype, a.num_sms));
   if (s != GW_OK) return s;
-  int rc = gw::grad1d_launch(a, c->ws, c->ws_bytes);
-  if (rc != GW_OK) {
-    cudaError_t e = cudaGetLastError();
-    return fail(c, (gw_status)rc, "gw_grad launch failed: %s", cudaGetErrorString(e));
-  }
-  c->err.clear();
-  return GW_OK;
+  char key[384];
+  snprintf(key, sizeof key, "grad1 %d %d %d %.17g %.17g %d %p %p %p %p %d %d %p %zu", a.n, a.m, a.k, a.hx, a.hy,
+           a.dtype, a.T, a.G, (void*)a.u, (void*)a.v, a.exact, a.force_generic, c->ws, c->ws_bytes);
+  return run_graph(
+      c, key, a.stream,
+      [&](cudaStream_t st) {
+        gw::Grad1DArgs ac = a;
+        ac.stream = st;
+        return gw::grad1d_launch(ac, c->ws, c->ws_bytes);
+      },
+      "gw_grad");
 }
 
 gw_status gw_grad_dense(gw_ctx* c, const gw_problem* p, const double* d_u, const double* d_v, const void* d_T,
@@ -461,53 +521,19 @@ gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const doub
   gw::SolveArgs a = solve_args(c, p, d_u, d_v, d_phi, d_psi, d_T, d_f, d_g, d_stats, stream);
   s = ensure_ws(c, gw::solve_workspace_bytes(a));
   if (s != GW_OK) return s;
-  int rc;
-  if (c->tracer) {
-    // Per-kernel timing wants eager launches.
-    rc = gw::solve_launch(a, c->ws, c->ws_bytes);
-  } else {
-    // The whole solve (thousands of short launches) as one CUDA graph,
-    // captured on a side stream and relaunched while the arguments match.
-    char key[512];
-    snprintf(key, sizeof key, "%d %d %d %d %d %d %.17g %.17g %.17g %.17g %d %d %d %p %p %p %p %p %p %p %p %p %zu",
-             a.dim, a.cost, a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.theta, a.n_outer, a.n_inner, a.feat_dim, (void*)a.u,
-             (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.f, (void*)a.g, (void*)a.stats, c->ws, c->ws_bytes);
-    if (!c->solve_exec || c->solve_key != key) {
-      if (c->solve_exec) {
-        cudaGraphExecDestroy(c->solve_exec);
-        c->solve_exec = nullptr;
-      }
-      if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
-        return cuda_fail(c, cudaGetLastError(), "capture stream");
-      gw::SolveArgs ac = a;
-      ac.stream = c->cap;
-      cudaGraph_t graph = nullptr;
-      cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
-      if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
-      rc = gw::solve_launch(ac, c->ws, c->ws_bytes);
-      e = cudaStreamEndCapture(c->cap, &graph);
-      if (rc != GW_OK || e != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        cudaGetLastError();
-        return fail(c, rc != GW_OK ? (gw_status)rc : GW_ERR_CUDA, "gw_solve capture failed");
-      }
-      e = cudaGraphInstantiate(&c->solve_exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess) {
-        c->solve_exec = nullptr;
-        return cuda_fail(c, e, "graph instantiate");
-      }
-      c->solve_key = key;
-    }
-    cudaError_t e = cudaGraphLaunch(c->solve_exec, a.stream);
-    rc = e == cudaSuccess ? GW_OK : GW_ERR_CUDA;
-  }
-  if (rc != GW_OK) {
-    cudaError_t e = cudaGetLastError();
-    return fail(c, (gw_status)rc, "gw_solve launch failed: %s", cudaGetErrorString(e));
-  }
-  c->err.clear();
-  return GW_OK;
+  char key[512];
+  snprintf(key, sizeof key, "solve %d %d %d %d %d %d %.17g %.17g %.17g %.17g %d %d %d %p %p %p %p %p %p %p %p %p %zu",
+           a.dim, a.cost, a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.theta, a.n_outer, a.n_inner, a.feat_dim,
+           (void*)a.u, (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.f, (void*)a.g, (void*)a.stats, c->ws,
+           c->ws_bytes);
+  return run_graph(
+      c, key, a.stream,
+      [&](cudaStream_t st) {
+        gw::SolveArgs ac = a;
+        ac.stream = st;
+        return gw::solve_launch(ac, c->ws, c->ws_bytes);
+      },
+      "gw_solve");
 }
 
 gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const double* const* d_u,

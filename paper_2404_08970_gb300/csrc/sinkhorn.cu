@@ -438,11 +438,19 @@ __global__ void __launch_bounds__(256) sk_cols(const __grid_constant__ SkBatch<R
   const int b0 = min(B, grp * per), b1 = min(B, b0 + per);
   Real S = 0, C = 0;
   if (p < m) {
-    for (int b = b0; b < b1; ++b) {
-      const Real yk = part[(size_t)b * m + p] - C;
-      const Real tk = S + yk;
-      C = (tk - S) - yk;
-      S = tk;
+    // Loads in batches of 8 (independent, all in flight), then the
+    // compensated sum in band order.
+    for (int b = b0; b < b1; b += 8) {
+      Real x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = b + q < b1 ? part[(size_t)(b + q) * m + p] : (Real)0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const Real yk = x[q] - C;
+        const Real tk = S + yk;
+        C = (tk - S) - yk;
+        S = tk;
+      }
     }
   }
   sS[grp][lane] = (double)S - (double)C;
