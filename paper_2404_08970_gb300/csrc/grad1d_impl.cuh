@@ -266,17 +266,16 @@ __global__ void __launch_bounds__(1024) k1a_band_moments(const Real* __restrict_
 //   A_r(a)  = sum_{j < s_a} (s_a - j)^r x_j      (forward, exclusive)
 //   Bk_r(a) = sum_{j >= s_a} (j - s_a)^r x_j     (from the band start on)
 //   q_e(a)  = C(K, K-e) [A_{K-e}(a) + (-1)^e Bk_{K-e}(a)],  Q(t) = sum_e q_e t^e
-// in three steps, all in float-float (double for double data):
-//   k1b_agg   per column and super-band (kSuper consecutive bands): the
-//             super-band's moments about its end;
-//   k1b_scan  per column: exclusive scan over super-bands (A at each
-//             super-band start) and the column's moments about row n;
-//   k1b_walk  per column and super-band: walks the bands with A, takes Bk
-//             from the column moments, writes q.
-// q layout [band][K+1][m]; agg/aS layout [super][K+1][m]; ntot [K+1][m].
+// in one kernel, all in float-float (double for double data).  A block
+// covers 32 columns (one per lane); its 8 warps split the bands into 8
+// consecutive groups:
+//   1. each warp: its group's moments about the group's end;
+//   2. each warp: the exclusive prefix over the groups before it (A at its
+//      group's start) and the column's moments about row n (all groups);
+//   3. each warp walks its bands with A, takes Bk from the column moments,
+//      writes q.
+// q layout [band][K+1][m].
 // ---------------------------------------------------------------------------
-constexpr int kSuper = 8;
-
 template <int K, typename Real>
 struct K1bOps {
   using A = typename AccT<Real>::type;
@@ -307,82 +306,66 @@ struct K1bOps {
   }
 };
 
+constexpr int kGroups = 8;
+
 template <int K, typename Real>
-__global__ void __launch_bounds__(256) k1b_agg(const Real* __restrict__ mu, int n, int m, int R, int B,
-                                               typename AccT<Real>::type* __restrict__ agg) {
+__global__ void __launch_bounds__(32 * kGroups) k1b_carries(const Real* __restrict__ mu, int n, int m, int R, int B,
+                                                          Real* __restrict__ q, double* __restrict__ colsum) {
   using A = typename AccT<Real>::type;
   using O = K1bOps<K, Real>;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int S = blockIdx.y;
-  if (p >= m) return;
-  const int a0 = S * kSuper, a1 = min(B, a0 + kSuper);
-  A FA[K + 1], M[K + 1], N[K + 1];
+  using F = typename AccReal<A>::type;
+  __shared__ A gagg[kGroups][K + 1][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + lane;
+  const int per = (B + kGroups - 1) / kGroups;
+  auto group_bands = [&](int g, int& g0, int& g1) {
+    g0 = min(B, g * per);
+    g1 = min(B, g0 + per);
+  };
+  int a0, a1;
+  group_bands(w, a0, a1);
+  A M[K + 1], N[K + 1];
+  // 1. group aggregate about the group's end
+  A FA[K + 1];
 #pragma unroll
   for (int r = 0; r <= K; ++r) FA[r] = acc_zero((A*)nullptr);
-  for (int a = a0; a < a1; ++a) {
-    const int Ra = min(R, n - a * R);
-    O::load_mu(mu, m, a, p, M);
-    O::nu_of(M, Ra, N);
-    shift_acc<K>(FA, Ra);
+  if (p < m) {
+    for (int a = a0; a < a1; ++a) {
+      const int Ra = min(R, n - a * R);
+      O::load_mu(mu, m, a, p, M);
+      O::nu_of(M, Ra, N);
+      shift_acc<K>(FA, Ra);
 #pragma unroll
-    for (int r = 0; r <= K; ++r) FA[r] = acc_add(FA[r], N[r]);
-  }
-#pragma unroll
-  for (int r = 0; r <= K; ++r) agg[((size_t)S * (K + 1) + r) * m + p] = FA[r];
-}
-
-template <int K, typename Real>
-__global__ void __launch_bounds__(256) k1b_scan(int n, int m, int R, int B, int NS,
-                                                const typename AccT<Real>::type* __restrict__ agg,
-                                                typename AccT<Real>::type* __restrict__ aS,
-                                                typename AccT<Real>::type* __restrict__ ntot,
-                                                double* __restrict__ colsum) {
-  using A = typename AccT<Real>::type;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= m) return;
-  A C[K + 1];
-#pragma unroll
-  for (int r = 0; r <= K; ++r) C[r] = acc_zero((A*)nullptr);
-  for (int S = 0; S < NS; ++S) {
-    A G[K + 1];
-#pragma unroll
-    for (int r = 0; r <= K; ++r) {
-      aS[((size_t)S * (K + 1) + r) * m + p] = C[r];
-      G[r] = agg[((size_t)S * (K + 1) + r) * m + p];
+      for (int r = 0; r <= K; ++r) FA[r] = acc_add(FA[r], N[r]);
     }
-    const int L = min(n, (S + 1) * kSuper * R) - S * kSuper * R;
-    shift_acc<K>(C, L);
-#pragma unroll
-    for (int r = 0; r <= K; ++r) C[r] = acc_add(C[r], G[r]);
   }
 #pragma unroll
-  for (int r = 0; r <= K; ++r) ntot[(size_t)r * m + p] = C[r];
-  if (colsum) {
-    if constexpr (sizeof(Real) == 4) colsum[p] = ff_to_double(C[0]);
-    else colsum[p] = C[0];
+  for (int r = 0; r <= K; ++r) gagg[w][r][lane] = FA[r];
+  __syncthreads();
+  // 2. exclusive prefix at the group start (Af) and the column total (Nt)
+  A Nt[K + 1], Af[K + 1];
+#pragma unroll
+  for (int r = 0; r <= K; ++r) Nt[r] = acc_zero((A*)nullptr);
+  for (int g = 0; g < kGroups; ++g) {
+    if (g == w) {
+#pragma unroll
+      for (int r = 0; r <= K; ++r) Af[r] = Nt[r];
+    }
+    int g0, g1;
+    group_bands(g, g0, g1);
+    const int L = g1 > g0 ? min(n, g1 * R) - g0 * R : 0;
+    shift_acc<K>(Nt, L);
+#pragma unroll
+    for (int r = 0; r <= K; ++r) Nt[r] = acc_add(Nt[r], gagg[g][r][lane]);
   }
-}
-
-template <int K, typename Real>
-__global__ void __launch_bounds__(256) k1b_walk(const Real* __restrict__ mu, int n, int m, int R, int B,
-                                                const typename AccT<Real>::type* __restrict__ aS,
-                                                const typename AccT<Real>::type* __restrict__ ntot,
-                                                Real* __restrict__ q) {
-  using A = typename AccT<Real>::type;
-  using O = K1bOps<K, Real>;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  const int S = blockIdx.y;
   if (p >= m) return;
-  const int a0 = S * kSuper, a1 = min(B, a0 + kSuper);
-  A Af[K + 1], Nt[K + 1], M[K + 1], N[K + 1];
-#pragma unroll
-  for (int r = 0; r <= K; ++r) {
-    Af[r] = aS[((size_t)S * (K + 1) + r) * m + p];
-    Nt[r] = ntot[(size_t)r * m + p];
+  if (colsum && w == 0) {
+    if constexpr (sizeof(Real) == 4) colsum[p] = ff_to_double(Nt[0]);
+    else colsum[p] = Nt[0];
   }
+  // 3. walk the group's bands
   for (int a = a0; a < a1; ++a) {
     const int sa = a * R;
-    using F = typename AccReal<A>::type;
     const F dn = (F)(n - sa);
     // Moments about s_a of the whole column (Horner in n - s_a, alternating
     // signs), then Bk = those minus (-1)^u A.
@@ -391,11 +374,11 @@ __global__ void __launch_bounds__(256) k1b_walk(const Real* __restrict__ mu, int
     for (int u = 0; u <= K; ++u) {
       A acc = Nt[0];
 #pragma unroll
-      for (int w = 1; w <= u; ++w) {
+      for (int w2 = 1; w2 <= u; ++w2) {
         acc = acc_mulf(acc, dn);
-        const int c = binom(u, w);
-        const A term = c == 1 ? Nt[w] : acc_mulf(Nt[w], (F)c);
-        acc = (w & 1) ? acc_sub(acc, term) : acc_add(acc, term);
+        const int c = binom(u, w2);
+        const A term = c == 1 ? Nt[w2] : acc_mulf(Nt[w2], (F)c);
+        acc = (w2 & 1) ? acc_sub(acc, term) : acc_add(acc, term);
       }
       Bk[u] = (u & 1) ? acc_add(acc, Af[u]) : acc_sub(acc, Af[u]);
     }
@@ -404,7 +387,7 @@ __global__ void __launch_bounds__(256) k1b_walk(const Real* __restrict__ mu, int
       const int r = K - e;
       A t = (e & 1) ? acc_sub(Af[r], Bk[r]) : acc_add(Af[r], Bk[r]);
       const int cb = binom(K, r);
-      if (cb != 1) t = acc_mulf(t, (typename AccReal<A>::type)cb);
+      if (cb != 1) t = acc_mulf(t, (F)cb);
       q[((size_t)a * (K + 1) + e) * m + p] = (Real)acc_round(t);
     }
     const int Ra = min(R, n - a * R);
@@ -727,9 +710,9 @@ namespace gw {
 // ---------------------------------------------------------------------------
 struct K1Layout {
   Bands bands;
-  size_t mu_off, q_off, agg_off, as_off, ntot_off, rowpart_off, r_off, c_off, cx_off, cy_off, partx_off,
+  size_t mu_off, q_off, rowpart_off, r_off, c_off, cx_off, cy_off, partx_off,
       party_off, end;
-  int nwchunks, NS;
+  int nwchunks;
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -742,10 +725,7 @@ inline K1Layout k1_layout(int n, int m, int k, size_t real_bytes, int target_ban
   size_t off = 0;
   L.mu_off = off;      off = align_up(off + (size_t)B * (k + 2) * m * real_bytes, 256);
   L.q_off = off;       off = align_up(off + (size_t)B * (k + 1) * m * real_bytes, 256);
-  L.NS = (B + kSuper - 1) / kSuper;
-  L.agg_off = off;     off = align_up(off + (size_t)L.NS * (k + 1) * m * 8, 256);
-  L.as_off = off;      off = align_up(off + (size_t)L.NS * (k + 1) * m * 8, 256);
-  L.ntot_off = off;    off = align_up(off + (size_t)(k + 1) * m * 8, 256);
+
   L.rowpart_off = off; off = align_up(off + (size_t)L.nwchunks * n * 2 * real_bytes, 256);
   L.r_off = off;       off = align_up(off + (size_t)n * 8, 256);
   L.c_off = off;       off = align_up(off + (size_t)m * 8, 256);
@@ -830,6 +810,20 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
   Real* mu = (Real*)(ws + L.mu_off);
   Real* rowpart = (Real*)(ws + L.rowpart_off);
 
+  // With target marginals the constant terms do not depend on T: given a
+  // side stream, they run there concurrently with k1a and k1b.
+  const int dt = sizeof(Real) == 4 ? GW_F32 : GW_F64;
+  const bool overlap = !g.exact && g.side && g.ev_fork && g.ev_join;
+  if (overlap) {
+    if (cudaEventRecord(g.ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(g.side, g.ev_fork, 0) != cudaSuccess)
+      return GW_ERR_CUDA;
+    int rc = marg_const2_launch(g.u, n, std::pow(g.hx, 2 * K) * g.out_scale, ws + L.cx_off, g.v, m,
+                                std::pow(g.hy, 2 * K) * g.out_scale, ws + L.cy_off, K, dt,
+                                (double*)(ws + L.partx_off), g.side, g.tracer);
+    if (rc != GW_OK) return rc;
+    if (cudaEventRecord(g.ev_join, g.side) != cudaSuccess) return GW_ERR_CUDA;
+  }
+
   // k1a: VEC columns per vector load, CPT column groups per thread.
   const bool vec_ok = (m % 4 == 0) && ((((uintptr_t)g.T) & 15) == 0);
   int vec_used = 1;
@@ -867,14 +861,8 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
   double* c = (double*)(ws + L.c_off);
   {
     TraceScope ts(g.tracer, "k1b_band_carries", st);
-    using A = typename AccT<Real>::type;
-    A* agg = (A*)(ws + L.agg_off);
-    A* aS = (A*)(ws + L.as_off);
-    A* ntot = (A*)(ws + L.ntot_off);
-    dim3 grid2((m + 255) / 256, L.NS);
-    k1b_agg<K, Real><<<grid2, 256, 0, st>>>(mu, n, m, R, B, agg);
-    k1b_scan<K, Real><<<(m + 63) / 64, 64, 0, st>>>(n, m, R, B, L.NS, agg, aS, ntot, g.exact ? c : nullptr);
-    k1b_walk<K, Real><<<grid2, 256, 0, st>>>(mu, n, m, R, B, aS, ntot, (Real*)(ws + L.q_off));
+    k1b_carries<K, Real><<<(m + 31) / 32, 32 * kGroups, 0, st>>>(mu, n, m, R, B, (Real*)(ws + L.q_off),
+                                                                g.exact ? c : nullptr);
   }
   if (cudaPeekAtLastError() != cudaSuccess) return GW_ERR_CUDA;
 
@@ -887,11 +875,14 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
     wx = r;
     wy = c;
   }
-  const int dt = sizeof(Real) == 4 ? GW_F32 : GW_F64;
-  int rc = marg_const2_launch(wx, n, std::pow(g.hx, 2 * K) * g.out_scale, ws + L.cx_off, wy, m,
-                              std::pow(g.hy, 2 * K) * g.out_scale, ws + L.cy_off, K, dt,
-                              (double*)(ws + L.partx_off), st, g.tracer);
-  if (rc != GW_OK) return rc;
+  if (overlap) {
+    if (cudaStreamWaitEvent(st, g.ev_join, 0) != cudaSuccess) return GW_ERR_CUDA;
+  } else {
+    int rc = marg_const2_launch(wx, n, std::pow(g.hx, 2 * K) * g.out_scale, ws + L.cx_off, wy, m,
+                                std::pow(g.hy, 2 * K) * g.out_scale, ws + L.cy_off, K, dt,
+                                (double*)(ws + L.partx_off), st, g.tracer);
+    if (rc != GW_OK) return rc;
+  }
 
   // k1c
   if constexpr (K <= 2) {

@@ -86,6 +86,9 @@ struct gw_ctx {
   // Graph of the last solve (the whole mirror descent), relaunched while the
   // arguments stay the same.
   cudaStream_t cap = nullptr;
+  // Side stream and events for work that overlaps inside one call.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // Graphs of recent calls (gradients, solves), keyed by their arguments and
   // relaunched while the arguments match; at most kGraphCache, oldest dropped.
   std::vector<std::pair<std::string, cudaGraphExec_t>> graphs;
@@ -252,6 +255,9 @@ void gw_ctx_destroy(gw_ctx* c) {
   if (c->status) cudaFree(c->status);
   gw::dense_state_destroy(c->dense);
   for (auto& g : c->graphs) cudaGraphExecDestroy(g.second);
+  if (c->side) cudaStreamDestroy(c->side);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
   for (auto st : c->bstreams) cudaStreamDestroy(st);
   for (auto ev : c->join_ev) cudaEventDestroy(ev);
@@ -388,6 +394,15 @@ gw_status gw_grad(gw_ctx* c, const gw_problem* p, const double* d_u, const doubl
   a.force_generic = c->force_generic;
   s = ensure_ws(c, gw::grad1d_workspace_bytes(a.n, a.m, a.k, a.dtype, a.num_sms));
   if (s != GW_OK) return s;
+  if (!c->side) {
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(c, cudaGetLastError(), "side stream");
+  }
+  a.side = c->side;
+  a.ev_fork = c->ev_fork;
+  a.ev_join = c->ev_join;
   char key[384];
   snprintf(key, sizeof key, "grad1 %d %d %d %.17g %.17g %d %p %p %p %p %d %d %p %zu", a.n, a.m, a.k, a.hx, a.hy,
            a.dtype, a.T, a.G, (void*)a.u, (void*)a.v, a.exact, a.force_generic, c->ws, c->ws_bytes);

@@ -72,6 +72,10 @@ struct Grad1DArgs {
   int num_sms;
   Tracer* tracer;       // nullable
   int force_generic;    // 1: use the block-scan row kernel even where the warp-specialised one applies
+  // Optional: a second stream and two events, to run the constant terms
+  // (target marginals) concurrently with the band passes.
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // Host-side failure notes (per thread): the launch helpers record what
