@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--no-serve", dest="serve", action="store_false")
     ap.add_argument("--serve-count", type=int, default=1500)
+    ap.add_argument("--serve-slots", type=int, default=8)
     return ap.parse_args()
 
 
@@ -292,7 +293,7 @@ def bench_batch(ctx, L, dev, stream, barrier, count):
             "first_call_s_incl_capture": t_first, "all_values_finite": bool(np.all(np.isfinite(vals)))}
 
 
-def bench_serve(L, device, count):
+def bench_serve(L, device, count, slots=8):
     """Serving: requests of four kinds (1D/2D, GW/fused GW), N per space
     log-uniform in [128, 16384], eps = 1e-2, 10 x 50, through gw_submit /
     gw_poll with a 40 GB budget and 8 slots.  Saturated throughput (all
@@ -302,7 +303,7 @@ def bench_serve(L, device, count):
     import numpy as np
     from paper_2404_08970_gb300 import inputs as I
     reqs = I.workload_serve(count, rate=2000.0, seed=0)
-    srv = L.Server(device, hbm_budget_bytes=40 << 30, max_slots=8)
+    srv = L.Server(device, hbm_budget_bytes=40 << 30, max_slots=slots)
 
     def prob(r):
         return L.problem(dim=r["dim"], nx=r["nx"], ny=r["ny"], hx=r["hx"], hy=r["hy"], k=r["k"],
@@ -340,7 +341,7 @@ def bench_serve(L, device, count):
         cap = count / wall
         out = {"workload": f"{count} requests: 1D GW, 1D FGW, 2D GW, 2D FGW (1/4 each), N per space log-uniform in "
                            "[128, 16384], 2D side round(sqrt(N)), FGW theta=0.5 with 16-dim N(0,1) features, "
-                           "eps=1e-2, 10 x 50, fp32; budget 40 GB, 8 slots",
+                           f"eps=1e-2, 10 x 50, fp32; budget 40 GB, {slots} slots",
                "saturated_solves_per_s": cap, "saturated_wall_s": wall, "errors": int(bad),
                "mean_nm": float(np.mean([(r["nx"] ** 2 if r["dim"] == 2 else r["nx"]) *
                                          (r["ny"] ** 2 if r["dim"] == 2 else r["ny"]) for r in reqs]))}
@@ -553,7 +554,7 @@ def run_ours(args):
 
     grid2d = bench_2d(ctx, L, dev, stream, barrier, min(args.steps, 20), args.solve) if args.grid2d else None
     batch = bench_batch(ctx, L, dev, stream, barrier, args.batch_count) if args.batch else None
-    serve = bench_serve(L, local, args.serve_count) if args.serve else None
+    serve = bench_serve(L, local, args.serve_count, args.serve_slots) if args.serve else None
 
     clk = clocks.stop()
 
