@@ -117,11 +117,12 @@ class Clocks:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="gw_clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
                                           "--format=csv,noheader,nounits", "-lms", "50", "-f", self.path],
                                          stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
@@ -153,6 +154,10 @@ class Clocks:
             for nm, val in zip(names, parts[5:9]):
                 if val.lower().startswith("active"):
                     reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
@@ -371,7 +376,7 @@ def run_reference(args):
     import numpy as np
     n = args.n
     # Each step: one bounded row sample of the oracle gradient.
-    rate0, rows, t = cpu_oracle_rate(w, budget_s=8.0)
+    rate0, rows, t = cpu_oracle_rate(w, budget_s=4.0)
     for _ in range(args.warmup):
         oracle_rows_time(w["T"], w["u"], w["v"], w["k"], w["hx"], rows)
     times = [oracle_rows_time(w["T"], w["u"], w["v"], w["k"], w["hx"], rows) for _ in range(args.steps)]
