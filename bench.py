@@ -48,6 +48,24 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over the ranks of the process group (x itself
+    without one).  Every rank calls it."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (replicas do equal work, weak scaling)."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -450,14 +468,9 @@ def run_ours(args):
     ctx.gw_ctx_profile(False)
     ctx.gw_ctx_check(stream)
 
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dev)
     per_step = ms_max / args.steps
-    value = world * args.steps / (ms_max / 1e3)
+    value = job_rate(world, args.steps, ms_max)
 
     # Roofline of the dominant kernel (largest total time).
     hbm_peak, bf16_peak, peak_kind = measured_peaks()
@@ -491,13 +504,8 @@ def run_ours(args):
         hG.copy_(dG, non_blocking=True)
     e1.record(stream)
     barrier()
-    e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
-    e2e = {"value": world * e_steps / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": 4 * nm,
+    e_ms = max_over_ranks(e0.elapsed_time(e1), dev)
+    e2e = {"value": job_rate(world, e_steps, e_ms), "unit": UNIT, "h2d_bytes_per_step": 4 * nm,
            "d2h_bytes_per_step": 4 * nm}
 
     # Dense comparison (cuBLAS, materialised distance matrices) on the same T.
