@@ -330,6 +330,7 @@ __global__ void __launch_bounds__(32 * kGroups) k1b_carries(const Real* __restri
 #pragma unroll
   for (int r = 0; r <= K; ++r) FA[r] = acc_zero((A*)nullptr);
   if (p < m) {
+#pragma unroll 4
     for (int a = a0; a < a1; ++a) {
       const int Ra = min(R, n - a * R);
       O::load_mu(mu, m, a, p, M);
@@ -364,6 +365,7 @@ __global__ void __launch_bounds__(32 * kGroups) k1b_carries(const Real* __restri
     else colsum[p] = Nt[0];
   }
   // 3. walk the group's bands
+#pragma unroll 4
   for (int a = a0; a < a1; ++a) {
     const int sa = a * R;
     const F dn = (F)(n - sa);
