@@ -554,7 +554,7 @@ def run_ours(args):
         ctx.gw_ctx_check(stream)
         sk = sprof.get("sk_pass", {"ms": 0.0, "launches": 1})
         sk_ms = sk["ms"] / max(1, sk["launches"])
-        grad_ms = sum(v["ms"] for kk, v in sprof.items() if kk.startswith("k1") or kk == "marg_const") / 20.0
+        grad_ms = sum(v["ms"] for kk, v in sprof.items() if kk.startswith("k1") or kk.startswith("marg")) / 20.0
         other = sms - 20 * grad_ms
         dense_grad_ms = min((d["ms"] for d in dense.values() if isinstance(d, dict) and "ms" in d), default=None)
         solve = {"workload": "same grids, eps=1e-2, 20 mirror-descent steps x 100 Sinkhorn iterations, fp32",

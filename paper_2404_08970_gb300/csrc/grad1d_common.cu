@@ -1,12 +1,11 @@
 // Host dispatch of the structured 1D gradient and the constant-term kernels.
-#include <algorithm>
-#include <cstdio>
-#include <vector>
-#include <cmath>
-
 #include <cuda.h>
 
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
 #include <mutex>
+#include <vector>
 
 #include "grad1d_impl.cuh"
 
@@ -189,17 +188,24 @@ size_t marg_part_doubles(int len, int k) {
 
 int marg_const2_launch(const double* wx, int n, double fx, void* outx, const double* wy, int m, double fy,
                        void* outy, int k, int dtype, double* part, cudaStream_t stream, Tracer* tracer) {
-  TraceScope ts(tracer, "marg_const", stream);
   const int P = 2 * k;
   const int nbx = (n + kMargBlock - 1) / kMargBlock, nby = (m + kMargBlock - 1) / kMargBlock;
   MargVec X{wx, n, fx, outx}, Y{wy, m, fy, outy};
   if (dtype == GW_F32) {
     const float fxh = (float)fx, fyh = (float)fy;
     const float fxl = (float)(fx - (double)fxh), fyl = (float)(fy - (double)fyh);
-    marg_moments2_ff<<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, P, (float*)part);
+    {
+      TraceScope ts(tracer, "marg_moments", stream);
+      marg_moments2_ff<<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, P, (float*)part);
+    }
+    TraceScope ts(tracer, "marg_eval", stream);
     marg_eval2_ff<<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, nby, P, (const float*)part, fxh, fxl, fyh, fyl);
   } else {
-    marg_moments2<<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, P, part);
+    {
+      TraceScope ts(tracer, "marg_moments", stream);
+      marg_moments2<<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, P, part);
+    }
+    TraceScope ts(tracer, "marg_eval", stream);
     marg_eval2<<<nbx + nby, kMargBlock, 0, stream>>>(X, Y, nbx, nby, nbx, P, part);
   }
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
