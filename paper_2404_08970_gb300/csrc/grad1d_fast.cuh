@@ -30,17 +30,27 @@ struct FastGeom {
   int vec_bytes;   // one swizzled vector of m_pad reals (multiple of 1024)
 };
 
+// Odd K: the in-chunk forward states of the pending row go from phase A(t) to
+// phase B(t) in registers for float; for double (twice the registers) they go
+// through a shared-memory buffer.
+template <int K, typename Real>
+struct FastFl {
+  static constexpr bool in_smem = (K & 1) && sizeof(Real) != 4;
+};
+
 template <int K, int NW, int VPT, typename Real>
 struct FastSmem {
   static constexpr int NT = 32 * NW;
+  static constexpr size_t fl_bytes = FastFl<K, Real>::in_smem ? sizeof(Real) * (size_t)VPT * NT + 16 : 0;
   static size_t bytes(int slot_bytes, int vec_bytes, int stages) {
     size_t b = 1024;  // alignment slack
     b += (size_t)stages * slot_bytes;
     b += 2 * (size_t)vec_bytes;                     // cy hi, lo
+    b += (size_t)vec_bytes;                         // output staging, one warp segment per warp
     b += 8 * (size_t)stages;                        // mbarriers
     b += sizeof(Real) * 2 * NW * 2 * (K + 1);       // warp totals [2][NW][2][K+1]
     b += sizeof(Real) * 2 * NW * (K + 2) + 64;      // polynomials [2][NW][K+2]
-    b += (K & 1) ? sizeof(Real) * (size_t)VPT * NT + 16 : 0;  // pending in-chunk forward states
+    b += fl_bytes;                                  // pending in-chunk forward states (double)
     return b;
   }
 };
@@ -66,10 +76,16 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
   unsigned char* ring = sm;
   unsigned char* cyH = ring + (size_t)stages * slot_bytes;
   unsigned char* cyL = cyH + vec_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(cyL + vec_bytes);
+  // Output staging: warp w's SEG outputs of a row, swizzled like the ring, so
+  // that each warp writes its segment to global memory 512 contiguous bytes
+  // per store instruction.
+  unsigned char* stg = cyL + vec_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(stg + vec_bytes);
   Real* wtot = reinterpret_cast<Real*>(bars + stages);             // [2][NW][2][K+1]
   Real* zw = wtot + 2 * NW * 2 * (K + 1);                          // [2][NW][K+2]
-  // In-chunk forward states of the pending row, [VPT/PER][NT] 16-byte chunks.
+  // Double only: in-chunk forward states of the pending row, [VPT/PER][NT]
+  // 16-byte chunks.
+  constexpr bool FL_SMEM = FastFl<K, Real>::in_smem;
   unsigned char* flraw = reinterpret_cast<unsigned char*>(zw + 2 * NW * (K + 2));
   float4* flbuf = reinterpret_cast<float4*>(flraw + ((16u - (smem_u32(flraw) & 15u)) & 15u));
 
@@ -178,9 +194,13 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
   }
   constexpr int PER = 16 / sizeof(Real);
   Real ex_prev[K + 1];
+  // In-chunk forward states of the pending row (odd K, float).
+  Real fl_prev[VPT];
   Real cxh_prev = 0, cxl_prev = 0;
 #pragma unroll
   for (int r = 0; r <= K; ++r) ex_prev[r] = 0;
+#pragma unroll
+  for (int v = 0; v < VPT; ++v) fl_prev[v] = 0;
 
   for (int t = 0; t <= Ra; ++t) {
     Real fl_new[VPT];
@@ -333,10 +353,9 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
 #pragma unroll
       for (int e = 1; e <= K; ++e) LC[e] = -scale * ZT[e];
       const Real cks = -scale * CK;
-      Real* grow = G + (size_t)i * m + c0;
-      const bool vec_store = (c0 + VPT <= m) && ((((uintptr_t)grow) & 15) == 0);
       // Four (float) or two (double) columns at a time: their constant term
-      // from swizzled shared memory, the outputs straight to global memory.
+      // from swizzled shared memory, the outputs into the warp's staging
+      // segment at the same swizzled offsets.
 #pragma unroll
       for (int j = 0; j < VPT / PER; ++j) {
         const uint32_t b = (uint32_t)((c0 + j * PER) * sizeof(Real));
@@ -344,9 +363,12 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
         const float4 lv = *reinterpret_cast<const float4*>(cyL + swz128(b));
         const Real* ch = reinterpret_cast<const Real*>(&hv);
         const Real* cl = reinterpret_cast<const Real*>(&lv);
-        float4 flv = make_float4(0.f, 0.f, 0.f, 0.f);
-        if constexpr (K & 1) flv = flbuf[j * NT + tid];
-        const Real* flp = reinterpret_cast<const Real*>(&flv);
+        if constexpr (FL_SMEM) {
+          const float4 flv = flbuf[j * NT + tid];
+          const Real* flp = reinterpret_cast<const Real*>(&flv);
+#pragma unroll
+          for (int w = 0; w < PER; ++w) fl_prev[j * PER + w] = flp[w];
+        }
         Real out[PER];
 #pragma unroll
         for (int w = 0; w < PER; ++w) {
@@ -355,23 +377,39 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
           Real lo = LC[K];
 #pragma unroll
           for (int e = K - 1; e >= 0; --e) lo = fma(lo, vv, LC[e]);
-          if constexpr (K & 1) lo = fma(cks, flp[w], lo);
+          if constexpr (K & 1) lo = fma(cks, fl_prev[v], lo);
           out[w] = (big0 + ch[w]) + (lo + cl[w]);
         }
-        if (vec_store) {
-          if constexpr (sizeof(Real) == 4)
-            *reinterpret_cast<float4*>(grow + j * PER) = make_float4(out[0], out[1], out[2], out[3]);
-          else
-            *reinterpret_cast<double2*>(grow + j * PER) = make_double2(out[0], out[1]);
+        float4 ov;
+        Real* op = reinterpret_cast<Real*>(&ov);
+#pragma unroll
+        for (int w = 0; w < PER; ++w) op[w] = out[w];
+        *reinterpret_cast<float4*>(stg + swz128(b)) = ov;
+      }
+      __syncwarp();
+      // Store pass: lane `lane` takes the 16 bytes at lane * 16 of each
+      // 512-byte piece of the warp's segment.
+      Real* grow = G + (size_t)i * m;
+      const bool row_vec = ((((uintptr_t)grow) & 15) == 0);
+#pragma unroll 2
+      for (int j = 0; j < VPT / PER; ++j) {
+        const int col = warp * SEG + (j * 32 + lane) * PER;
+        const float4 ov = *reinterpret_cast<const float4*>(stg + swz128((uint32_t)(col * sizeof(Real))));
+        if (row_vec && col + PER <= m) {
+          *reinterpret_cast<float4*>(grow + col) = ov;
         } else {
+          const Real* op = reinterpret_cast<const Real*>(&ov);
 #pragma unroll
           for (int w = 0; w < PER; ++w)
-            if (c0 + j * PER + w < m) grow[j * PER + w] = out[w];
+            if (col + w < m) grow[col + w] = op[w];
         }
       }
+      // The next row's outputs overwrite the segment only after every lane
+      // has read it.
+      __syncwarp();
     }
     if (t < Ra) {
-      if constexpr (K & 1) {
+      if constexpr (FL_SMEM) {
 #pragma unroll
         for (int j = 0; j < VPT / PER; ++j) {
           float4 f;
@@ -380,6 +418,9 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
           for (int w = 0; w < PER; ++w) fr[w] = fl_new[j * PER + w];
           flbuf[j * NT + tid] = f;
         }
+      } else if constexpr (K & 1) {
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) fl_prev[v] = fl_new[v];
       }
 #pragma unroll
       for (int r = 0; r <= K; ++r) ex_prev[r] = ex_new[r];

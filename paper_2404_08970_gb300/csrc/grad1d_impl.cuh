@@ -306,7 +306,7 @@ struct K1bOps {
   }
 };
 
-constexpr int kGroups = 8;
+constexpr int kGroups = 16;
 
 template <int K, typename Real>
 __global__ void __launch_bounds__(32 * kGroups) k1b_carries(const Real* __restrict__ mu, int n, int m, int R, int B,
@@ -777,8 +777,8 @@ int launch_k1c_fast(const Grad1DArgs& g, const K1Layout& L, char* ws, cudaStream
   const int vec_bytes = (int)align_up((size_t)cover * sizeof(Real), 1024);
   const int slot_bytes = vec_bytes;
   int stages = 2;
-  const int fl_bytes = (K & 1) ? (int)(sizeof(Real) * VPT * 32 * NW) : 0;
-  if (use_tma) stages = std::max(2, std::min(4, (200 * 1024 - 2 * vec_bytes - fl_bytes) / slot_bytes));
+  const int fl_bytes = (int)FastSmem<K, NW, VPT, Real>::fl_bytes;
+  if (use_tma) stages = std::max(2, std::min(4, (200 * 1024 - 3 * vec_bytes - fl_bytes) / slot_bytes));
   const size_t smem = FastSmem<K, NW, VPT, Real>::bytes(slot_bytes, vec_bytes, stages);
   auto kern = k1c_fast_rows<K, NW, VPT, Real>;
   TraceScope ts(g.tracer, "k1c_fast_rows", st);
