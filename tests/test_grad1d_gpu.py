@@ -11,8 +11,10 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"f32": 1e-6, "f64": 1e-12}
 
+# (70, 1056) and (40, 6144): rows fed by TMA (m a multiple of 32) with the last
+# warps of the row partly or wholly past m.
 SHAPES = [(1, 1), (1, 7), (5, 1), (3, 5), (17, 33), (64, 64), (100, 257), (200, 200), (513, 300), (1000, 1023),
-          (257, 2049), (300, 4100)]
+          (257, 2049), (300, 4100), (70, 1056), (40, 6144)]
 
 
 def _case(n, m, seed, alpha=1.0):
