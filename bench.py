@@ -107,6 +107,18 @@ def oracle_rows_time(T64, u, v, k, h, rows):
     return time.perf_counter() - t0
 
 
+def oracle_rows(T64, u, v, k, hx, hy, rows):
+    """Rows `rows` of the FP64 oracle gradient with target marginals."""
+    import numpy as np
+    from oracle import gw_oracle as O
+    n, m = T64.shape
+    idx = np.arange(n, dtype=np.float64)
+    sel = np.asarray(rows)
+    DXr = (hx ** k) * np.abs(idx[sel][:, None] - idx[None, :]) ** k
+    DY = O.grid_dist_1d(m, hy, k)
+    return O.grad_rows(DXr, DY, T64, (DXr * DXr) @ u, (DY * DY) @ v)
+
+
 def cpu_oracle_rate(w, budget_s=15.0):
     """Gradient evals/s of the oracle on the host, from a timed sample of rows
     (the full dense gradient at n = 8192 takes minutes in FP64)."""
@@ -529,6 +541,24 @@ def run_ours(args):
     best = max((d.get("evals_per_s", 0.0) for d in dense.values()), default=0.0)
     dense["structured_over_best_dense"] = (value / world) / best if best > 0 else None
 
+    # Sampled rows of each form's output (one untimed evaluation each), compared
+    # with the FP64 oracle in the CPU leg below.
+    with_cpu = rank == 0 and world == 1 and not args.no_cpu_baseline
+    err_rows = sorted({r for r in (0, 1, n // 152, n // 152 + 1, n // 2 - 1, n // 2, n - 2, n - 1) if 0 <= r < n})
+    gpu_rows = {}
+    if with_cpu:
+        sel = torch.tensor(err_rows, device=dev)
+        step()
+        barrier()
+        gpu_rows["structured_f32"] = dG.index_select(0, sel).double().cpu().numpy()
+        for name, prec in (("bf16", L.GW_DENSE_BF16), ("tf32", L.GW_DENSE_TF32)):
+            if "ms" not in dense.get(name, {}):
+                continue
+            ctx.gw_grad_dense(prob, du, dv, dT, dG, L.GW_MARG_TARGET, prec, stream)
+            barrier()
+            gpu_rows["dense_" + name] = dG.index_select(0, sel).double().cpu().numpy()
+        ctx.gw_ctx_check(stream)
+
     # Full entropic GW solve on the same grids (20 outer x 100 Sinkhorn), one run.
     solve = None
     if args.solve:
@@ -572,17 +602,25 @@ def run_ours(args):
     clk = clocks.stop()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    errs = None
+    if with_cpu:
         rate, rows, t = cpu_oracle_rate(w)
         cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{rows} of {n} rows of the FP64 dense-definition gradient (numpy), {t:.1f} s"}
+        # The oracle reads the same FP32 values of T as the GPU paths.
+        Gs = oracle_rows(T32.numpy().astype(np.float64), w["u"], w["v"], k, w["hx"], w["hy"], err_rows)
+        den = float(np.max(np.abs(Gs)))
+        errs = {name: float(np.max(np.abs(g - Gs)) / den) for name, g in gpu_rows.items()}
+        errs["rows"] = err_rows
+        errs["metric"] = "max|G - G*| / max|G*| over the sampled rows; G* = FP64 oracle on the same FP32 T"
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(n, k),
                 "roofline": roof, "whole_gradient_gbs": whole_gbs, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clk, "gpu_launches": launches, "kernels": prof, "dense": dense, "solve": solve,
+                "clocks": clk, "gpu_launches": launches, "kernels": prof, "dense": dense,
+                "errors_vs_fp64": errs, "solve": solve,
                 "grid2d": grid2d, "batch": batch, "serve": serve}
         print(json.dumps(line))
     if world > 1:
