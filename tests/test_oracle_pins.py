@@ -336,6 +336,34 @@ def test_fgw_limits():
     assert relerr(T0, O.plan(CC, f, g, 0.1)) < 1e-13
 
 
+@pytest.mark.parametrize("theta", [0.0, 0.3, 1.0])
+def test_fgw_value_matches_brute_force(theta):
+    """Fused GW objective (Remark "FGW"): (1 - theta) sum_ip c_ip^2 T_ip +
+    theta sum_ijpq (D_ij - D'_pq)^2 T_ip T_jq, summed term by term."""
+    rng = np.random.default_rng(26)
+    n, m = 4, 3
+    DX, DY = O.grid_dist_1d(n, 0.5, 2), O.grid_dist_1d(m, 1.0 / 3, 1)
+    phi, psi = I.features(n, 3, rng), I.features(m, 3, rng)
+    CC = O.fgw_feature_cost(phi, psi)
+    T = rng.uniform(0.1, 1.0, size=(n, m))
+    lin = sum(CC[i, p] * T[i, p] for i in range(n) for p in range(m))
+    quad = sum((DX[i, j] - DY[p, q]) ** 2 * T[i, p] * T[j, q]
+               for i in range(n) for j in range(n) for p in range(m) for q in range(m))
+    want = (1.0 - theta) * lin + theta * quad
+    assert abs(O.fgw_value(DX, DY, T, theta, CC) - want) <= 1e-13 * abs(want)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_fgc_apply_exact_integers(k):
+    """D-tilde x = L x + L^T x (Sec. 3) equals the dense |i-j|^k product exactly
+    on integer input."""
+    N = 9
+    x = np.array([3, -1, 4, 1, -5, 9, 2, -6, 5], dtype=object)
+    D = [[abs(i - j) ** k for j in range(N)] for i in range(N)]
+    want = [sum(D[i][j] * x[j] for j in range(N)) for i in range(N)]
+    assert list(O.fgc_apply(x, k)) == want
+
+
 def test_feature_cost_definition():
     rng = np.random.default_rng(24)
     phi, psi = I.features(5, 3, rng), I.features(4, 3, rng)

@@ -50,7 +50,7 @@ def oracle_solve(w, theta=1.0, phi=None, psi=None):
     T, f, g = O.mirror_descent(DX, DY, w["u"], w["v"], w["eps"], w["n_outer"], w["n_inner"], theta=theta, CC=CC)
     E = O.value(DX, DY, T)
     lin = 0.0 if CC is None else float(np.sum(CC * T))
-    return T, f, g, dict(E=E, lin=lin, obj=(1 - theta) * lin + theta * E, H=w["eps"] * O.entropy(T),
+    return T, f, g, dict(E=E, lin=lin, obj=O.fgw_value(DX, DY, T, theta, CC), H=w["eps"] * O.entropy(T),
                          row=float(np.sum(np.abs(T.sum(1) - w["u"]))), col=float(np.sum(np.abs(T.sum(0) - w["v"]))))
 
 
