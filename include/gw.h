@@ -300,6 +300,57 @@ const char* gw_server_last_error(gw_server* server);
  * requests (any pointer may be NULL). */
 gw_status gw_server_info(gw_server* server, long* queued, long* completed, size_t* bytes_in_use);
 
+/*
+ * Tuned row configurations (process-wide).
+ *
+ * Each pass of the Sinkhorn kernels splits a row of Pi over a row group of
+ * 32*NW threads holding VPT values each (32*NW*VPT >= m), with NG row groups
+ * per block.  The built-in choice depends on the row length m and the dtype.
+ * A tuning table replaces it per row-length range: the sweep in
+ * paper_2404_08970_gb300/tune.py times every candidate on the GPU, keeps
+ * only candidates whose plan matches the built-in configuration's, and writes
+ * the table.  The configuration sets the order of a row's reductions, so
+ * every entry point (gw_solve, gw_solve_batch, the server) reads the same
+ * table and gives the same results for it; change the table only while no
+ * solve is running.  With no table the built-in choice is used.
+ *
+ * At the first gw_ctx_create of the process the library loads the table named
+ * by the environment variable GW_TUNE_TABLE, or else tune_table.txt beside
+ * the library if that file exists.  Format: one entry per line,
+ *     <kernel> <dtype> <m_lo> <m_hi> <config>
+ * with '#' starting a comment.  Later entries take precedence.
+ */
+typedef enum { GW_TUNE_SINKHORN = 0 } gw_tune_kernel;
+
+/* Use configuration `config` for rows of m_lo <= m <= m_hi columns of dtype.
+ * GW_ERR_INVALID for an unknown kernel, dtype or configuration, an empty
+ * range, or a configuration that does not cover m_hi columns. */
+gw_status gw_tune_set(int kernel, int dtype, int m_lo, int m_hi, int config);
+
+/* Drops every table entry (the built-in choice applies again). */
+gw_status gw_tune_clear(void);
+
+/* Adds the entries of a table file (format above).  GW_ERR_INVALID if the
+ * file cannot be read or a line is malformed or invalid; the entries read
+ * before the bad line stay. */
+gw_status gw_tune_load(const char* path);
+
+/* The configuration in effect for rows of m columns (table entry, or the
+ * built-in choice); -1 for an unknown kernel or dtype, or m outside
+ * [1, 16384]. */
+int gw_tune_config(int kernel, int dtype, int m);
+
+/* The candidate configurations for rows of m columns: the built-in choice
+ * first, then every other configuration that covers m columns but at most
+ * four times the built-in choice's.  Writes at most `cap` of them to out (out
+ * may be NULL when cap is 0) and returns how many there are; -1 for an
+ * unknown kernel or dtype, or m outside [1, 16384]. */
+int gw_tune_candidates(int kernel, int dtype, int m, int* out, int cap);
+
+/* Shape of a configuration: warps per row group, values per thread, row
+ * groups per block.  GW_ERR_INVALID for an unknown configuration. */
+gw_status gw_tune_shape(int kernel, int config, int* nw, int* vpt, int* ng);
+
 #ifdef __cplusplus
 }
 #endif

@@ -101,6 +101,12 @@ def load() -> ctypes.CDLL:
         "gw_server_info": (S, [P, ctypes.POINTER(ctypes.c_long), ctypes.POINTER(ctypes.c_long),
                                ctypes.POINTER(ctypes.c_size_t)]),
         "gw_server_last_error": (ctypes.c_char_p, [P]),
+        "gw_tune_set": (S, [I, I, I, I, I]),
+        "gw_tune_clear": (S, []),
+        "gw_tune_load": (S, [ctypes.c_char_p]),
+        "gw_tune_config": (I, [I, I, I]),
+        "gw_tune_candidates": (I, [I, I, I, ctypes.POINTER(I), I]),
+        "gw_tune_shape": (S, [I, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -108,6 +114,53 @@ def load() -> ctypes.CDLL:
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+# gw_tune_kernel
+GW_TUNE_SINKHORN = 0
+
+
+def _tune_check(st: int, what: str) -> None:
+    if st != GW_OK:
+        raise GWError(st, what)
+
+
+def gw_tune_set(kernel: int, dtype: int, m_lo: int, m_hi: int, config: int) -> None:
+    """Table entry: rows of m_lo..m_hi columns of `dtype` use `config`."""
+    _tune_check(load().gw_tune_set(kernel, dtype, m_lo, m_hi, config),
+                f"gw_tune_set({kernel}, {dtype}, {m_lo}, {m_hi}, {config})")
+
+
+def gw_tune_clear() -> None:
+    _tune_check(load().gw_tune_clear(), "gw_tune_clear")
+
+
+def gw_tune_load(path: str) -> None:
+    _tune_check(load().gw_tune_load(os.fsencode(path)), f"gw_tune_load({path})")
+
+
+def gw_tune_config(kernel: int, dtype: int, m: int) -> int:
+    """Configuration in effect for rows of m columns (-1: invalid arguments)."""
+    return load().gw_tune_config(kernel, dtype, m)
+
+
+def gw_tune_candidates(kernel: int, dtype: int, m: int) -> list[int]:
+    """Candidate configurations for rows of m columns, built-in choice first."""
+    lib = load()
+    count = lib.gw_tune_candidates(kernel, dtype, m, None, 0)
+    if count < 0:
+        raise GWError(GW_ERR_INVALID, f"gw_tune_candidates({kernel}, {dtype}, {m})")
+    buf = (ctypes.c_int * max(1, count))()
+    lib.gw_tune_candidates(kernel, dtype, m, buf, count)
+    return list(buf[:count])
+
+
+def gw_tune_shape(kernel: int, config: int) -> tuple[int, int, int]:
+    """(warps per row group, values per thread, row groups per block)."""
+    nw, vpt, ng = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _tune_check(load().gw_tune_shape(kernel, config, ctypes.byref(nw), ctypes.byref(vpt), ctypes.byref(ng)),
+                f"gw_tune_shape({kernel}, {config})")
+    return nw.value, vpt.value, ng.value
 
 
 def declared_functions() -> list[str]:

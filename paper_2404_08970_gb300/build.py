@@ -79,7 +79,7 @@ def build(verbose_ptxas: bool = False, force: bool = False, quiet: bool = True) 
     if not os.path.isdir(libdir):
         libdir = os.path.join(home, "lib")
     tmp = LIB + ".tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-L" + libdir, "-lcudart", "-lcublas",
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-L" + libdir, "-lcudart", "-lcublas", "-ldl",
                                                           "-Xlinker", "-rpath=" + libdir]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

@@ -153,9 +153,12 @@ gw_status run_graph(gw_ctx* c, const std::string& key, cudaStream_t stream, F&& 
   if (c->tracer) {
     rc = enqueue(stream);
   } else {
+    // A captured graph holds the row configurations of its time: the tuning
+    // table's generation is part of the key.
+    const std::string tkey = key + " tune" + std::to_string(gw::tune_generation());
     cudaGraphExec_t exec = nullptr;
     for (size_t i = 0; i < c->graphs.size(); ++i)
-      if (c->graphs[i].first == key) {
+      if (c->graphs[i].first == tkey) {
         exec = c->graphs[i].second;
         break;
       }
@@ -180,7 +183,7 @@ gw_status run_graph(gw_ctx* c, const std::string& key, cudaStream_t stream, F&& 
         cudaGraphExecDestroy(c->graphs.front().second);
         c->graphs.erase(c->graphs.begin());
       }
-      c->graphs.emplace_back(key, exec);
+      c->graphs.emplace_back(tkey, exec);
     }
     rc = cudaGraphLaunch(exec, stream) == cudaSuccess ? GW_OK : GW_ERR_CUDA;
   }
@@ -226,6 +229,7 @@ extern "C" {
 gw_status gw_ctx_create(gw_ctx** out, int device) {
   if (!out) return GW_ERR_INVALID;
   *out = nullptr;
+  gw::tune_autoload();
   cudaError_t e = cudaSetDevice(device);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -648,7 +652,7 @@ gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const do
   } else {
     std::string key;
     char buf[512];
-    snprintf(buf, sizeof buf, "%d %p %zu|", count, c->bws, c->bws_bytes);
+    snprintf(buf, sizeof buf, "%d %p %zu %u|", count, c->bws, c->bws_bytes, gw::tune_generation());
     key += buf;
     for (int i = 0; i < count; ++i) {
       const gw::SolveArgs& a = args[i];

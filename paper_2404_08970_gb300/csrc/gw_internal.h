@@ -183,4 +183,18 @@ int solve_group_key(const SolveArgs& a);
 int solve_group_launch(const SolveArgs* const* a, void* const* ws, const size_t* ws_bytes, int count,
                        cudaStream_t stream);
 
+// Sinkhorn row configurations (sinkhorn.cu): the built-in choice for m
+// columns, the shape of a configuration id, and every id (count returned, at
+// most cap written).
+int sk_default_config(int m, int dtype);
+bool sk_config_shape(int id, int* dtype, int* nw, int* vpt, int* ng);
+int sk_config_ids(int* out, int cap);
+
+// Tuning table (tune.cu): the entry for m columns (-1 if none), a counter
+// that changes whenever the table does (part of every cached graph's key),
+// and the one-time load at the first context creation.
+int tune_lookup(int kernel, int dtype, int m);
+unsigned tune_generation();
+void tune_autoload();
+
 }  // namespace gw

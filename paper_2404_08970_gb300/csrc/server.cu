@@ -206,6 +206,7 @@ extern "C" {
 gw_status gw_server_create(gw_server** out, int device, size_t hbm_budget_bytes, int max_slots) {
   if (!out || hbm_budget_bytes == 0 || max_slots < 1 || max_slots > 64) return GW_ERR_INVALID;
   *out = nullptr;
+  gw::tune_autoload();
   if (cudaSetDevice(device) != cudaSuccess) {
     cudaGetLastError();
     return GW_ERR_CUDA;

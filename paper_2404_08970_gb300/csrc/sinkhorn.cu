@@ -1067,10 +1067,43 @@ int solve_group(const SolveArgs* const* A, void* const* ws, const size_t* ws_byt
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }
 
-// Row configuration of the Sinkhorn kernels for m columns: warps per row
-// group NW, values per thread VPT (32 NW VPT >= m), row groups per block NG.
-// The configuration index also groups batched problems.
-int row_config(int m, int dtype) {
+// Row configurations of the Sinkhorn kernels: warps per row group NW, values
+// per thread VPT (a row group covers 32 NW VPT >= m columns), row groups per
+// block NG.  Ids 0-13 are the built-in choices by row length; ids 20-32 are
+// alternatives for the tuning table, each with half the values per thread of
+// the built-in configuration that covers the same columns.  with_config
+// below has one case per entry.
+struct SkConfig {
+  int id, dtype, nw, vpt, ng;
+};
+constexpr SkConfig kSkConfigs[] = {
+    {0, GW_F32, 1, 16, 16}, {1, GW_F32, 2, 16, 8},  {2, GW_F32, 4, 16, 4},  {3, GW_F32, 8, 16, 2},
+    {4, GW_F32, 16, 16, 1}, {5, GW_F32, 18, 16, 1}, {6, GW_F32, 32, 16, 1}, {10, GW_F64, 1, 8, 16},
+    {11, GW_F64, 4, 8, 4},  {12, GW_F64, 16, 8, 1}, {13, GW_F64, 32, 16, 1}, {20, GW_F32, 2, 8, 8},
+    {21, GW_F32, 4, 8, 4},  {22, GW_F32, 8, 8, 2},  {23, GW_F32, 16, 8, 1}, {24, GW_F32, 32, 8, 1},
+    {30, GW_F64, 2, 4, 8},  {31, GW_F64, 8, 4, 2},  {32, GW_F64, 32, 4, 1},
+};
+
+bool sk_config_shape(int id, int* dtype, int* nw, int* vpt, int* ng) {
+  for (const SkConfig& c : kSkConfigs)
+    if (c.id == id) {
+      if (dtype) *dtype = c.dtype;
+      if (nw) *nw = c.nw;
+      if (vpt) *vpt = c.vpt;
+      if (ng) *ng = c.ng;
+      return true;
+    }
+  return false;
+}
+
+int sk_config_ids(int* out, int cap) {
+  const int count = (int)(sizeof(kSkConfigs) / sizeof(kSkConfigs[0]));
+  for (int i = 0; i < count && i < cap; ++i) out[i] = kSkConfigs[i].id;
+  return count;
+}
+
+// Built-in row configuration for m columns.
+int sk_default_config(int m, int dtype) {
   if (dtype == GW_F32) {
     if (m <= 512) return 0;
     if (m <= 1024) return 1;
@@ -1086,6 +1119,13 @@ int row_config(int m, int dtype) {
   return 13;
 }
 
+// Configuration in effect for m columns: the tuning table's entry, else the
+// built-in choice.  The index also groups batched problems.
+int row_config(int m, int dtype) {
+  const int t = tune_lookup(GW_TUNE_SINKHORN, dtype, m);
+  return t >= 0 ? t : sk_default_config(m, dtype);
+}
+
 template <typename F>
 int with_config(int cfg, F&& f) {
   switch (cfg) {
@@ -1099,6 +1139,14 @@ int with_config(int cfg, F&& f) {
     case 10: return f.template run<1, 8, 16, double>();
     case 11: return f.template run<4, 8, 4, double>();
     case 12: return f.template run<16, 8, 1, double>();
+    case 20: return f.template run<2, 8, 8, float>();
+    case 21: return f.template run<4, 8, 4, float>();
+    case 22: return f.template run<8, 8, 2, float>();
+    case 23: return f.template run<16, 8, 1, float>();
+    case 24: return f.template run<32, 8, 1, float>();
+    case 30: return f.template run<2, 4, 8, double>();
+    case 31: return f.template run<8, 4, 2, double>();
+    case 32: return f.template run<32, 4, 1, double>();
     default: return f.template run<32, 16, 1, double>();
   }
 }

@@ -1,0 +1,116 @@
+"""Host logic of the tuning table (gw_tune_*): entries, precedence, checks,
+candidates and the table file.  No GPU: these entry points make no CUDA call."""
+import pytest
+
+from paper_2404_08970_gb300 import _lib as L
+
+SK = L.GW_TUNE_SINKHORN
+F32, F64 = L.GW_F32, L.GW_F64
+ROW_LENGTHS = [1, 7, 255, 256, 257, 512, 513, 900, 1024, 1025, 2048, 2049, 4096, 4097, 5000, 8192, 8193,
+               9216, 9217, 12000, 16384]
+
+
+@pytest.fixture(autouse=True)
+def clean_table():
+    L.gw_tune_clear()
+    yield
+    L.gw_tune_clear()
+
+
+def cover(config):
+    nw, vpt, _ = L.gw_tune_shape(SK, config)
+    return 32 * nw * vpt
+
+
+@pytest.mark.parametrize("dtype", [F32, F64])
+def test_builtin_choice_covers_the_row(dtype):
+    for m in ROW_LENGTHS:
+        c = L.gw_tune_config(SK, dtype, m)
+        assert c >= 0 and cover(c) >= m, (m, c)
+
+
+@pytest.mark.parametrize("dtype", [F32, F64])
+def test_candidates(dtype):
+    esz = 4 if dtype == F32 else 8
+    for m in ROW_LENGTHS:
+        cands = L.gw_tune_candidates(SK, dtype, m)
+        assert cands[0] == L.gw_tune_config(SK, dtype, m)
+        assert len(set(cands)) == len(cands)
+        base = cover(cands[0])
+        for c in cands:
+            nw, vpt, ng = L.gw_tune_shape(SK, c)
+            assert m <= 32 * nw * vpt <= 4 * base, (m, c)
+            assert 32 * nw * ng <= 1024 and (vpt * esz) % 16 == 0, (m, c)
+            # A candidate is accepted as an entry for exactly this row length.
+            L.gw_tune_set(SK, dtype, m, m, c)
+            assert L.gw_tune_config(SK, dtype, m) == c
+
+
+def test_entries_and_precedence():
+    default_800 = L.gw_tune_config(SK, F32, 800)
+    L.gw_tune_set(SK, F32, 700, 900, 21)
+    assert L.gw_tune_config(SK, F32, 800) == 21
+    assert L.gw_tune_config(SK, F32, 699) == L.gw_tune_config(SK, F32, 600)
+    assert L.gw_tune_config(SK, F32, 901) == default_800   # same built-in range (513..1024)
+    assert L.gw_tune_config(SK, F64, 800) != 21            # per dtype
+    L.gw_tune_set(SK, F32, 800, 800, 2)                    # a later entry wins
+    assert L.gw_tune_config(SK, F32, 800) == 2
+    assert L.gw_tune_config(SK, F32, 799) == 21
+    L.gw_tune_clear()
+    assert L.gw_tune_config(SK, F32, 800) == default_800
+
+
+@pytest.mark.parametrize("args", [
+    (1, F32, 1, 512, 0),        # unknown kernel
+    (SK, 7, 1, 512, 0),         # unknown dtype
+    (SK, F32, 0, 512, 0),       # empty / non-positive range
+    (SK, F32, 600, 500, 1),
+    (SK, F32, 1, 20000, 6),     # beyond the solver's 16384 columns
+    (SK, F32, 1, 2000, 21),     # 4 x 8 x 32 = 1024 columns do not cover 2000
+    (SK, F64, 1, 256, 20),      # a float configuration for double rows
+    (SK, F32, 1, 256, 99),      # no such configuration
+])
+def test_invalid_entries_rejected(args):
+    with pytest.raises(L.GWError) as e:
+        L.gw_tune_set(*args)
+    assert e.value.status == L.GW_ERR_INVALID
+    assert L.gw_tune_config(SK, F32, 300) == L.gw_tune_candidates(SK, F32, 300)[0]
+
+
+def test_queries_reject_bad_arguments():
+    assert L.gw_tune_config(SK, F32, 0) == -1
+    assert L.gw_tune_config(SK, F32, 16385) == -1
+    assert L.gw_tune_config(3, F32, 100) == -1
+    with pytest.raises(L.GWError):
+        L.gw_tune_candidates(SK, 5, 100)
+    with pytest.raises(L.GWError):
+        L.gw_tune_shape(SK, 99)
+
+
+def test_table_file(tmp_path):
+    good = tmp_path / "tune_table.txt"
+    good.write_text("# kernel dtype m_lo m_hi config\n"
+                    "\n"
+                    f"{SK} {F32} 513 1024 21   # 4 x 8 x 4\n"
+                    f"   {SK} {F64} 1 256 30\n")
+    L.gw_tune_load(str(good))
+    assert L.gw_tune_config(SK, F32, 600) == 21
+    assert L.gw_tune_config(SK, F64, 100) == 30
+
+    L.gw_tune_clear()
+    bad = tmp_path / "bad.txt"
+    bad.write_text(f"{SK} {F32} 513 1024 21\n"
+                   f"{SK} {F32} 1 2000 21\n"       # does not cover 2000 columns
+                   f"{SK} {F64} 1 256 30\n")
+    with pytest.raises(L.GWError):
+        L.gw_tune_load(str(bad))
+    assert L.gw_tune_config(SK, F32, 600) == 21      # the line before the bad one stays
+    assert L.gw_tune_config(SK, F64, 100) != 30      # the lines after it are not read
+
+    L.gw_tune_clear()
+    junk = tmp_path / "junk.txt"
+    junk.write_text(f"{SK} {F32} 513 1024\n")
+    with pytest.raises(L.GWError):
+        L.gw_tune_load(str(junk))
+    with pytest.raises(L.GWError):
+        L.gw_tune_load(str(tmp_path / "missing.txt"))
