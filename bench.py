@@ -78,10 +78,16 @@ def workload(n, k):
     return I.workload_1d_grad(n, k, "uniform", seed=0)
 
 
+L2_BYTES = 126 * 2 ** 20
+
+
 def config(n, k, extra=None):
+    mb = 4 * n * n / 1e6
+    l2 = (f"inputs larger than L2 ({mb:.0f} MB T, {mb:.0f} MB G)" if 4 * n * n > L2_BYTES else
+          f"inputs fit in L2 ({mb:.1f} MB T, {mb:.1f} MB G): not a valid bench size, for profiling only")
     c = {"workload": f"1D uniform grids n=m={n}, k={k}, uniform marginals, random positive coupling, h=1/n; "
                      f"one structured gradient evaluation per step",
-         "n": n, "m": n, "k": k, "marginals": "target (uniform)", "l2": "inputs larger than L2 (268 MB T, 268 MB G)",
+         "n": n, "m": n, "k": k, "marginals": "target (uniform)", "l2": l2,
          "global_batch": 1, "parallelism": "replicas"}
     if extra:
         c.update(extra)
