@@ -98,9 +98,9 @@ def sweep(n: int = 2048, reps: int = 3, log=print):
     return entries, notes
 
 
-def write_table(path: str, entries, notes, n: int, reps: int) -> None:
-    import torch
-    name = torch.cuda.get_device_name(0)
+def write_table(path: str, entries, notes, n: int, reps: int, device_name: str) -> None:
+    """Writes the table in the format gw_tune_load reads."""
+    name = device_name
     when = datetime.datetime.now(datetime.timezone.utc).strftime("%Y-%m-%dT%H:%M:%SZ")
     lines = [f"# Sinkhorn row configurations tuned on {name}, {when}",
              f"# n = {n} rows, best of {reps} solves of one mirror-descent step x 20 iterations",
@@ -118,8 +118,9 @@ def main() -> int:
     ap.add_argument("--n", type=int, default=2048)
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
+    import torch
     entries, notes = sweep(args.n, args.reps)
-    write_table(args.out, entries, notes, args.n, args.reps)
+    write_table(args.out, entries, notes, args.n, args.reps, torch.cuda.get_device_name(0))
     print(f"wrote {args.out}: {len(entries)} entries, {len(notes)} notes")
     return 0
 

@@ -114,3 +114,28 @@ def test_table_file(tmp_path):
         L.gw_tune_load(str(junk))
     with pytest.raises(L.GWError):
         L.gw_tune_load(str(tmp_path / "missing.txt"))
+
+
+def test_sweep_ranges_and_table_round_trip(tmp_path):
+    """The sweep's half ranges tile each built-in range, and the table it
+    writes is read back by gw_tune_load with the same entries."""
+    from paper_2404_08970_gb300 import tune
+    for dtype, ranges in tune.RANGES.items():
+        prev_hi = 0
+        for lo, hi in ranges:
+            assert lo == prev_hi + 1
+            assert L.gw_tune_config(SK, dtype, lo) == L.gw_tune_config(SK, dtype, hi)   # one built-in choice
+            parts = tune.halves(lo, hi)
+            assert parts[0][0] == lo and parts[-1][1] == hi
+            assert all(b + 1 == c for (_, b), (c, _) in zip(parts, parts[1:]))
+            prev_hi = hi
+        assert prev_hi == 16384
+    entries = [(F32, 513, 768, 21, {1: 0.5, 21: 0.4}), (F32, 769, 1024, 1, {1: 0.5, 21: 0.6}),
+               (F64, 1, 128, 30, {10: 1.0, 30: 0.9})]
+    path = tmp_path / "tune_table.txt"
+    tune.write_table(str(path), entries, ["dtype 0 m 1024 config 2: plan differs by 1.00e-02; dropped"], 2048, 3,
+                     "test device")
+    L.gw_tune_load(str(path))
+    assert L.gw_tune_config(SK, F32, 600) == 21
+    assert L.gw_tune_config(SK, F32, 900) == 1
+    assert L.gw_tune_config(SK, F64, 100) == 30
