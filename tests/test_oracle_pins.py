@@ -414,3 +414,101 @@ def test_planted_mistakes():
         a2[i + 1] = x[i - 1] + a1[i] + a2[i]
         a3[i + 1] = x[i - 1] + a1[i] + 1 * a2[i] + a3[i]
     assert [int(a3[i]) for i in range(1, 9)] != [int(w) for w in want]
+
+
+# ---------------------------------------------------------------------------
+# Entropy (eq. "entropic GW") and the sampled-row gradient
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,m", [(1, 1), (3, 5), (40, 17)])
+def test_entropy_product_coupling_closed_form(n, m):
+    """Uniform product coupling T = u v^T, T_ip = 1/(nm):
+    H = sum T (ln T - 1) = -ln(nm) - 1."""
+    T = np.full((n, m), 1.0 / (n * m))
+    assert abs(O.entropy(T) - (-math.log(n * m) - 1.0)) < 1e-13
+
+
+@pytest.mark.parametrize("n", [1, 4, 9])
+def test_entropy_with_exact_zeros(n):
+    """A permutation coupling T = I / n has n entries 1/n and n^2 - n exact
+    zeros; with 0 ln 0 = 0 the entropy is ln(1/n) - 1, finite."""
+    T = np.eye(n) / n
+    H = O.entropy(T)
+    assert math.isfinite(H)
+    assert abs(H - (-math.log(n) - 1.0)) < 1e-13
+
+
+def test_entropy_sinkhorn_identity():
+    """For a plan T = exp((f_i + g_p - Pi_ip) / eps), ln T is known exactly, so
+    eps H(T) = sum T (f_i + g_p - Pi_ip) - eps sum T.  This fixes the sign and
+    the -1 independently of how ln is evaluated."""
+    u, v, Pi = _small_problem(seed=7)
+    eps = 0.05
+    f, g = O.sinkhorn_log(Pi, u, v, eps, 25)
+    T = O.plan(Pi, f, g, eps)
+    want = float(np.sum(T * (f[:, None] + g[None, :] - Pi))) - eps * float(np.sum(T))
+    assert abs(eps * O.entropy(T) - want) <= 1e-13 * abs(want)
+
+
+def test_entropy_scaling_law():
+    """H(cT) = c H(T) + c ln(c) sum T for c > 0 (ln(cT) = ln c + ln T)."""
+    rng = np.random.default_rng(41)
+    T = rng.uniform(0.0, 1.0, size=(6, 7))
+    T[1, 2] = 0.0
+    c = 3.7
+    want = c * O.entropy(T) + c * math.log(c) * float(np.sum(T))
+    assert abs(O.entropy(c * T) - want) <= 1e-13 * abs(want)
+
+
+def _grad_rows_cases():
+    rng = np.random.default_rng(43)
+    n, m = 11, 11          # square, so a transposed T would still multiply
+    DX, DY = O.grid_dist_1d(n, 0.3, 2), O.grid_dist_1d(m, 0.2, 1)
+    T = rng.uniform(0.1, 1.0, size=(n, m))
+    yield DX, DY, T, T.sum(axis=1), T.sum(axis=0), [0, 3, 10]
+    sx, sy = 3, 4
+    DX2 = O.grid_dist_2d(sx, 0.5, "manhattan")
+    DY2 = O.grid_dist_2d(sy, 1.0 / 3, "sqeuclid")
+    T2 = rng.uniform(0.1, 1.0, size=(sx * sx, sy * sy))
+    u2, v2 = I.dirichlet(sx * sx, 1.0, rng), I.dirichlet(sy * sy, 1.0, rng)
+    yield DX2, DY2, T2, u2, v2, [8, 1, 4]
+
+
+def test_grad_rows_equals_selected_rows_of_grad():
+    """grad_rows on the rows I (their distance rows and constant terms) is
+    exactly the rows I of the full gradient, 1D and 2D."""
+    for DX, DY, T, r, c, rows in _grad_rows_cases():
+        G = O.grad(DX, DY, T, r, c)
+        cx = (DX * DX) @ r
+        cy = (DY * DY) @ c
+        Gr = O.grad_rows(DX[rows], DY, T, cx[rows], cy)
+        assert relerr(Gr, G[rows]) < 1e-14
+        # ... and, with T's marginals, equal to the brute-force entry formula.
+        if r is not None and np.allclose(r, T.sum(axis=1)):
+            assert relerr(Gr, O.grad_brute(DX, DY, T)[rows]) < 1e-12
+
+
+def test_entropy_and_grad_rows_planted_mistakes():
+    """Each plausible mistake in entropy() or grad_rows() fails a pin above."""
+    n, m = 3, 5
+    T = np.full((n, m), 1.0 / (n * m))
+    closed = -math.log(n * m) - 1.0
+    no_minus_one = float(np.sum(T * np.log(T)))
+    flipped = -O.entropy(T)
+    assert abs(no_minus_one - closed) > 0.5 and abs(flipped - closed) > 0.5
+    Z = np.eye(4) / 4
+    with np.errstate(divide="ignore", invalid="ignore"):
+        nan_zero = float(np.sum(Z * (np.log(Z) - 1.0)))
+    assert not math.isfinite(nan_zero)
+    for DX, DY, T, r, c, rows in _grad_rows_cases():
+        G = O.grad(DX, DY, T, r, c)
+        cx, cy = (DX * DX) @ r, (DY * DY) @ c
+        wrong = {
+            "T transposed": cx[rows][:, None] + cy[None, :] - 2.0 * ((DX[rows] @ T.T) @ DY) if T.shape[0] == T.shape[1] else None,
+            "constant terms of other rows": cx[rows[::-1]][:, None] + cy[None, :] - 2.0 * ((DX[rows] @ T) @ DY),
+            "factor 4": cx[rows][:, None] + cy[None, :] - 4.0 * ((DX[rows] @ T) @ DY),
+            "distance rows off by one": cx[rows][:, None] + cy[None, :] - 2.0 * ((DX[np.array(rows) - 1] @ T) @ DY),
+        }
+        for name, Gr in wrong.items():
+            if Gr is not None:
+                assert relerr(Gr, G[rows]) > 1e-3, name
