@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-serve", dest="serve", action="store_false")
     ap.add_argument("--serve-count", type=int, default=1500)
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
@@ -334,6 +335,10 @@ def bench_batch(ctx, L, dev, stream, barrier, count):
             "first_call_s_incl_capture": t_first, "all_values_finite": bool(np.all(np.isfinite(vals)))}
 
 
+# Size classes of served requests by n*m (points of X times points of Y).
+SIZE_CLASSES = [("nm<1e6", 0, 1e6), ("1e6<=nm<1e7", 1e6, 1e7), ("1e7<=nm<1e8", 1e7, 1e8), ("nm>=1e8", 1e8, 1e30)]
+
+
 def bench_serve(L, device, count, slots=8):
     """Serving: requests of four kinds (1D/2D, GW/fused GW), N per space
     log-uniform in [128, 16384], eps = 1e-2, 10 x 50, through gw_submit /
@@ -353,6 +358,8 @@ def bench_serve(L, device, count, slots=8):
                          feat_dim=0 if r.get("phi") is None else r["phi"].shape[1], dtype=L.GW_F32)
 
     probs = [prob(r) for r in reqs]
+    sizes = [(r["nx"] ** 2 if r["dim"] == 2 else r["nx"]) * (r["ny"] ** 2 if r["dim"] == 2 else r["ny"])
+             for r in reqs]
 
     def run(arrivals):
         t0 = time.perf_counter()
@@ -373,7 +380,14 @@ def bench_serve(L, device, count, slots=8):
                     bad += res[0] != L.GW_OK
             time.sleep(0.001)
         wall = time.perf_counter() - t0
-        la = np.array([lat[i] for i in range(100, len(tickets))]) if len(tickets) > 100 else np.array(list(lat.values()))
+        keep = range(100, len(tickets)) if len(tickets) > 100 else range(len(tickets))
+        la = np.array([lat[i] for i in keep])
+        run.by_class = {}
+        for name, lo, hi in SIZE_CLASSES:
+            sel = [lat[i] for i in keep if lo <= sizes[i] < hi]
+            if sel:
+                run.by_class[name] = {"count": len(sel), "p50_s": float(np.percentile(sel, 50)),
+                                      "p99_s": float(np.percentile(sel, 99))}
         return wall, la, bad
 
     try:
@@ -394,7 +408,8 @@ def bench_serve(L, device, count, slots=8):
         gaps = np.random.default_rng(1).exponential(1.0 / rate, size=count)
         wall, la, bad = run(list(np.cumsum(gaps)))
         out["at_0.8_capacity"] = {"rate_per_s": rate, "p50_s": float(np.percentile(la, 50)),
-                                  "p99_s": float(np.percentile(la, 99)), "errors": int(bad)}
+                                  "p99_s": float(np.percentile(la, 99)), "errors": int(bad),
+                                  "by_size_class": run.by_class}
         return out
     finally:
         srv.close()
@@ -405,14 +420,19 @@ def bench_serve(L, device, count, slots=8):
 # ---------------------------------------------------------------------------
 
 def run_reference(args):
+    """The oracle arm: each step is one bounded sample of the workload, the
+    first R rows of the FP64 dense-definition gradient, with R chosen so that
+    the whole warm-up + timed run takes about REF_RUN_S seconds.  ms_per_step
+    is the measured time of one such step; value converts it to whole
+    gradients per second (R/n of a gradient per step)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     w = workload(args.n, args.k)
-    import numpy as np
     n = args.n
-    # Each step: one bounded row sample of the oracle gradient.
-    rate0, rows, t = cpu_oracle_rate(w, budget_s=4.0)
+    t16 = oracle_rows_time(w["T"], w["u"], w["v"], w["k"], w["hx"], 16)
+    per_row = max(t16 / 16, 1e-6)
+    rows = int(min(n, max(16, REF_RUN_S / max(1, args.steps + args.warmup) / per_row)))
     for _ in range(args.warmup):
         oracle_rows_time(w["T"], w["u"], w["v"], w["k"], w["hx"], rows)
     times = [oracle_rows_time(w["T"], w["u"], w["v"], w["k"], w["hx"], rows) for _ in range(args.steps)]
@@ -420,14 +440,34 @@ def run_reference(args):
     value = args.steps * (rows / n) / tot
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps / (rows / n),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "step": f"first {rows} of {n} rows of one gradient ({rows / n:.4f} of a gradient evaluation)",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config(n, args.k),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{rows} of {n} gradient rows per step (dense FP64 definition, numpy)"},
+                             "sample": f"{rows} of {n} gradient rows per step (dense FP64 definition, numpy), "
+                                       f"{1e3 * tot / args.steps:.0f} ms per step"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
+
+
+REF_RUN_S = 90.0
+
+
+def single_thread_oracle(w, rows):
+    """Seconds for `rows` oracle gradient rows in a child process limited to
+    one BLAS/OpenMP thread (the paper times single-threaded).  None if the
+    child fails."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               BLIS_NUM_THREADS="1", VECLIB_MAXIMUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-sample", str(rows), "--n", str(w["T"].shape[0]),
+           "--k", str(w["k"])]
+    try:
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=300)
+        return float(json.loads(out.stdout.strip().splitlines()[-1])["seconds"])
+    except Exception:
+        return None
 
 
 def run_ours(args):
@@ -506,25 +546,28 @@ def run_ours(args):
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms}
     whole_gbs = 8.0 * nm / (per_step / 1e3) / 1e9
 
-    # End to end: pinned host T -> device, gradient, G -> pinned host, every step.
+    # End to end through gw_grad_host: page-locked host u, v, T in, G out, every
+    # step (the library pipelines one step's copy-in with the previous step's
+    # gradient and copy-out over two device slots).  Timed on the host clock
+    # from the first call to the synchronisation after the last.
     hT = T32.pin_memory()
     hG = torch.empty_like(hT).pin_memory()
+    hu = torch.from_numpy(w["u"]).pin_memory()
+    hv = torch.from_numpy(w["v"]).pin_memory()
     e_steps = max(3, min(args.steps, 20))
-    for _ in range(2):
-        dT.copy_(hT, non_blocking=True)
-        step()
-        hG.copy_(dG, non_blocking=True)
+    for _ in range(3):
+        ctx.gw_grad_host(prob, hu, hv, hT, hG, L.GW_MARG_TARGET, stream)
+    ctx.gw_ctx_check(stream)
     barrier()
-    e0.record(stream)
+    t0 = time.perf_counter()
     for _ in range(e_steps):
-        dT.copy_(hT, non_blocking=True)
-        step()
-        hG.copy_(dG, non_blocking=True)
-    e1.record(stream)
+        ctx.gw_grad_host(prob, hu, hv, hT, hG, L.GW_MARG_TARGET, stream)
     barrier()
-    e_ms = max_over_ranks(e0.elapsed_time(e1), dev)
-    e2e = {"value": job_rate(world, e_steps, e_ms), "unit": UNIT, "h2d_bytes_per_step": 4 * nm,
-           "d2h_bytes_per_step": 4 * nm}
+    e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), dev)
+    ctx.gw_ctx_check(stream)
+    e2e = {"value": job_rate(world, e_steps, e_ms), "unit": UNIT, "h2d_bytes_per_step": 4 * nm + 16 * n,
+           "d2h_bytes_per_step": 4 * nm, "api": "gw_grad_host (C ABI, page-locked host buffers)",
+           "ms_per_step": e_ms / e_steps, "copy_gbs_per_direction": 4 * nm / (e_ms / e_steps / 1e3) / 1e9}
 
     # Dense comparison (cuBLAS, materialised distance matrices) on the same T.
     dense = {}
@@ -544,6 +587,27 @@ def run_ours(args):
                            "tflops": 2.0 * 2.0 * n * n * n / (dms / 1e3) / 1e12}
         except Exception as ex:  # reported, not hidden
             dense[name] = {"error": str(ex)[:200]}
+    # The structured gradient in FP64 on the same T (the paper's precision).
+    try:
+        dT64 = dT.double()
+        dG64 = torch.empty_like(dT64)
+        prob64 = L.problem(dim=1, nx=n, ny=n, hx=w["hx"], hy=w["hy"], k=k, dtype=L.GW_F64)
+        for _ in range(3):
+            ctx.gw_grad(prob64, du, dv, dT64, dG64, L.GW_MARG_TARGET, stream)
+        barrier()
+        e0.record(stream)
+        for _ in range(10):
+            ctx.gw_grad(prob64, du, dv, dT64, dG64, L.GW_MARG_TARGET, stream)
+        e1.record(stream)
+        barrier()
+        ctx.gw_ctx_check(stream)
+        f64ms = e0.elapsed_time(e1) / 10
+        structured_f64 = {"evals_per_s": 1e3 / f64ms, "ms": f64ms,
+                          "whole_gradient_gbs": 16.0 * nm / (f64ms / 1e3) / 1e9,
+                          "note": "same T widened to double; 16 B per element (read T, write G)"}
+        del dT64, dG64
+    except Exception as ex:
+        structured_f64 = {"error": str(ex)[:200]}
     best = max((d.get("evals_per_s", 0.0) for d in dense.values()), default=0.0)
     dense["structured_over_best_dense"] = (value / world) / best if best > 0 else None
 
@@ -613,6 +677,11 @@ def run_ours(args):
         rate, rows, t = cpu_oracle_rate(w)
         cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{rows} of {n} rows of the FP64 dense-definition gradient (numpy), {t:.1f} s"}
+        st_rows = max(16, min(n, int(rows * 8.0 / max(t, 1e-3) / max(1, os.cpu_count()))))
+        t1 = single_thread_oracle(w, st_rows)
+        if t1:
+            cpu["single_thread"] = {"value": (st_rows / n) / t1, "unit": UNIT, "cores": 1,
+                                    "sample": f"{st_rows} of {n} rows, {t1:.1f} s, one BLAS thread"}
         # The oracle reads the same FP32 values of T as the GPU paths.
         Gs = oracle_rows(T32.numpy().astype(np.float64), w["u"], w["v"], k, w["hx"], w["hy"], err_rows)
         den = float(np.max(np.abs(Gs)))
@@ -626,6 +695,7 @@ def run_ours(args):
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(n, k),
                 "roofline": roof, "whole_gradient_gbs": whole_gbs, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": launches, "kernels": prof, "dense": dense,
+                "structured_f64": structured_f64,
                 "errors_vs_fp64": errs, "solve": solve,
                 "grid2d": grid2d, "batch": batch, "serve": serve}
         print(json.dumps(line))
@@ -637,6 +707,12 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.oracle_sample:
+        # Child of single_thread_oracle: time `rows` oracle rows, print seconds.
+        w = workload(args.n, args.k)
+        t = oracle_rows_time(w["T"], w["u"], w["v"], w["k"], w["hx"], args.oracle_sample)
+        print(json.dumps({"seconds": t}))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

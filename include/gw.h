@@ -62,7 +62,14 @@ typedef enum { GW_F32 = 0, GW_F64 = 1 } gw_dtype;
 typedef enum { GW_COST_POW = 0, GW_COST_SQEUCLID = 1 } gw_cost;
 
 /* Arithmetic of the dense comparison gradient (gw_grad_dense). */
-typedef enum { GW_DENSE_FP32 = 0, GW_DENSE_TF32 = 1, GW_DENSE_BF16 = 2, GW_DENSE_FP64 = 3 } gw_dense_precision;
+typedef enum {
+  GW_DENSE_FP32 = 0,
+  GW_DENSE_TF32 = 1,
+  GW_DENSE_BF16 = 2,
+  GW_DENSE_FP64 = 3,
+  GW_DENSE_TC_TF32 = 4, /* the library's own tcgen05 kernels, TF32 inputs */
+  GW_DENSE_TC_BF16 = 5  /* the library's own tcgen05 kernels, BF16 inputs */
+} gw_dense_precision;
 
 /* Which marginals build the constant term c_x, c_y of the gradient. */
 typedef enum { GW_MARG_TARGET = 0, GW_MARG_EXACT = 1 } gw_marginals;
@@ -142,6 +149,37 @@ gw_status gw_grad(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const 
                   const void* d_T, void* d_G, int marginals, void* stream);
 
 /*
+ * gw_grad_host - gw_grad on host buffers: the same gradient (Sec. 3, eqs.
+ * "Dx", "1d y", "1d recursive relation"; Sec. 3.1 for dim 2), for callers
+ * whose T lives in host memory.
+ *
+ *   prob, marginals   as for gw_grad.
+ *   h_u, h_v          host marginals (double, n and m); read only with
+ *                     GW_MARG_TARGET.
+ *   h_T               host coupling, n x m row-major, prob->dtype.
+ *   h_G               host output, n x m row-major, prob->dtype; must not
+ *                     overlap h_T.
+ *   stream            the caller's stream: work enqueued on it after this
+ *                     call runs after h_G has been written, so
+ *                     cudaStreamSynchronize(stream) (or gw_ctx_check with
+ *                     the same stream) makes h_G ready to read.
+ *
+ * Asynchronous: the call returns once the copy of h_T to the device, the
+ * gradient and the copy of G back are enqueued on the context's own streams.
+ * It does not wait for earlier work on `stream`, so h_u, h_v and h_T must
+ * hold their values when the call is made, and none of the host buffers may
+ * be changed or freed until `stream` has been synchronised.  Two device
+ * slots (T and G each) owned by the context are used in turn, so a call's
+ * copy-in overlaps the previous call's gradient and copy-out.  Page-locked
+ * host buffers (cudaHostAlloc) make the copies fully asynchronous; pageable
+ * ones are still correct, at copy speeds the driver chooses.  The slots are
+ * grown on demand (the device is synchronised when that happens).
+ * Errors: as gw_grad; GW_ERR_OOM if the slots cannot be allocated.
+ */
+gw_status gw_grad_host(gw_ctx* ctx, const gw_problem* prob, const double* h_u, const double* h_v,
+                       const void* h_T, void* h_G, int marginals, void* stream);
+
+/*
  * gw_grad_noalloc - gw_grad without any device allocation (the paper has no
  * counterpart; this is a deployment convenience).
  *
@@ -159,8 +197,11 @@ gw_status gw_grad(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const 
  *   The first call on each device looks up the array's device address (make
  *   that first call before any stream capture).  All calls share the array:
  *   calls that overlap on the GPU (different streams, no ordering) race.
- *   Bounded device waits still end, but this entry point does not report
- *   them (there is no context status word).
+ *   hx and hy must be finite and positive.  The kernels' bounded device
+ *   waits share one static status word too, cleared on `stream` before each
+ *   launch, so that a launch whose wait has run out ends quickly; such a
+ *   failure leaves G invalid and is not reported by the return value (the
+ *   call returns before the kernels run).
  */
 gw_status gw_grad_noalloc(const gw_problem* prob, const double* d_u, const double* d_v, const void* d_T,
                           void* d_G, int marginals, void* stream);
@@ -174,7 +215,13 @@ gw_status gw_grad_noalloc(const gw_problem* prob, const double* d_u, const doubl
  *
  *   precision  GW_DENSE_FP32 (FP32 CUDA cores), GW_DENSE_TF32 or GW_DENSE_BF16
  *              (tensor cores, FP32 accumulation; BF16 rounds T, D and the
- *              intermediate D_X T to bfloat16), GW_DENSE_FP64.
+ *              intermediate D_X T to bfloat16), GW_DENSE_FP64: products by
+ *              cuBLAS.  GW_DENSE_TC_TF32 and GW_DENSE_TC_BF16: the same
+ *              products on the library's own tcgen05 kernels (TMA-fed
+ *              128 x 256 tiles, FP32 accumulators in tensor memory, the
+ *              constant terms added in the second product's epilogue, so Z
+ *              is never stored); inputs rounded as for the cuBLAS forms
+ *              (TF32 keeps the top 19 bits of each float).
  *   prob->dtype must be GW_F64 for GW_DENSE_FP64 and GW_F32 otherwise; the
  *   other arguments are as for gw_grad (dim 1 or 2; in 2D the distance
  *   matrices are n x n and m x m over the grid points).  The dense distance
@@ -254,10 +301,16 @@ gw_status gw_solve_batch(gw_ctx* ctx, int count, const gw_problem* probs, const 
  * mode of the same method; the paper has no counterpart).
  *
  * gw_server_create starts `max_slots` (1..64) worker threads on CUDA device
- * `device`, each with its own stream.  Requests run in arrival order as soon
- * as the device-memory budget `hbm_budget_bytes` has room for them (inputs,
- * plan, statistics and solve workspace); a finished request frees its memory
- * and slot for the next one.  Up to max_slots requests run concurrently.
+ * `device`, each with its own stream.  A free worker takes the oldest queued
+ * request that fits in the unused part of the device-memory budget
+ * `hbm_budget_bytes` (inputs, plan, statistics and solve workspace), so a
+ * large request waiting for memory does not hold up smaller ones behind it;
+ * once the oldest request has been passed over 32 times, nothing else is
+ * admitted until it fits (no starvation).  A finished request frees its
+ * memory and slot for the next one.  Up to max_slots requests run
+ * concurrently.  Inputs are copied to the device from page-locked staging
+ * buffers; the plan is copied into h_T as given (page-locked h_T copies
+ * fastest).
  */
 typedef struct gw_server gw_server;
 

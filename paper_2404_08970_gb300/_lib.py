@@ -93,6 +93,7 @@ def load() -> ctypes.CDLL:
         "gw_solve": (S, [P, prob, P, P, P, P, P, P, P, P, P]),
         "gw_grad_dense": (S, [P, prob, P, P, P, P, I, I, P]),
         "gw_grad_noalloc": (S, [prob, P, P, P, P, I, P]),
+        "gw_grad_host": (S, [P, prob, P, P, P, P, I, P]),
         "gw_solve_batch": (S, [P, I, prob, P, P, P, P, P, P, P]),
         "gw_server_create": (S, [ctypes.POINTER(P), I, ctypes.c_size_t, I]),
         "gw_server_destroy": (None, [P]),
@@ -249,6 +250,13 @@ class Context:
                               _stream(stream))
         return self._check(st, "gw_grad")
 
+    def gw_grad_host(self, prob: gw_problem, u, v, T, G, marginals=GW_MARG_TARGET, stream=None) -> int:
+        """u, v, T, G: host arrays (numpy, or CPU tensors, preferably pinned);
+        G is ready once `stream` is synchronised."""
+        st = self.lib.gw_grad_host(self.h, ctypes.byref(prob), _host_ptr(u), _host_ptr(v), _host_ptr(T),
+                                   _host_ptr(G), marginals, _stream(stream))
+        return self._check(st, "gw_grad_host")
+
     def gw_solve(self, prob: gw_problem, u, v, T, f=None, g=None, stats=None, phi=None, psi=None,
                  stream=None) -> int:
         st = self.lib.gw_solve(self.h, ctypes.byref(prob), _ptr(u), _ptr(v), _ptr(phi), _ptr(psi), _ptr(T),
@@ -279,9 +287,13 @@ class Context:
 
 
 def _host_ptr(a):
-    """Address of a C-contiguous numpy array (or None)."""
+    """Address of a C-contiguous numpy array or CPU tensor (or None)."""
     if a is None:
         return None
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("host tensors must be contiguous CPU tensors")
+        return a.data_ptr()
     if not a.flags["C_CONTIGUOUS"]:
         raise ValueError("host arrays must be C-contiguous")
     return a.ctypes.data

@@ -18,7 +18,7 @@ namespace gw {
 // of side x side points (i = a * side + b): Manhattan h (|a-a'| + |b-b'|)
 // (sq = 0) or squared Euclidean h^2 ((a-a')^2 + (b-b')^2) (sq = 1).
 template <typename Out>
-__global__ void build_dist(Out* __restrict__ D, int n, double hk, int k, int side, int sq) {
+__global__ void build_dist(Out* __restrict__ D, int n, double hk, int k, int side, int sq, int pitch) {
   const size_t N = (size_t)n * n;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
     const long long i = (long long)(idx / n), j = (long long)(idx % n);
@@ -31,7 +31,7 @@ __global__ void build_dist(Out* __restrict__ D, int n, double hk, int k, int sid
       v = 1.0;
       for (int e = 0; e < k; ++e) v *= d;
     }
-    D[idx] = (Out)(hk * v);
+    D[(size_t)i * pitch + j] = (Out)(hk * v);
   }
 }
 
@@ -47,6 +47,17 @@ __global__ void to_bf16(const float4* __restrict__ x, __nv_bfloat162* __restrict
 __global__ void to_bf16_tail(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, size_t from, size_t N) {
   for (size_t i = from + (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
     y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// Rows of a float matrix (n x m) copied to pitch mp >= m in type Out, the
+// padding zero.
+template <typename Out>
+__global__ void pad_rows(const float* __restrict__ T, int n, int m, Out* __restrict__ Tp, int mp) {
+  const size_t N = (size_t)n * mp;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = idx / mp, p = idx % mp;
+    Tp[idx] = (Out)(p < (size_t)m ? T[i * m + p] : 0.f);
+  }
 }
 
 // G = cx_i + cy_p - s * Z_ip, in place on Z (= G).  cx, cy hold hi parts first.
@@ -120,10 +131,18 @@ __global__ void col_sums(const Real* __restrict__ T, int n, int m, double* __res
 }
 
 struct DenseCache {
-  int n = 0, k = 0, prec = -1, side = 0, sq = 0;
+  int n = 0, k = 0, prec = -1, side = 0, sq = 0, pitch = 0;
   double h = 0;
   void* D = nullptr;
 };
+
+// Row pitch (elements) of the matrices the tcgen05 kernels read: a multiple
+// of 16 bytes, padding zero.
+int tc_pitch(int n, int prec) {
+  const int q = prec == GW_DENSE_TC_BF16 ? 8 : 4;
+  return (n + q - 1) / q * q;
+}
+bool is_tc(int prec) { return prec == GW_DENSE_TC_BF16 || prec == GW_DENSE_TC_TF32; }
 
 struct DenseState {
   cublasHandle_t handle = nullptr;
@@ -137,19 +156,23 @@ static int ensure_dist(DenseCache& c, int n, double h, int k, int side, int sq, 
     cudaFree(c.D);
     c.D = nullptr;
   }
-  const size_t esz = prec == GW_DENSE_BF16 ? 2 : (prec == GW_DENSE_FP64 ? 8 : 4);
-  if (cudaMalloc(&c.D, (size_t)n * n * esz) != cudaSuccess) {
+  const bool bf = prec == GW_DENSE_BF16 || prec == GW_DENSE_TC_BF16;
+  const size_t esz = bf ? 2 : (prec == GW_DENSE_FP64 ? 8 : 4);
+  const int pitch = is_tc(prec) ? tc_pitch(n, prec) : n;
+  if (cudaMalloc(&c.D, (size_t)pitch * pitch * esz) != cudaSuccess) {
     cudaGetLastError();
     c.D = nullptr;
     return GW_ERR_OOM;
   }
   const double hk = side > 0 ? (sq ? h * h : h) : std::pow(h, k);
-  if (prec == GW_DENSE_BF16)
-    build_dist<__nv_bfloat16><<<1024, 256, 0, st>>>((__nv_bfloat16*)c.D, n, hk, k, side, sq);
+  if (pitch != n) cudaMemsetAsync(c.D, 0, (size_t)pitch * pitch * esz, st);
+  if (bf)
+    build_dist<__nv_bfloat16><<<1024, 256, 0, st>>>((__nv_bfloat16*)c.D, n, hk, k, side, sq, pitch);
   else if (prec == GW_DENSE_FP64)
-    build_dist<double><<<1024, 256, 0, st>>>((double*)c.D, n, hk, k, side, sq);
+    build_dist<double><<<1024, 256, 0, st>>>((double*)c.D, n, hk, k, side, sq, pitch);
   else
-    build_dist<float><<<1024, 256, 0, st>>>((float*)c.D, n, hk, k, side, sq);
+    build_dist<float><<<1024, 256, 0, st>>>((float*)c.D, n, hk, k, side, sq, pitch);
+  c.pitch = pitch;
   c.n = n;
   c.h = h;
   c.k = k;
@@ -173,7 +196,11 @@ void dense_state_destroy(void* p) {
 size_t dense_workspace_bytes(int n, int m, int prec) {
   const size_t nm = (size_t)n * m;
   size_t b = 0;
-  if (prec == GW_DENSE_BF16) b += 2 * nm * 2;           // T and Y in bf16
+  if (is_tc(prec)) {
+    // T with padded rows (n x mp) and C1 = D_Y T^T (m x np), in the input type.
+    const size_t es = prec == GW_DENSE_TC_BF16 ? 2 : 4;
+    b += (size_t)n * tc_pitch(m, prec) * es + (size_t)m * tc_pitch(n, prec) * es + 1024;
+  } else if (prec == GW_DENSE_BF16) b += 2 * nm * 2;   // T and Y in bf16
   else if (prec == GW_DENSE_FP64) b += nm * 8;          // Y
   else b += nm * 4;                                     // Y
   b += ((size_t)2 * (n + m) * 8) + (size_t)(n + m) * 8 + marg_part_doubles(n, 3) * 8 + marg_part_doubles(m, 3) * 8 + 8192;
@@ -205,7 +232,13 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
   const size_t rb = dbl ? 8 : 4;
   void* Tin = (void*)a.T;
   void* Y = nullptr;
-  if (a.prec == GW_DENSE_BF16) {
+  const bool tc = is_tc(a.prec);
+  const int np = tc ? tc_pitch(n, a.prec) : n, mp = tc ? tc_pitch(m, a.prec) : m;
+  if (tc) {
+    const size_t es = a.prec == GW_DENSE_TC_BF16 ? 2 : 4;
+    Tin = take((size_t)n * mp * es);
+    Y = take((size_t)m * np * es);
+  } else if (a.prec == GW_DENSE_BF16) {
     Tin = take(nm * 2);
     Y = take(nm * 2);
   } else {
@@ -246,6 +279,30 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
     rc = marg_const2_launch(wx, n, std::pow(a.hx, 2 * a.k), cx, wy, m, std::pow(a.hy, 2 * a.k), cy, a.k,
                             dbl ? GW_F64 : GW_F32, part, st, a.tracer);
     if (rc != GW_OK) return rc;
+  }
+
+  if (tc) {
+    // C1 = D_Y T^T (m x np), then G = c_x + c_y - 2 D_X C1^T in the second
+    // product's epilogue.  T is copied with zero-padded rows (pitch mp) in the
+    // input type; the padding columns of C1 come out zero.
+    const bool tf32 = a.prec == GW_DENSE_TC_TF32;
+    const void* Tk = Tin;
+    {
+      TraceScope ts(a.tracer, "dense_pad_T", st);
+      if (tf32 && mp == m && (reinterpret_cast<uintptr_t>(a.T) & 15) == 0)
+        Tk = a.T;
+      else if (tf32)
+        pad_rows<float><<<8 * 152, 256, 0, st>>>((const float*)a.T, n, m, (float*)Tin, mp);
+      else
+        pad_rows<__nv_bfloat16><<<8 * 152, 256, 0, st>>>((const float*)a.T, n, m, (__nv_bfloat16*)Tin, mp);
+    }
+    rc = tc_gemm_abt_launch(tf32, S->Y.D, mp, Tk, mp, m, n, mp, tf32 ? 1 : 0, Y, np, m, np, nullptr, nullptr, 0.f,
+                            a.status, a.num_sms, st, a.tracer);
+    if (rc != GW_OK) return rc;
+    rc = tc_gemm_abt_launch(tf32, S->X.D, np, Y, np, n, m, np, 2, a.G, m, n, m, (const float*)cx, (const float*)cy,
+                            2.f, a.status, a.num_sms, st, a.tracer);
+    if (rc != GW_OK) return rc;
+    return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
   }
 
   // Row-major n x m arrays are column-major m x n.  Y^T = T^T D_X and

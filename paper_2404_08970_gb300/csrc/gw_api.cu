@@ -101,6 +101,20 @@ struct gw_ctx {
   size_t bws_bytes = 0;
   cudaGraphExec_t batch_exec = nullptr;
   std::string batch_key;
+  // gw_grad_host: two device slots used in turn, so that one call's copy-in
+  // overlaps the previous call's gradient and copy-out; a stream each for
+  // copy-in, gradient and copy-out.
+  struct HostSlot {
+    void* dT = nullptr;
+    void* dG = nullptr;
+    void* dm = nullptr;  // marginals u (n doubles) then v (m doubles)
+    size_t tg_bytes = 0, marg_bytes = 0;
+    cudaEvent_t in = nullptr, comp = nullptr, out = nullptr;
+    bool used = false;
+  };
+  HostSlot hslot[2];
+  int hnext = 0;
+  cudaStream_t h_in = nullptr, h_comp = nullptr, h_out = nullptr;
   gw::Tracer* tr() { return tracer; }
 };
 
@@ -268,6 +282,14 @@ void gw_ctx_destroy(gw_ctx* c) {
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->bws) cudaFree(c->bws);
   if (c->cap) cudaStreamDestroy(c->cap);
+  for (auto& h : c->hslot) {
+    for (void* q : {h.dT, h.dG, h.dm})
+      if (q) cudaFree(q);
+    for (cudaEvent_t q : {h.in, h.comp, h.out})
+      if (q) cudaEventDestroy(q);
+  }
+  for (cudaStream_t q : {c->h_in, c->h_comp, c->h_out})
+    if (q) cudaStreamDestroy(q);
   delete c->tracer;
   delete c;
 }
@@ -327,22 +349,34 @@ gw_status gw_ctx_check(gw_ctx* c, void* stream) {
   return GW_OK;
 }
 
-gw_status gw_grad(gw_ctx* c, const gw_problem* p, const double* d_u, const double* d_v, const void* d_T, void* d_G,
-                  int marginals, void* stream) {
-  if (!c) return GW_ERR_INVALID;
-  std::lock_guard<std::mutex> lk(c->mu);
+}  // extern "C"
+
+namespace {
+
+// Argument checks shared by gw_grad and gw_grad_host (the pointers may be
+// device or host pointers; only their presence is checked here).
+gw_status check_grad_args(gw_ctx* c, const gw_problem* p, const void* u, const void* v, const void* T, void* G,
+                          int marginals) {
   gw_status s = check_grid(c, p);
   if (s != GW_OK) return s;
   if (marginals != GW_MARG_TARGET && marginals != GW_MARG_EXACT)
     return fail(c, GW_ERR_INVALID, "marginals must be GW_MARG_TARGET or GW_MARG_EXACT");
-  if (!d_T || !d_G) return fail(c, GW_ERR_INVALID, "d_T and d_G must not be NULL");
-  if (marginals == GW_MARG_TARGET && (!d_u || !d_v))
-    return fail(c, GW_ERR_INVALID, "target marginals requested but d_u or d_v is NULL");
+  if (!T || !G) return fail(c, GW_ERR_INVALID, "T and G must not be NULL");
+  if (marginals == GW_MARG_TARGET && (!u || !v))
+    return fail(c, GW_ERR_INVALID, "target marginals requested but u or v is NULL");
   const size_t esz = p->dtype == GW_F32 ? 4 : 8;
   const size_t nm = points_x(p) * points_y(p);
-  const char* t0 = (const char*)d_T;
-  const char* g0 = (const char*)d_G;
-  if (t0 < g0 + nm * esz && g0 < t0 + nm * esz) return fail(c, GW_ERR_INVALID, "d_T and d_G overlap");
+  const char* t0 = (const char*)T;
+  const char* g0 = (const char*)G;
+  if (t0 < g0 + nm * esz && g0 < t0 + nm * esz) return fail(c, GW_ERR_INVALID, "T and G overlap");
+  return GW_OK;
+}
+
+// The gradient on device buffers, enqueued on `stream`; the caller holds
+// c->mu and has checked the arguments.
+gw_status grad_device(gw_ctx* c, const gw_problem* p, const double* d_u, const double* d_v, const void* d_T,
+                      void* d_G, int marginals, void* stream) {
+  gw_status s;
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
 
   if (p->dim == 2) {
@@ -420,13 +454,100 @@ gw_status gw_grad(gw_ctx* c, const gw_problem* p, const double* d_u, const doubl
       "gw_grad");
 }
 
+// Grows one host-call slot to hold the problem's T and G (device) and its
+// marginals; synchronises the device when it has to reallocate.
+gw_status ensure_host_slot(gw_ctx* c, gw_ctx::HostSlot& h, size_t tg_bytes, size_t marg_bytes) {
+  if (tg_bytes <= h.tg_bytes && marg_bytes <= h.marg_bytes) return GW_OK;
+  cudaDeviceSynchronize();
+  for (void** q : {&h.dT, &h.dG, &h.dm}) {
+    if (*q) cudaFree(*q);
+    *q = nullptr;
+  }
+  h.tg_bytes = h.marg_bytes = 0;
+  cudaError_t e = cudaMalloc(&h.dT, tg_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h.dG, tg_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h.dm, marg_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, GW_ERR_OOM, "host-call staging of %zu bytes failed: %s", 2 * tg_bytes + marg_bytes,
+                cudaGetErrorString(e));
+  }
+  h.tg_bytes = tg_bytes;
+  h.marg_bytes = marg_bytes;
+  return GW_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+gw_status gw_grad(gw_ctx* c, const gw_problem* p, const double* d_u, const double* d_v, const void* d_T, void* d_G,
+                  int marginals, void* stream) {
+  if (!c) return GW_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  gw_status s = check_grad_args(c, p, d_u, d_v, d_T, d_G, marginals);
+  if (s != GW_OK) return s;
+  return grad_device(c, p, d_u, d_v, d_T, d_G, marginals, stream);
+}
+
+gw_status gw_grad_host(gw_ctx* c, const gw_problem* p, const double* h_u, const double* h_v, const void* h_T,
+                       void* h_G, int marginals, void* stream) {
+  if (!c) return GW_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  gw_status s = check_grad_args(c, p, h_u, h_v, h_T, h_G, marginals);
+  if (s != GW_OK) return s;
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
+  if (!c->h_in) {
+    for (cudaStream_t* q : {&c->h_in, &c->h_comp, &c->h_out})
+      if (cudaStreamCreateWithFlags(q, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "host-call streams");
+    for (auto& h : c->hslot)
+      for (cudaEvent_t* q : {&h.in, &h.comp, &h.out})
+        if (cudaEventCreateWithFlags(q, cudaEventDisableTiming) != cudaSuccess)
+          return cuda_fail(c, cudaGetLastError(), "host-call events");
+  }
+  const size_t esz = p->dtype == GW_F32 ? 4 : 8;
+  const size_t n = points_x(p), m = points_y(p);
+  const size_t tg = n * m * esz;
+  gw_ctx::HostSlot& h = c->hslot[c->hnext];
+  s = ensure_host_slot(c, h, tg, (n + m) * sizeof(double));
+  if (s != GW_OK) return s;
+  c->hnext ^= 1;
+  const bool target = marginals == GW_MARG_TARGET;
+  double* du = (double*)h.dm;
+  double* dv = du + n;
+  cudaError_t e = cudaSuccess;
+  // Copy in, once the slot's previous gradient has read its T.
+  if (h.used) e = cudaStreamWaitEvent(c->h_in, h.comp, 0);
+  if (e == cudaSuccess && target) e = cudaMemcpyAsync(du, h_u, n * sizeof(double), cudaMemcpyHostToDevice, c->h_in);
+  if (e == cudaSuccess && target) e = cudaMemcpyAsync(dv, h_v, m * sizeof(double), cudaMemcpyHostToDevice, c->h_in);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.dT, h_T, tg, cudaMemcpyHostToDevice, c->h_in);
+  if (e == cudaSuccess) e = cudaEventRecord(h.in, c->h_in);
+  // The gradient, once T is in and the slot's previous G has been copied out.
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->h_comp, h.in, 0);
+  if (e == cudaSuccess && h.used) e = cudaStreamWaitEvent(c->h_comp, h.out, 0);
+  if (e != cudaSuccess) return cuda_fail(c, e, "gw_grad_host copy-in");
+  s = grad_device(c, p, target ? du : nullptr, target ? dv : nullptr, h.dT, h.dG, marginals, c->h_comp);
+  if (s != GW_OK) return s;
+  e = cudaEventRecord(h.comp, c->h_comp);
+  // Copy out, then order the caller's stream after it.
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->h_out, h.comp, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h_G, h.dG, tg, cudaMemcpyDeviceToHost, c->h_out);
+  if (e == cudaSuccess) e = cudaEventRecord(h.out, c->h_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent((cudaStream_t)stream, h.out, 0);
+  if (e != cudaSuccess) return cuda_fail(c, e, "gw_grad_host copy-out");
+  h.used = true;
+  c->err.clear();
+  return GW_OK;
+}
+
 gw_status gw_grad_dense(gw_ctx* c, const gw_problem* p, const double* d_u, const double* d_v, const void* d_T,
                         void* d_G, int marginals, int precision, void* stream) {
   if (!c) return GW_ERR_INVALID;
   std::lock_guard<std::mutex> lk(c->mu);
   gw_status s = check_grid(c, p);
   if (s != GW_OK) return s;
-  if (precision < GW_DENSE_FP32 || precision > GW_DENSE_FP64)
+  if (precision < GW_DENSE_FP32 || precision > GW_DENSE_TC_BF16)
     return fail(c, GW_ERR_INVALID, "gw_grad_dense: unknown precision %d", precision);
   if ((precision == GW_DENSE_FP64) != (p->dtype == GW_F64))
     return fail(c, GW_ERR_INVALID, "gw_grad_dense: dtype must be GW_F64 exactly for GW_DENSE_FP64");
@@ -460,12 +581,14 @@ gw_status gw_grad_dense(gw_ctx* c, const gw_problem* p, const double* d_u, const
   a.G = d_G;
   a.stream = (cudaStream_t)stream;
   a.tracer = c->tr();
+  a.status = c->status;
+  a.num_sms = c->num_sms;
   s = ensure_ws(c, gw::dense_workspace_bytes(a.n, a.m, precision));
   if (s != GW_OK) return s;
   int rc = gw::dense_grad_launch(c->dense, a, c->ws, c->ws_bytes);
   if (rc != GW_OK) {
     cudaError_t e = cudaGetLastError();
-    return fail(c, (gw_status)rc, "gw_grad_dense failed: %s", cudaGetErrorString(e));
+    return fail(c, (gw_status)rc, "gw_grad_dense failed: %s (%s)", cudaGetErrorString(e), gw::last_failure());
   }
   c->err.clear();
   return GW_OK;

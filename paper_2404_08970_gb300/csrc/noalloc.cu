@@ -10,6 +10,7 @@
 // passed by the caller.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 
 #include "gw_internal.h"
@@ -21,16 +22,22 @@ namespace {
 // 4096 x 4096 (k <= 2); larger problems are rejected.
 constexpr size_t kNoallocScratchBytes = (size_t)32 << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+// Status word of the kernels' bounded waits, shared by all calls like the
+// scratch.  Cleared on the caller's stream before every launch; once a wait
+// has run out, the other waits of the same launch see the bit and give up at
+// once instead of each running to its own limit.
+static __device__ __align__(256) unsigned g_noalloc_status;
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
+unsigned* g_status_ptr[kMaxDevices] = {};
 int g_num_sms[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device.  The array's
-// name in host code is only a host-side stand-in, so the address is looked
-// up once per device, with that device current.
-int scratch_for_current_device(void** ptr, int* num_sms) {
+// Device addresses of the scratch array and the status word on the current
+// device.  Their names in host code are only host-side stand-ins, so the
+// addresses are looked up once per device, with that device current.
+int scratch_for_current_device(void** ptr, unsigned** status, int* num_sms) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
@@ -39,7 +46,9 @@ int scratch_for_current_device(void** ptr, int* num_sms) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+    void* q = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p ||
+        cudaGetSymbolAddress(&q, g_noalloc_status) != cudaSuccess || !q) {
       cudaGetLastError();
       return GW_ERR_CUDA;
     }
@@ -49,9 +58,11 @@ int scratch_for_current_device(void** ptr, int* num_sms) {
       return GW_ERR_CUDA;
     }
     g_scratch_ptr[dev] = p;
+    g_status_ptr[dev] = (unsigned*)q;
     g_num_sms[dev] = sms;
   }
   *ptr = g_scratch_ptr[dev];
+  *status = g_status_ptr[dev];
   *num_sms = g_num_sms[dev];
   return GW_OK;
 }
@@ -61,7 +72,7 @@ int scratch_for_current_device(void** ptr, int* num_sms) {
 extern "C" gw_status gw_grad_noalloc(const gw_problem* p, const double* d_u, const double* d_v, const void* d_T,
                                      void* d_G, int marginals, void* stream) {
   if (!p || p->dim != 1 || p->nx < 1 || p->ny < 1 || p->k < 1 || p->k > 3 || p->ny > 16384 ||
-      !(p->hx > 0.0) || !(p->hy > 0.0) || (p->dtype != GW_F32 && p->dtype != GW_F64))
+      !(std::isfinite(p->hx) && p->hx > 0.0) || !(std::isfinite(p->hy) && p->hy > 0.0) || (p->dtype != GW_F32 && p->dtype != GW_F64))
     return GW_ERR_INVALID;
   if (marginals != GW_MARG_TARGET && marginals != GW_MARG_EXACT) return GW_ERR_INVALID;
   if (!d_T || !d_G || (marginals == GW_MARG_TARGET && (!d_u || !d_v))) return GW_ERR_INVALID;
@@ -71,8 +82,9 @@ extern "C" gw_status gw_grad_noalloc(const gw_problem* p, const double* d_u, con
   const char* g0 = (const char*)d_G;
   if (t0 < g0 + nm * esz && g0 < t0 + nm * esz) return GW_ERR_INVALID;
   void* scratch = nullptr;
+  unsigned* status = nullptr;
   int num_sms = 0;
-  int rc = scratch_for_current_device(&scratch, &num_sms);
+  int rc = scratch_for_current_device(&scratch, &status, &num_sms);
   if (rc != GW_OK) return (gw_status)rc;
   // Too large for the fixed scratch: reject rather than allocate.
   if (gw::grad1d_workspace_bytes(p->nx, p->ny, p->k, p->dtype, num_sms) > kNoallocScratchBytes)
@@ -91,10 +103,14 @@ extern "C" gw_status gw_grad_noalloc(const gw_problem* p, const double* d_u, con
   a.exact = marginals == GW_MARG_EXACT;
   a.out_scale = 1.0;
   a.stream = (cudaStream_t)stream;
-  a.status = nullptr;  // no status word: bounded waits still end, but are not reported here
+  a.status = status;
   a.num_sms = num_sms;
   a.tracer = nullptr;
   a.force_generic = 0;
+  if (cudaMemsetAsync(status, 0, sizeof(unsigned), a.stream) != cudaSuccess) {
+    cudaGetLastError();
+    return GW_ERR_CUDA;
+  }
   rc = gw::grad1d_launch(a, scratch, kNoallocScratchBytes);
   if (rc != GW_OK) {
     cudaGetLastError();

@@ -2,14 +2,19 @@
 // admitted under a device-memory budget and run concurrently.
 //
 // gw_submit copies a request's inputs into host memory owned by the server
-// and returns a ticket at once.  Worker threads (one per slot) take requests
-// in arrival order as soon as the budget has room for them (continuous
+// and returns a ticket at once.  Worker threads (one per slot) take the
+// oldest queued request that fits in the free part of the budget (continuous
 // admission: a finished request frees its memory and its slot for the next
-// one, whatever the shapes), each on its own CUDA stream: device buffers
-// from the stream-ordered allocator, host-to-device copies, the solve
-// (the same launch sequence as gw_solve), device-to-host copies of the
-// statistics and, if requested, the plan.  gw_poll reports completion,
-// statistics and the latency from submission to completion.
+// one, whatever the shapes).  A request too large for the free budget does
+// not block smaller ones behind it, but only for a bounded number of
+// bypasses: once the oldest request has been passed over kMaxBypass times,
+// nothing else is admitted until it fits, so large requests cannot starve.
+// Each worker runs on its own CUDA stream: device buffers from the
+// stream-ordered allocator, inputs staged in the worker's page-locked buffer
+// and copied asynchronously, the solve (the same launch sequence as
+// gw_solve), device-to-host copies of the statistics and, if requested, the
+// plan.  gw_poll reports completion, statistics and the latency from
+// submission to completion.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -30,8 +35,13 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// How often the oldest queued request may be passed over by younger ones
+// that fit the free budget before admission waits for it.
+constexpr int kMaxBypass = 32;
+
 struct Request {
   uint64_t ticket = 0;
+  int bypassed = 0;     // younger requests admitted while this one waited
   gw_problem prob{};
   std::vector<double> u, v, phi, psi;
   void* h_T = nullptr;  // caller's plan buffer, or null
@@ -95,8 +105,32 @@ gw::SolveArgs args_for(const gw_server* s, const gw_problem& p) {
   return a;
 }
 
+// Page-locked staging buffer of one worker, grown on demand, so that the
+// input copies are truly asynchronous.
+struct Staging {
+  double* p = nullptr;
+  size_t cap = 0;  // doubles
+  ~Staging() {
+    if (p) cudaFreeHost(p);
+  }
+  double* get(size_t count) {
+    if (count <= cap) return p;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    if (cudaMallocHost((void**)&p, count * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return nullptr;
+    }
+    cap = count;
+    return p;
+  }
+};
+
 // Runs one request on `st`; returns its status and, on failure, a message.
-gw_status run_request(gw_server* s, Request& r, cudaStream_t st, unsigned* d_status, std::string* msg) {
+gw_status run_request(gw_server* s, Request& r, cudaStream_t st, unsigned* d_status, Staging* stage,
+                      std::string* msg) {
   gw::SolveArgs a = args_for(s, r.prob);
   const size_t n = a.n, m = a.m;
   const size_t rb = r.prob.dtype == GW_F32 ? 4 : 8;
@@ -126,11 +160,30 @@ gw_status run_request(gw_server* s, Request& r, cudaStream_t st, unsigned* d_sta
   void* dT = take(n * m * rb);
   double* dstats = (double*)take(8 * 8);
   void* ws = take(ws_bytes);
-  cudaMemcpyAsync(du, r.u.data(), n * 8, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(dv, r.v.data(), m * 8, cudaMemcpyHostToDevice, st);
-  if (a.feat_dim > 0) {
-    cudaMemcpyAsync(dphi, r.phi.data(), n * a.feat_dim * 8, cudaMemcpyHostToDevice, st);
-    cudaMemcpyAsync(dpsi, r.psi.data(), m * a.feat_dim * 8, cudaMemcpyHostToDevice, st);
+  // Inputs go through the page-locked staging buffer (the previous request's
+  // copies out of it finished with that request's stream synchronisation).
+  const size_t nin = n + m + (a.feat_dim > 0 ? (n + m) * (size_t)a.feat_dim : 0);
+  double* h = stage->get(nin);
+  if (h) {
+    memcpy(h, r.u.data(), n * 8);
+    memcpy(h + n, r.v.data(), m * 8);
+    if (a.feat_dim > 0) {
+      memcpy(h + n + m, r.phi.data(), n * a.feat_dim * 8);
+      memcpy(h + n + m + n * a.feat_dim, r.psi.data(), m * a.feat_dim * 8);
+    }
+    cudaMemcpyAsync(du, h, n * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dv, h + n, m * 8, cudaMemcpyHostToDevice, st);
+    if (a.feat_dim > 0) {
+      cudaMemcpyAsync(dphi, h + n + m, n * a.feat_dim * 8, cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(dpsi, h + n + m + n * a.feat_dim, m * a.feat_dim * 8, cudaMemcpyHostToDevice, st);
+    }
+  } else {  // no page-locked memory to be had: copy from the request itself
+    cudaMemcpyAsync(du, r.u.data(), n * 8, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(dv, r.v.data(), m * 8, cudaMemcpyHostToDevice, st);
+    if (a.feat_dim > 0) {
+      cudaMemcpyAsync(dphi, r.phi.data(), n * a.feat_dim * 8, cudaMemcpyHostToDevice, st);
+      cudaMemcpyAsync(dpsi, r.psi.data(), m * a.feat_dim * 8, cudaMemcpyHostToDevice, st);
+    }
   }
   cudaMemsetAsync(d_status, 0, sizeof(unsigned), st);
   a.u = du;
@@ -166,25 +219,44 @@ gw_status run_request(gw_server* s, Request& r, cudaStream_t st, unsigned* d_sta
   return GW_OK;
 }
 
+// The request to admit next: the oldest one that fits in the free budget,
+// except that once the oldest has been bypassed kMaxBypass times only it may
+// go.  queue.end() if none can go now.  Called with s->mu held.
+std::deque<std::shared_ptr<Request>>::iterator admissible(gw_server* s) {
+  const size_t free_bytes = s->budget - s->used;
+  if (s->queue.empty()) return s->queue.end();
+  if (s->queue.front()->need <= free_bytes) return s->queue.begin();
+  if (s->queue.front()->bypassed >= kMaxBypass) return s->queue.end();
+  for (auto it = s->queue.begin() + 1; it != s->queue.end(); ++it)
+    if ((*it)->need <= free_bytes) return it;
+  return s->queue.end();
+}
+
 void worker_loop(gw_server* s) {
   cudaSetDevice(s->device);
   cudaStream_t st = nullptr;
   unsigned* d_status = nullptr;
   cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   cudaMalloc(&d_status, sizeof(unsigned));
+  Staging stage;
   for (;;) {
     std::shared_ptr<Request> r;
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      // Arrival order: the head request runs as soon as the budget has room.
-      s->cv_work.wait(lk, [&] { return s->stop || (!s->queue.empty() && s->used + s->queue.front()->need <= s->budget); });
+      auto pick = s->queue.end();
+      s->cv_work.wait(lk, [&] {
+        if (s->stop) return true;
+        pick = admissible(s);
+        return pick != s->queue.end();
+      });
       if (s->stop) break;
-      r = s->queue.front();
-      s->queue.pop_front();
+      r = *pick;
+      if (pick != s->queue.begin()) s->queue.front()->bypassed += 1;
+      s->queue.erase(pick);
       s->used += r->need;
     }
     std::string msg;
-    const gw_status rc = run_request(s, *r, st, d_status, &msg);
+    const gw_status rc = run_request(s, *r, st, d_status, &stage, &msg);
     {
       std::lock_guard<std::mutex> lk(s->mu);
       if (rc != GW_OK) s->last_error = "ticket " + std::to_string(r->ticket) + ": " + msg;

@@ -1,7 +1,7 @@
 """Batched solves (gw_solve_batch): each problem's result agrees with the
 single-problem solve on the same inputs (the batch uses longer row bands, so
 partial sums are grouped differently: double agrees to 1e-11, float to the
-tolerances of the solve parity tests), and the double-precision problems
+1e-5 value tolerance of the solve parity tests), and the double-precision problems
 match the FP64 oracle."""
 import numpy as np
 import pytest
@@ -77,7 +77,7 @@ def test_batch_equals_single_solves(dtype):
             assert abs(E - E1) <= 1e-11 * abs(E1), i
         else:
             assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b), i
-            assert abs(E - E1) <= 3e-5 * abs(E1), i
+            assert abs(E - E1) <= 1e-5 * abs(E1), i
     # A second launch of the cached graph gives the same results.
     T0 = [t.clone() for t in T]
     for t in T:

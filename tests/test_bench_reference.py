@@ -25,3 +25,26 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["n"] == 256 and "profiling only" in d["config"]["l2"]
+
+
+def test_reference_arm_step_time_is_measured():
+    """ms_per_step is the measured time of one step (a bounded row sample),
+    so steps x ms_per_step is time the run actually spent."""
+    import time
+    t0 = time.time()
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "512",
+                        "--steps", "3", "--warmup", "1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    wall = time.time() - t0
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][0])
+    assert d["steps"] * d["ms_per_step"] / 1e3 <= wall
+    assert "rows" in d["step"]
+
+
+def test_single_thread_oracle_child():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2404_08970_gb300 import inputs as I
+    w = I.workload_1d_grad(256, 1, "uniform", seed=0)
+    t = bench.single_thread_oracle(w, 32)
+    assert t is not None and t > 0

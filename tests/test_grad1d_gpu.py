@@ -122,3 +122,25 @@ def test_grad1d_generic_row_kernel():
         Gs = U.oracle_grad_1d(Tc.astype(np.float64), u, v, k, 1.0 / n, 1.0 / m, "target")
         assert U.relerr(dG.double().cpu().numpy(), Gs) <= TOL["f32"], (n, m, k)
     c.close()
+
+
+@pytest.mark.parametrize("n,m,k", [(24, 8192, 1), (8192, 24, 2)])
+def test_grad1d_peaked_late_iterate_plan(n, m, k):
+    """The plan the solver actually hands to the gradient: a late mirror-descent
+    iterate of the FP64 oracle at eps = 5e-3 (20 x 100), whose entries span
+    many orders of magnitude (nearly empty rows and columns included), rounded
+    to float32.  Target and exact marginals, 1e-6 relative."""
+    from oracle import gw_oracle as O
+    rng = np.random.default_rng(n + 3 * m + k)
+    u, v = I.dirichlet(n, 1.0, rng), I.dirichlet(m, 1.0, rng)
+    hx, hy = 1.0 / n, 1.0 / m
+    DX, DY = O.grid_dist_1d(n, hx, k), O.grid_dist_1d(m, hy, k)
+    T, _, _ = O.mirror_descent(DX, DY, u, v, 5e-3, 20, 100)
+    Tc = T.astype(np.float32)
+    pos = Tc[Tc > 0].astype(np.float64)
+    assert pos.max() / pos.min() > 1e6  # peaked: many orders of magnitude
+    for marg in ("target", "exact"):
+        G = U.gpu_grad_1d(Tc, u, v, k, hx, hy, "f32", marg)
+        Gs = U.oracle_grad_1d(Tc.astype(np.float64), u, v, k, hx, hy, marg)
+        err = U.relerr(G, Gs)
+        assert err <= TOL["f32"], f"{marg} rel err {err:.3e}"

@@ -107,3 +107,29 @@ def test_server_shutdown_with_queued_requests():
     for r in reqs:
         srv.submit(_prob(L, r, L.GW_F32), r["u"], r["v"], r.get("phi"), r.get("psi"))
     srv.close()  # running request finishes, the queued ones end with GW_ERR_SHUTDOWN
+
+
+def test_server_small_requests_pass_a_waiting_large_one():
+    """Two large requests that cannot run together under the budget, then
+    small ones: the small ones run beside the first large request instead of
+    queueing behind the second (no head-of-line blocking), and the second
+    large request still finishes."""
+    from paper_2404_08970_gb300 import _lib as L
+    rng = np.random.default_rng(8)
+
+    def req(n, n_outer, n_inner):
+        return dict(dim=1, nx=n, ny=n, hx=1.0 / n, hy=1.0 / n, k=1, eps=5e-2, n_outer=n_outer, n_inner=n_inner,
+                    theta=1.0, u=I.dirichlet(n, 1.0, rng), v=I.dirichlet(n, 1.0, rng))
+
+    big = [req(4096, 10, 50), req(4096, 10, 50)]   # about 140 MB each while running
+    small = [req(200, 3, 20) for _ in range(4)]      # well under 1 MB each
+    srv = L.Server(0, hbm_budget_bytes=200 << 20, max_slots=4)
+    try:
+        tb = [srv.submit(_prob(L, r, L.GW_F32), r["u"], r["v"]) for r in big]
+        ts = [srv.submit(_prob(L, r, L.GW_F32), r["u"], r["v"]) for r in small]
+        res = _wait(srv, tb + ts)
+        assert all(v[0] == L.GW_OK for v in res.values()), srv.last_error()
+        lat_b2 = res[tb[1]][2]
+        assert max(res[t][2] for t in ts) < lat_b2, ([res[t][2] for t in ts], lat_b2)
+    finally:
+        srv.close()

@@ -3,13 +3,11 @@ FP64 oracle's mirror descent (same schedule: T^0 = u v^T, f = g = 0 at every
 outer step, f then g, fixed iteration counts).
 
 Tolerances: double arithmetic reproduces the oracle to 1e-9 (plan) and 1e-10
-(value).  Float arithmetic keeps the GW value within 1e-5 relative on the small
-benchmark workload (n = m = 200, eps = 1e-2).  On other shapes the bound is
-3e-5: the float gradient is accurate to ~3e-7 of max|G| and the mirror
-descent amplifies a gradient perturbation by up to ~1/eps in the value (the
-oracle moves by up to 2e-5 under a 1e-6 gradient perturbation at
-eps = 5e-2, 100 x 256), so 1e-5 is not a bound a float gradient can meet
-everywhere."""
+(value).  Float arithmetic keeps the GW value within 1e-5 relative (the bound
+the method is held to in FP32) on every shape here, including the rows of
+8192 and more columns that use the widest Sinkhorn row configurations, at the
+full-size schedule eps = 1e-2, 20 x 100; column marginals stay within 1e-5
+after the g update."""
 import numpy as np
 import pytest
 
@@ -95,7 +93,7 @@ def test_solve_shapes(shape, k, dtype):
         assert U.relerr(T, Ts) < 1e-9
         assert abs(st[1] - ss["E"]) <= 1e-10 * max(abs(ss["E"]), 1e-300) + 1e-300
     else:
-        assert abs(st[1] - ss["E"]) <= 3e-5 * abs(ss["E"]) + 1e-12
+        assert abs(st[1] - ss["E"]) <= 1e-5 * abs(ss["E"]) + 1e-12
         assert fro(T, Ts) < 1e-3
 
 
@@ -109,11 +107,28 @@ def test_solve_fused_gw(dtype):
     phi, psi = I.features(n, 16, rng) * 0.1, I.features(m, 16, rng) * 0.1
     T, f, g, st = gpu_solve(w, dtype, theta=0.5, phi=phi, psi=psi)
     Ts, fs, gs, ss = oracle_solve(w, theta=0.5, phi=phi, psi=psi)
-    tol = 1e-9 if dtype == "f64" else 3e-5
+    tol = 1e-9 if dtype == "f64" else 1e-5
     assert abs(st[0] - ss["obj"]) <= tol * abs(ss["obj"])
     assert abs(st[2] - ss["lin"]) <= tol * abs(ss["lin"])
     if dtype == "f64":
         assert U.relerr(T, Ts) < 1e-9
+
+
+@pytest.mark.parametrize("n,m,k", [(32, 8192, 1), (24, 8192, 2), (8192, 32, 1), (8192, 24, 2), (16, 9216, 1),
+                                   (16, 12000, 1)])
+def test_solve_full_size_row_configurations_fp32(n, m, k):
+    """FP32 solve at the full-size schedule (eps = 1e-2, 20 x 100) on shapes
+    whose rows (8192 to 12000 columns) or columns (8192 rows) are as long
+    as the n = m = 8192 workload's, so that the widest Sinkhorn row
+    configurations and the longest column passes run."""
+    rng = np.random.default_rng(n + m + k)
+    w = dict(nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=k, eps=1e-2, n_outer=20, n_inner=100,
+             u=I.dirichlet(n, 1.0, rng), v=I.dirichlet(m, 1.0, rng))
+    T, f, g, st = gpu_solve(w, "f32")
+    Ts, fs, gs, ss = oracle_solve(w)
+    assert abs(st[1] - ss["E"]) <= 1e-5 * abs(ss["E"]), (st[1], ss["E"])
+    assert st[5] < 1e-5
+    assert fro(T, Ts) < 1e-4
 
 
 def test_solve_reflection_and_single_point():

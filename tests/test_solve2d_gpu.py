@@ -4,8 +4,7 @@ schedule as the 1D solve: T^0 = u v^T, f = g = 0 at every outer step, f then
 g, fixed counts).  The cost inside each step is the 2D separable gradient.
 
 Tolerances as for the 1D solve: double 1e-9 (plan) and 1e-10 (value); float
-3e-5 on the value (the float gradient's ~1e-7 relative error is amplified by
-up to ~1/eps through the mirror descent)."""
+1e-5 on the value."""
 import numpy as np
 import pytest
 
@@ -76,7 +75,7 @@ def test_solve2d_fp32_image_workload(cost):
     w = small_2d(16, 20, cost, eps=5e-3, n_outer=20, n_inner=100, seed=5)
     T, f, g, st = gpu_solve_2d(w, "f32")
     Ts, fs, gs, ss = oracle_solve_2d(w)
-    assert abs(st[1] - ss["E"]) <= 3e-5 * abs(ss["E"]), (st[1], ss["E"])
+    assert abs(st[1] - ss["E"]) <= 1e-5 * abs(ss["E"]), (st[1], ss["E"])
     assert st[5] < 1e-5
 
 
@@ -88,7 +87,7 @@ def test_solve2d_fused(dtype):
     phi, psi = I.features(64, 16, rng) * 0.1, I.features(100, 16, rng) * 0.1
     T, f, g, st = gpu_solve_2d(w, dtype, theta=0.5, phi=phi, psi=psi)
     Ts, fs, gs, ss = oracle_solve_2d(w, theta=0.5, phi=phi, psi=psi)
-    tol = 1e-9 if dtype == "f64" else 3e-5
+    tol = 1e-9 if dtype == "f64" else 1e-5
     assert abs(st[0] - ss["obj"]) <= tol * abs(ss["obj"])
     if dtype == "f64":
         assert U.relerr(T, Ts) < 1e-9

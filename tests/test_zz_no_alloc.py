@@ -29,11 +29,16 @@ def test_noalloc_matches_gw_grad_on_two_calls():
         prob = L.problem(dim=1, nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=k, dtype=L.GW_F32)
         mg = L.GW_MARG_TARGET if marg == "target" else L.GW_MARG_EXACT
         U.ctx().gw_grad(prob, du, dv, dT, G_ref, mg)
-        L.gw_grad_noalloc(prob, du, dv, dT, G_na, mg)
-        torch.cuda.synchronize()
-        a, b = G_na.double().cpu().numpy(), G_ref.double().cpu().numpy()
-        assert np.all(np.isfinite(a))
-        assert U.relerr(a, b) <= 1e-6
+        b = G_ref.double().cpu().numpy()
+        for _ in range(2):  # the second call reuses the scratch the first one left behind
+            G_na.fill_(float("nan"))
+            L.gw_grad_noalloc(prob, du, dv, dT, G_na, mg)
+            torch.cuda.synchronize()
+            a = G_na.double().cpu().numpy()
+            assert np.all(np.isfinite(a))
+            assert U.relerr(a, b) <= 1e-6
+            # The same kernels on the same inputs: the results are identical.
+            assert torch.equal(G_na, G_ref)
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch():
@@ -45,5 +50,17 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     G = torch.empty(1, device="cuda")
     with pytest.raises(L.GWError) as e:
         # Sizes are checked before any device work; the tiny buffers are never touched.
+        L.gw_grad_noalloc(prob, None, None, T, G, L.GW_MARG_EXACT)
+    assert e.value.status == L.GW_ERR_INVALID
+
+
+@pytest.mark.parametrize("hx", [float("inf"), float("nan"), 0.0, -1.0])
+def test_noalloc_rejects_bad_spacing(hx):
+    import torch
+    from paper_2404_08970_gb300 import _lib as L
+    prob = L.problem(dim=1, nx=8, ny=8, hx=hx, hy=0.125, k=1, dtype=L.GW_F32)
+    T = torch.empty(8, 8, device="cuda")
+    G = torch.empty(8, 8, device="cuda")
+    with pytest.raises(L.GWError) as e:
         L.gw_grad_noalloc(prob, None, None, T, G, L.GW_MARG_EXACT)
     assert e.value.status == L.GW_ERR_INVALID
