@@ -571,7 +571,8 @@ def run_ours(args):
 
     # Dense comparison (cuBLAS, materialised distance matrices) on the same T.
     dense = {}
-    for name, prec in (("bf16", L.GW_DENSE_BF16), ("tf32", L.GW_DENSE_TF32)):
+    for name, prec in (("bf16", L.GW_DENSE_BF16), ("tf32", L.GW_DENSE_TF32), ("tc_bf16", L.GW_DENSE_TC_BF16),
+                       ("tc_tf32", L.GW_DENSE_TC_TF32)):
         try:
             for _ in range(2):
                 ctx.gw_grad_dense(prob, du, dv, dT, dG, L.GW_MARG_TARGET, prec, stream)
@@ -621,7 +622,8 @@ def run_ours(args):
         step()
         barrier()
         gpu_rows["structured_f32"] = dG.index_select(0, sel).double().cpu().numpy()
-        for name, prec in (("bf16", L.GW_DENSE_BF16), ("tf32", L.GW_DENSE_TF32)):
+        for name, prec in (("bf16", L.GW_DENSE_BF16), ("tf32", L.GW_DENSE_TF32), ("tc_bf16", L.GW_DENSE_TC_BF16),
+                           ("tc_tf32", L.GW_DENSE_TC_TF32)):
             if "ms" not in dense.get(name, {}):
                 continue
             ctx.gw_grad_dense(prob, du, dv, dT, dG, L.GW_MARG_TARGET, prec, stream)

@@ -37,6 +37,8 @@ GW_DENSE_FP32 = 0
 GW_DENSE_TF32 = 1
 GW_DENSE_BF16 = 2
 GW_DENSE_FP64 = 3
+GW_DENSE_TC_TF32 = 4
+GW_DENSE_TC_BF16 = 5
 # gw_marginals
 GW_MARG_TARGET = 0
 GW_MARG_EXACT = 1

@@ -18,7 +18,7 @@ namespace gw {
 // of side x side points (i = a * side + b): Manhattan h (|a-a'| + |b-b'|)
 // (sq = 0) or squared Euclidean h^2 ((a-a')^2 + (b-b')^2) (sq = 1).
 template <typename Out>
-__global__ void build_dist(Out* __restrict__ D, int n, double hk, int k, int side, int sq, int pitch) {
+__global__ void build_dist(Out* __restrict__ D, int n, double hk, int k, int side, int sq, int pitch, int tf32) {
   const size_t N = (size_t)n * n;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
     const long long i = (long long)(idx / n), j = (long long)(idx % n);
@@ -31,7 +31,15 @@ __global__ void build_dist(Out* __restrict__ D, int n, double hk, int k, int sid
       v = 1.0;
       for (int e = 0; e < k; ++e) v *= d;
     }
-    D[(size_t)i * pitch + j] = (Out)(hk * v);
+    Out o = (Out)(hk * v);
+    if constexpr (sizeof(Out) == 4) {
+      if (tf32) {
+        uint32_t r;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"((float)(hk * v)));
+        o = (Out)__uint_as_float(r);
+      }
+    }
+    D[(size_t)i * pitch + j] = o;
   }
 }
 
@@ -49,14 +57,34 @@ __global__ void to_bf16_tail(const float* __restrict__ x, __nv_bfloat16* __restr
     y[i] = __float2bfloat16_rn(x[i]);
 }
 
-// Rows of a float matrix (n x m) copied to pitch mp >= m in type Out, the
-// padding zero.
+// Float rounded to the nearest TF32 value (10 mantissa bits), kept in a
+// float: the tensor cores then read it exactly instead of dropping the low
+// bits.
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+template <typename Out> __device__ __forceinline__ Out to_input(float x);
+template <> __device__ __forceinline__ float to_input<float>(float x) { return round_tf32(x); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_input<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+// Four floats -> four TF32-rounded floats per thread (16-byte accesses).
+__global__ void to_tf32(const float4* __restrict__ x, float4* __restrict__ y, size_t N4) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = x[i];
+    y[i] = make_float4(round_tf32(v.x), round_tf32(v.y), round_tf32(v.z), round_tf32(v.w));
+  }
+}
+
+// Rows of a float matrix (n x m) copied to pitch mp >= m in the tensor-core
+// input type Out (TF32 values in floats, or bfloat16), the padding zero.
 template <typename Out>
 __global__ void pad_rows(const float* __restrict__ T, int n, int m, Out* __restrict__ Tp, int mp) {
   const size_t N = (size_t)n * mp;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
     const size_t i = idx / mp, p = idx % mp;
-    Tp[idx] = (Out)(p < (size_t)m ? T[i * m + p] : 0.f);
+    Tp[idx] = to_input<Out>(p < (size_t)m ? T[i * m + p] : 0.f);
   }
 }
 
@@ -166,12 +194,13 @@ static int ensure_dist(DenseCache& c, int n, double h, int k, int side, int sq, 
   }
   const double hk = side > 0 ? (sq ? h * h : h) : std::pow(h, k);
   if (pitch != n) cudaMemsetAsync(c.D, 0, (size_t)pitch * pitch * esz, st);
+  const int tf = prec == GW_DENSE_TC_TF32;
   if (bf)
-    build_dist<__nv_bfloat16><<<1024, 256, 0, st>>>((__nv_bfloat16*)c.D, n, hk, k, side, sq, pitch);
+    build_dist<__nv_bfloat16><<<1024, 256, 0, st>>>((__nv_bfloat16*)c.D, n, hk, k, side, sq, pitch, 0);
   else if (prec == GW_DENSE_FP64)
-    build_dist<double><<<1024, 256, 0, st>>>((double*)c.D, n, hk, k, side, sq, pitch);
+    build_dist<double><<<1024, 256, 0, st>>>((double*)c.D, n, hk, k, side, sq, pitch, 0);
   else
-    build_dist<float><<<1024, 256, 0, st>>>((float*)c.D, n, hk, k, side, sq, pitch);
+    build_dist<float><<<1024, 256, 0, st>>>((float*)c.D, n, hk, k, side, sq, pitch, tf);
   c.pitch = pitch;
   c.n = n;
   c.h = h;
@@ -289,8 +318,11 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
     const void* Tk = Tin;
     {
       TraceScope ts(a.tracer, "dense_pad_T", st);
-      if (tf32 && mp == m && (reinterpret_cast<uintptr_t>(a.T) & 15) == 0)
-        Tk = a.T;
+      const bool vec = mp == m && nm % 4 == 0 && (reinterpret_cast<uintptr_t>(a.T) & 15) == 0;
+      if (vec && tf32)
+        to_tf32<<<8 * 152, 256, 0, st>>>((const float4*)a.T, (float4*)Tin, nm / 4);
+      else if (vec)
+        to_bf16<<<8 * 152, 256, 0, st>>>((const float4*)a.T, (__nv_bfloat162*)Tin, nm / 4);
       else if (tf32)
         pad_rows<float><<<8 * 152, 256, 0, st>>>((const float*)a.T, n, m, (float*)Tin, mp);
       else

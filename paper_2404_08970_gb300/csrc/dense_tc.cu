@@ -56,7 +56,7 @@ constexpr size_t tc_smem_bytes() {
 }
 
 struct TcEpilogue {
-  int mode;            // 0: store bf16, 1: store f32, 2: G = fma(-scale, z, cx[row] + cy[col]) as f32
+  int mode;            // 0: store bf16, 1: store f32 rounded to TF32, 2: G = fma(-scale, z, cx[row] + cy[col]) as f32
   void* out;
   long long ldo;       // elements between output rows
   int rows, cols;      // valid output extent
@@ -99,8 +99,13 @@ __device__ __forceinline__ void epi_store(const TcEpilogue& e, int row, int col0
       v[j] = fmaf(-e.scale, __uint_as_float(r[j]), ci + cyv);
     }
   } else {
+    // mode 1 feeds the next TF32 product: round to the nearest TF32 value.
 #pragma unroll
-    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+    for (int j = 0; j < 32; ++j) {
+      uint32_t t;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(__uint_as_float(r[j])));
+      v[j] = __uint_as_float(t);
+    }
   }
   if (col0 + 32 <= e.cols && (e.ldo & 3) == 0 && ((reinterpret_cast<uintptr_t>(e.out) & 15) == 0)) {
 #pragma unroll
@@ -186,6 +191,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_wait_bounded(&full[q], last, status);
       }
     }
+    __syncwarp();
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
@@ -225,6 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc::commit(drain);
       mbar_wait_bounded(drain, 0, status);
     }
+    __syncwarp();
   } else {
     // ---------------- Epilogue (warps 2..5) ----------------
     const int quarter = warp & 3;  // TMEM lane quarter this warp may read
@@ -232,7 +239,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++it) {
       const int a = it & 1;
       const uint32_t aph = (uint32_t)((it >> 1) & 1);
-      if (!mbar_wait_bounded(&acc_full[a], aph, status)) break;
+      // The whole warp leaves together: tcgen05.ld below is warp-collective.
+      const bool ok = mbar_wait_bounded(&acc_full[a], aph, status);
+      if (!__all_sync(0xffffffffu, ok)) break;
       tc::fence_after_sync();
       const int tm = t % tiles_m, tn = t / tiles_m;
       const int row = tm * kBM + quarter * 32 + lane;

@@ -155,7 +155,7 @@ struct DenseArgs {
 // C = A B^T on the tcgen05 tensor cores (dense_tc.cu).  A: M x K row-major
 // (pitch lda elements), B: N x K row-major (pitch ldb), BF16 (tf32 = false)
 // or FP32 read as TF32; pitches a multiple of 16 bytes, bases 16-byte
-// aligned.  mode 0 stores C as bf16, 1 as float, 2 stores
+// aligned.  mode 0 stores C as bf16, 1 as float rounded to TF32, 2 stores
 // fma(-scale, C, cx[row] + cy[col]) as float; out_rows x out_cols outputs
 // are written (row pitch ldo).
 int tc_gemm_abt_launch(bool tf32, const void* A, long long lda, const void* B, long long ldb, int M, int N, int K,
