@@ -17,8 +17,9 @@ direct, each function citing the part of the paper it follows:
 * log-domain Sinkhorn for the entropic OT subproblem (Sec. 2.1, eq. "GW
   sinkhorn"; the paper only cites Sinkhorn, the log-domain form with f then g
   updates and a fixed iteration count is this module's reading),
-* mirror descent with tau = eps (Remark after eq. "GW sinkhorn"), including
-  the fused-GW cost (Remark "FGW"),
+* mirror descent (eqs. "GW proximal gradient" and "GW sinkhorn") with the
+  proximal weight tau = eps of the Remark or any tau > 0, optionally with
+  warm-started Sinkhorn solves, including the fused-GW cost (Remark "FGW"),
 * the paper's O(N) recursion for y = L x (Sec. 3, eqs. "1d y" and "1d
   recursive relation"), kept here as an independently pinned statement of
   the method's core step.
@@ -193,26 +194,37 @@ def sinkhorn_scaling(K: np.ndarray, u: np.ndarray, v: np.ndarray,
 def mirror_descent(DX: np.ndarray, DY: np.ndarray, u: np.ndarray,
                    v: np.ndarray, eps: float, n_outer: int, n_inner: int,
                    theta: float = 1.0, CC: np.ndarray | None = None,
-                   T0: np.ndarray | None = None, grad_scale: float = 2.0):
-    """Entropic (F)GW by mirror descent with tau = eps (Sec. 2.1 and its
-    Remark on tau = eps): each outer step solves the entropic OT problem whose
-    cost is the gradient at the current plan,
-      Pi = grad_scale * G(T; u, v)                      (GW, theta = 1)
-      Pi = (1 - theta) CC + theta * grad_scale * G      (FGW, Remark "FGW")
-    and replaces T by that problem's plan.  grad_scale = 2 is the paper's
-    grad E = 2 G.  T starts at the product coupling u v^T.
+                   T0: np.ndarray | None = None, grad_scale: float = 2.0,
+                   tau: float | None = None, warm_start: bool = False):
+    """Entropic (F)GW by mirror descent (Sec. 2.1, eqs. "GW proximal
+    gradient" and "GW sinkhorn"): each outer step solves the entropic OT
+    problem
+      argmin <Pi, Gamma> + tau H(Gamma),  Pi = grad E(T) + (eps - tau) grad H(T),
+    with grad H(T) = ln T, and replaces T by its plan.  grad E is
+      grad_scale * G(T; u, v)                      (GW, theta = 1)
+      (1 - theta) CC + theta * grad_scale * G      (FGW, Remark "FGW")
+    with grad_scale = 2 the paper's grad E = 2 G.  tau = None means tau = eps
+    (the Remark's choice; the (eps - tau) term then vanishes).  T starts at
+    the product coupling u v^T.  Each Sinkhorn solve starts from f = g = 0,
+    or with warm_start from the previous step's potentials.
 
     Returns (T, f, g) after n_outer steps.
     """
+    tau = eps if tau is None else tau
     T = np.outer(u, v) if T0 is None else np.array(T0, dtype=np.float64)
     f = np.zeros(u.size)
     g = np.zeros(v.size)
-    for _ in range(n_outer):
+    for l in range(n_outer):
         Pi = grad_scale * grad(DX, DY, T, u, v)
         if theta != 1.0:
             Pi = (1.0 - theta) * CC + theta * Pi
-        f, g = sinkhorn_log(Pi, u, v, eps, n_inner)
-        T = plan(Pi, f, g, eps)
+        if tau != eps:
+            Pi = Pi + (eps - tau) * np.log(T)
+        if warm_start and l > 0:
+            f, g = sinkhorn_log(Pi, u, v, tau, n_inner, f0=f, g0=g)
+        else:
+            f, g = sinkhorn_log(Pi, u, v, tau, n_inner)
+        T = plan(Pi, f, g, tau)
     return T, f, g
 
 

@@ -512,3 +512,80 @@ def test_entropy_and_grad_rows_planted_mistakes():
         for name, Gr in wrong.items():
             if Gr is not None:
                 assert relerr(Gr, G[rows]) > 1e-3, name
+
+
+# ---------------------------------------------------------------------------
+# Mirror descent with tau != eps (eqs. "GW proximal gradient", "GW sinkhorn")
+# and warm-started Sinkhorn
+# ---------------------------------------------------------------------------
+
+def test_warm_sinkhorn_equals_cold_on_shifted_cost():
+    """Starting the log-domain iteration from (f0, g0) is the cold iteration on
+    the cost Pi - f0_i - g0_p: every iterate is shifted by (f0, g0) and every
+    plan is the same (exact up to rounding)."""
+    u, v, Pi = _small_problem(seed=11)
+    rng = np.random.default_rng(12)
+    f0, g0 = rng.normal(size=u.size) * 0.3, rng.normal(size=v.size) * 0.3
+    eps = 0.07
+    for it in (1, 3, 17):
+        fw, gw = O.sinkhorn_log(Pi, u, v, eps, it, f0=f0, g0=g0)
+        Ps = Pi - f0[:, None] - g0[None, :]
+        fc, gc = O.sinkhorn_log(Ps, u, v, eps, it)
+        assert relerr(O.plan(Pi, fw, gw, eps), O.plan(Ps, fc, gc, eps)) < 1e-12
+        assert relerr(fw - f0, fc) < 1e-11 and relerr(gw - g0, gc) < 1e-11
+
+
+def _md_problem(n=9, m=7, seed=51):
+    rng = np.random.default_rng(seed)
+    u, v = I.dirichlet(n, 1.0, rng), I.dirichlet(m, 1.0, rng)
+    return u, v, O.grid_dist_1d(n, 1.0 / n, 1), O.grid_dist_1d(m, 1.0 / m, 1)
+
+
+def test_tau_equal_eps_is_the_remark():
+    u, v, DX, DY = _md_problem()
+    T1, f1, g1 = O.mirror_descent(DX, DY, u, v, 0.05, 4, 30)
+    T2, f2, g2 = O.mirror_descent(DX, DY, u, v, 0.05, 4, 30, tau=0.05)
+    assert np.array_equal(T1, T2)
+
+
+def test_tau_first_step_is_entropic_ot_at_tau():
+    """From T0 = u v^T, ln T0 = ln u_i + ln v_p is separable, so with the
+    Sinkhorn solve converged the first step's plan is the entropic OT plan of
+    the cost grad E(T0) at regularisation tau, whatever eps is."""
+    u, v, DX, DY = _md_problem()
+    eps, tau = 0.08, 0.03
+    T1, _, _ = O.mirror_descent(DX, DY, u, v, eps, 1, 3000, tau=tau)
+    Pi = 2.0 * O.grad(DX, DY, np.outer(u, v), u, v)
+    f, g = O.sinkhorn_log(Pi, u, v, tau, 3000)
+    assert relerr(T1, O.plan(Pi, f, g, tau)) < 1e-9
+
+
+def test_tau_keeps_the_fixed_point():
+    """A fixed point of the step satisfies grad E(T) + eps ln T = f + g for any
+    tau (the (eps - tau) ln T term and the tau H term combine), so long runs
+    with tau = eps and tau = 2 eps reach the same plan, and that plan
+    satisfies the fixed-point equation; a sign error in the (eps - tau) term
+    moves the fixed point."""
+    u, v, DX, DY = _md_problem(7, 6, 52)
+    eps, tau = 0.2, 0.4
+    Ta, _, _ = O.mirror_descent(DX, DY, u, v, eps, 150, 300)
+    Tb, fb, gb = O.mirror_descent(DX, DY, u, v, eps, 300, 300, tau=tau)
+    assert relerr(Tb, Ta) < 1e-10
+    Pi = 2.0 * O.grad(DX, DY, Tb, u, v)
+    assert np.max(np.abs(Pi + eps * np.log(Tb) - fb[:, None] - gb[None, :])) < 1e-10
+    # Planted mistake: (tau - eps) instead of (eps - tau).
+    T = np.outer(u, v)
+    for _ in range(300):
+        Pi = 2.0 * O.grad(DX, DY, T, u, v) + (tau - eps) * np.log(T)
+        f, g = O.sinkhorn_log(Pi, u, v, tau, 300)
+        T = O.plan(Pi, f, g, tau)
+    assert relerr(T, Ta) > 1e-4
+
+
+def test_warm_start_converged_inner_loop_matches_cold():
+    """With each Sinkhorn solve converged, warm and cold starts give the same
+    mirror-descent iterates."""
+    u, v, DX, DY = _md_problem(8, 8, 53)
+    Tc, _, _ = O.mirror_descent(DX, DY, u, v, 0.1, 5, 2000)
+    Tw, _, _ = O.mirror_descent(DX, DY, u, v, 0.1, 5, 2000, warm_start=True)
+    assert relerr(Tw, Tc) < 1e-9
