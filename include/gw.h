@@ -87,6 +87,11 @@ typedef struct gw_problem {
   double theta;  /* fused-GW weight of the GW term, in [0, 1]; 1 = plain GW */
   int feat_dim;  /* fused-GW feature dimension (0 = none) */
   int dtype;     /* gw_dtype of T, G (and of the solver's arithmetic) */
+  double tau;    /* mirror-descent proximal weight (eq. "GW proximal gradient"),
+                    solver only: > 0, or 0 for tau = eps (the Remark's choice) */
+  int warm_start; /* solver only: 1 starts each mirror-descent step's Sinkhorn
+                    iteration from the previous step's potentials, 0 from
+                    f = g = 0 */
 } gw_problem;
 
 typedef struct gw_ctx gw_ctx;
@@ -231,18 +236,23 @@ gw_status gw_grad_dense(gw_ctx* ctx, const gw_problem* prob, const double* d_u, 
                         const void* d_T, void* d_G, int marginals, int precision, void* stream);
 
 /*
- * gw_solve - entropic (fused) Gromov-Wasserstein by mirror descent with
- * tau = eps (Sec. 2.1, eq. "GW sinkhorn" and the Remark on tau = eps; fused
- * GW by the Remark "FGW").
+ * gw_solve - entropic (fused) Gromov-Wasserstein by mirror descent (Sec.
+ * 2.1, eqs. "GW proximal gradient" and "GW sinkhorn", with the Remark's
+ * tau = eps unless prob->tau is set; fused GW by the Remark "FGW").
  *
  * Starting from T^0 = u v^T, each of prob->n_outer steps forms the cost
- *     Pi = 2 theta G(T) + (1 - theta) C o C,   G = L(C_X, C_Y) (x) T with the
- *     target marginals (gw_grad), C o C_ip = ||phi_i - psi_p||^2,
- * and runs prob->n_inner log-domain Sinkhorn iterations from f = g = 0
- * (f then g each iteration), then sets T_ip = exp((f_i + g_p - Pi_ip) / eps).
+ *     Pi = 2 theta G(T) + (1 - theta) C o C + (eps - tau) ln T,
+ *     G = L(C_X, C_Y) (x) T with the target marginals (gw_grad),
+ *     C o C_ip = ||phi_i - psi_p||^2 (the last term vanishes for tau = eps;
+ *     an entry of T that underflowed to 0 counts as the smallest normal),
+ * and runs prob->n_inner log-domain Sinkhorn iterations at regularisation
+ * tau from f = g = 0 (with prob->warm_start, from the previous step's f, g
+ * after the first step), f then g each iteration, then sets
+ * T_ip = exp((f_i + g_p - Pi_ip) / tau).
  *
  *   prob         dim 1 or 2; nx, ny, hx, hy, k, cost as for gw_grad, with at
  *                most 16384 points in Y (ny, or ny^2 in 2D); eps > 0;
+ *                tau = 0 (tau = eps) or > 0; warm_start 0 or 1;
  *                n_outer >= 0; n_inner >= 1; theta in [0, 1]; feat_dim in
  *                [1, 64] when theta < 1; dtype GW_F32 or GW_F64 (the
  *                arithmetic precision of the whole solve).
@@ -250,7 +260,9 @@ gw_status gw_grad_dense(gw_ctx* ctx, const gw_problem* prob, const double* d_u, 
  *   d_phi,d_psi  fused-GW features, double, row-major n x feat_dim and
  *                m x feat_dim; read only when theta < 1 (else may be NULL).
  *   d_T          output plan, n x m row-major, prob->dtype.
- *   d_f, d_g     output potentials (double, lengths n and m) or NULL.
+ *   d_f, d_g     output potentials of the last Sinkhorn solve (double,
+ *                lengths n and m, in the units of its regularisation tau)
+ *                or NULL.
  *   d_stats      NULL or 8 doubles on the device: [0] objective
  *                (1 - theta) <C o C, T> + theta E(T), [1] E(T) (the GW
  *                energy, Sec. 2), [2] <C o C, T>, [3] eps H(T),

@@ -603,6 +603,9 @@ gw_status check_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const d
   gw_status s = check_grid(c, p);
   if (s != GW_OK) return s;
   if (!finite_pos(p->eps)) return fail(c, GW_ERR_INVALID, "%s: eps must be finite and > 0", who);
+  if (!(p->tau == 0.0 || finite_pos(p->tau)))
+    return fail(c, GW_ERR_INVALID, "%s: tau must be 0 (tau = eps) or finite and > 0", who);
+  if (p->warm_start != 0 && p->warm_start != 1) return fail(c, GW_ERR_INVALID, "%s: warm_start must be 0 or 1", who);
   if (p->n_outer < 0 || p->n_inner < 1)
     return fail(c, GW_ERR_INVALID, "%s: need n_outer >= 0 and n_inner >= 1", who);
   if (!(p->theta >= 0.0 && p->theta <= 1.0)) return fail(c, GW_ERR_INVALID, "%s: theta must be in [0, 1]", who);
@@ -629,6 +632,8 @@ gw::SolveArgs solve_args(gw_ctx* c, const gw_problem* p, const double* d_u, cons
   a.hx = p->hx;
   a.hy = p->hy;
   a.eps = p->eps;
+  a.tau = p->tau > 0.0 ? p->tau : p->eps;
+  a.warm_start = p->warm_start;
   a.theta = p->theta;
   a.n_outer = p->n_outer;
   a.n_inner = p->n_inner;
@@ -664,8 +669,10 @@ gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const doub
   s = ensure_ws(c, gw::solve_workspace_bytes(a));
   if (s != GW_OK) return s;
   char key[512];
-  snprintf(key, sizeof key, "solve %d %d %d %d %d %d %.17g %.17g %.17g %.17g %d %d %d %p %p %p %p %p %p %p %p %p %zu",
-           a.dim, a.cost, a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.theta, a.n_outer, a.n_inner, a.feat_dim,
+  snprintf(key, sizeof key,
+           "solve %d %d %d %d %d %d %.17g %.17g %.17g %.17g %.17g %d %d %d %d %p %p %p %p %p %p %p %p %p %zu", a.dim,
+           a.cost, a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.tau, a.theta, a.warm_start, a.n_outer, a.n_inner,
+           a.feat_dim,
            (void*)a.u, (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.f, (void*)a.g, (void*)a.stats, c->ws,
            c->ws_bytes);
   return run_graph(
@@ -779,9 +786,9 @@ gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const do
     key += buf;
     for (int i = 0; i < count; ++i) {
       const gw::SolveArgs& a = args[i];
-      snprintf(buf, sizeof buf, "%d %d %d %d %d %d %.17g %.17g %.17g %.17g %d %d %d %p %p %p %p %p %p|", a.dim,
-               a.cost, a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.theta, a.n_outer, a.n_inner, a.feat_dim,
-               (void*)a.u, (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.stats);
+      snprintf(buf, sizeof buf, "%d %d %d %d %d %d %.17g %.17g %.17g %.17g %.17g %d %d %d %d %p %p %p %p %p %p|",
+               a.dim, a.cost, a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.tau, a.theta, a.warm_start, a.n_outer,
+               a.n_inner, a.feat_dim, (void*)a.u, (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.stats);
       key += buf;
     }
     if (!c->batch_exec || c->batch_key != key) {

@@ -174,6 +174,8 @@ struct SolveArgs {
   int nx, ny;
   int n, m, k, dtype;
   double hx, hy, eps, theta;
+  double tau;      // Sinkhorn regularisation of each step (= eps unless set)
+  int warm_start;  // 1: Sinkhorn starts from the previous step's potentials
   int n_outer, n_inner, feat_dim;
   const double *u, *v, *phi, *psi;
   void* T;

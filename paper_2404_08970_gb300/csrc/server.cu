@@ -97,6 +97,8 @@ gw::SolveArgs args_for(const gw_server* s, const gw_problem& p) {
   a.hx = p.hx;
   a.hy = p.hy;
   a.eps = p.eps;
+  a.tau = p.tau > 0.0 ? p.tau : p.eps;
+  a.warm_start = p.warm_start;
   a.theta = p.theta;
   a.n_outer = p.n_outer;
   a.n_inner = p.n_inner;
@@ -317,7 +319,8 @@ gw_status gw_submit(gw_server* s, const gw_problem* p, const double* h_u, const 
   if (!s || !p || !h_u || !h_v || !ticket) return GW_ERR_INVALID;
   const gw_problem& q = *p;
   if ((q.dim != 1 && q.dim != 2) || q.nx < 1 || q.ny < 1 || !(q.hx > 0) || !(q.hy > 0) || q.k < 1 ||
-      (q.dtype != GW_F32 && q.dtype != GW_F64) || !(q.eps > 0) || q.n_outer < 0 || q.n_inner < 1 ||
+      (q.dtype != GW_F32 && q.dtype != GW_F64) || !(q.eps > 0) || !(q.tau == 0.0 || q.tau > 0) ||
+      (q.warm_start != 0 && q.warm_start != 1) || q.n_outer < 0 || q.n_inner < 1 ||
       !(q.theta >= 0.0 && q.theta <= 1.0))
     return GW_ERR_INVALID;
   if (q.dim == 1 && (q.k > 3 || q.ny > 16384)) return GW_ERR_INVALID;

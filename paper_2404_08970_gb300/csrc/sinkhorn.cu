@@ -777,6 +777,15 @@ __global__ void finish_stats(const double* __restrict__ dotE, int nE, const doub
   }
 }
 
+// Pi += coef * ln T elementwise; an entry of T that underflowed to zero
+// counts as the smallest normal number of the type.
+template <typename Real>
+__global__ void add_log_plan(Real* __restrict__ Pi, const Real* __restrict__ T, size_t N, Real coef) {
+  const Real tiny = sizeof(Real) == 4 ? (Real)1.17549435e-38f : (Real)2.2250738585072014e-308;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    Pi[i] = fma(coef, log(fmax(T[i], tiny)), Pi[i]);
+}
+
 template <typename Real>
 __global__ void potentials_out(const Real* __restrict__ F, int len, double scale, double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -838,7 +847,7 @@ int prepare(const SolveArgs& A, void* wsv, size_t ws_bytes, SolveState<Real>* S)
   k.m = m;
   k.B = bands.B;
   k.R = bands.R;
-  k.c = (Real)(1.4426950408889634 / A.eps);
+  k.c = (Real)(1.4426950408889634 / A.tau);  // each step's Sinkhorn regularisation is tau
   k.Pi = (Real*)take((size_t)n * m * sizeof(Real));
   k.F = (Real*)take((size_t)n * sizeof(Real));
   k.G = (Real*)take((size_t)m * sizeof(Real));
@@ -924,9 +933,10 @@ void step_setup(const SolveState<Real>& S, cudaStream_t st) {
   fill_product<Real><<<4 * A.num_sms, 256, 0, st>>>(A.u, A.v, A.n, A.m, (Real*)A.T);
 }
 
-// Pi for one mirror-descent step, then f = g = 0.
+// Pi for mirror-descent step l, then f = g = 0 (or, warm-started after the
+// first step, the previous step's potentials stay).
 template <typename Real>
-int step_cost(const SolveState<Real>& S, cudaStream_t st) {
+int step_cost(const SolveState<Real>& S, cudaStream_t st, int l) {
   const SolveArgs& A = *S.A;
   int rc = gradient(S, 0, 2.0 * A.theta, st);
   if (rc != GW_OK) return rc;
@@ -935,6 +945,13 @@ int step_cost(const SolveState<Real>& S, cudaStream_t st) {
     const dim3 grid((A.m + 255) / 256, (A.n + kFeatRows - 1) / kFeatRows);
     add_feature_cost<Real><<<grid, 256, 0, st>>>((Real*)S.sk.Pi, A.n, A.m, A.feat_dim, A.phi, A.psi, 1.0 - A.theta);
   }
+  if (A.tau != A.eps) {
+    // Pi += (eps - tau) grad H(T), grad H(T) = ln T (eq. "GW sinkhorn").
+    TraceScope ts(A.tracer, "add_log_plan", st);
+    add_log_plan<Real><<<4 * A.num_sms, 256, 0, st>>>((Real*)S.sk.Pi, (const Real*)A.T, (size_t)A.n * A.m,
+                                                      (Real)(A.eps - A.tau));
+  }
+  if (A.warm_start && l > 0) return GW_OK;
   TraceScope ts(A.tracer, "solve_setup", st);
   fill_val<Real><<<(A.n + 255) / 256, 256, 0, st>>>(S.sk.F, A.n, (Real)0);
   fill_val<Real><<<(A.m + 255) / 256, 256, 0, st>>>(S.sk.G, A.m, (Real)0);
@@ -946,8 +963,8 @@ template <typename Real>
 int step_finish(const SolveState<Real>& S, cudaStream_t st) {
   const SolveArgs& A = *S.A;
   const int n = A.n, m = A.m;
-  if (A.f) potentials_out<Real><<<(n + 255) / 256, 256, 0, st>>>(S.sk.F, n, A.eps / 1.4426950408889634, A.f);
-  if (A.g) potentials_out<Real><<<(m + 255) / 256, 256, 0, st>>>(S.sk.G, m, A.eps / 1.4426950408889634, A.g);
+  if (A.f) potentials_out<Real><<<(n + 255) / 256, 256, 0, st>>>(S.sk.F, n, A.tau / 1.4426950408889634, A.f);
+  if (A.g) potentials_out<Real><<<(m + 255) / 256, 256, 0, st>>>(S.sk.G, m, A.tau / 1.4426950408889634, A.g);
   if (!A.stats) return GW_OK;
   TraceScope ts(A.tracer, "solve_stats", st);
   // E(T) = <G(T; T's marginals), T>; the gradient overwrites Pi.
@@ -1019,7 +1036,7 @@ int solve_typed(const SolveArgs& A, void* ws, size_t ws_bytes) {
   SolveState<Real>* list[1] = {&S};
   step_setup(S, st);
   for (int l = 0; l < A.n_outer; ++l) {
-    rc = step_cost(S, st);
+    rc = step_cost(S, st, l);
     if (rc != GW_OK) return rc;
     for (int it = 0; it < A.n_inner; ++it) {
       rc = launch_rows<NW, VPT, NG, Real, 1>(list, 1, false, st, A.status, A.tracer);
@@ -1050,7 +1067,7 @@ int solve_group(const SolveArgs* const* A, void* const* ws, const size_t* ws_byt
   for (auto& s : S) step_setup(s, st);
   for (int l = 0; l < A[0]->n_outer; ++l) {
     for (auto& s : S) {
-      int rc = step_cost(s, st);
+      int rc = step_cost(s, st, l);
       if (rc != GW_OK) return rc;
     }
     for (int it = 0; it < A[0]->n_inner; ++it) {

@@ -17,7 +17,8 @@ def _prob(L, w, dtype):
     return L.problem(dim=w.get("dim", 1), nx=w["nx"], ny=w["ny"], hx=w["hx"], hy=w["hy"], k=w["k"],
                      cost=w.get("cost", 0), eps=w["eps"], n_outer=w["n_outer"], n_inner=w["n_inner"],
                      theta=w.get("theta", 1.0), feat_dim=0 if w.get("phi") is None else w["phi"].shape[1],
-                     dtype=L.GW_F32 if dtype == "f32" else L.GW_F64)
+                     dtype=L.GW_F32 if dtype == "f32" else L.GW_F64, tau=w.get("tau", 0.0),
+                     warm_start=w.get("warm", 0))
 
 
 def _points(w):
@@ -34,6 +35,8 @@ def _mixed():
     r2 = I.rng_for(3)
     ws.append(dict(dim=2, cost="sqeuclid", nx=6, ny=9, hx=0.2, hy=0.125, k=1, eps=5e-2, n_outer=3, n_inner=30,
                    u=I.abs_normal_image(6, r2), v=I.abs_normal_image(9, r2)))
+    ws.append(dict(nx=90, ny=70, hx=1 / 90, hy=1 / 70, k=1, eps=5e-2, n_outer=3, n_inner=30, tau=0.1, warm=1,
+                   u=I.dirichlet(90, 1.0, rng), v=I.dirichlet(70, 1.0, rng)))
     ws.append(dict(nx=50, ny=60, hx=0.02, hy=1 / 60, k=1, eps=5e-2, n_outer=3, n_inner=30, theta=0.5,
                    u=I.dirichlet(50, 1.0, rng), v=I.dirichlet(60, 1.0, rng),
                    phi=I.features(50, 16, rng) * 0.1, psi=I.features(60, 16, rng) * 0.1))
@@ -97,7 +100,8 @@ def test_batch_fp64_matches_oracle():
     c.gw_ctx_check()
     for i, w in enumerate(ws):
         DX, DY = O.grid_dist_1d(w["nx"], w["hx"], w["k"]), O.grid_dist_1d(w["ny"], w["hy"], w["k"])
-        Ts, _, _ = O.mirror_descent(DX, DY, w["u"], w["v"], w["eps"], w["n_outer"], w["n_inner"])
+        Ts, _, _ = O.mirror_descent(DX, DY, w["u"], w["v"], w["eps"], w["n_outer"], w["n_inner"], tau=w.get("tau"),
+                                    warm_start=bool(w.get("warm", 0)))
         assert U.relerr(T[i].cpu().numpy(), Ts) < 1e-9, i
 
 

@@ -35,7 +35,8 @@ def gpu_solve(w, dtype, theta=1.0, phi=None, psi=None):
     dpsi = None if psi is None else torch.from_numpy(np.ascontiguousarray(psi)).cuda()
     prob = L.problem(dim=1, nx=n, ny=m, hx=w["hx"], hy=w["hy"], k=w["k"], eps=w["eps"], n_outer=w["n_outer"],
                      n_inner=w["n_inner"], theta=theta, feat_dim=D,
-                     dtype=L.GW_F32 if dtype == "f32" else L.GW_F64)
+                     dtype=L.GW_F32 if dtype == "f32" else L.GW_F64, tau=w.get("tau", 0.0),
+                     warm_start=int(w.get("warm", False)))
     c.gw_solve(prob, du, dv, T, f, g, stats, dphi, dpsi)
     c.gw_ctx_check()
     return T.double().cpu().numpy(), f.cpu().numpy(), g.cpu().numpy(), stats.cpu().numpy()
@@ -45,7 +46,8 @@ def oracle_solve(w, theta=1.0, phi=None, psi=None):
     n, m, k = w["nx"], w["ny"], w["k"]
     DX, DY = O.grid_dist_1d(n, w["hx"], k), O.grid_dist_1d(m, w["hy"], k)
     CC = None if phi is None else O.fgw_feature_cost(phi, psi)
-    T, f, g = O.mirror_descent(DX, DY, w["u"], w["v"], w["eps"], w["n_outer"], w["n_inner"], theta=theta, CC=CC)
+    T, f, g = O.mirror_descent(DX, DY, w["u"], w["v"], w["eps"], w["n_outer"], w["n_inner"], theta=theta, CC=CC,
+                               tau=w.get("tau"), warm_start=w.get("warm", False))
     E = O.value(DX, DY, T)
     lin = 0.0 if CC is None else float(np.sum(CC * T))
     return T, f, g, dict(E=E, lin=lin, obj=O.fgw_value(DX, DY, T, theta, CC), H=w["eps"] * O.entropy(T),
@@ -129,6 +131,31 @@ def test_solve_full_size_row_configurations_fp32(n, m, k):
     assert abs(st[1] - ss["E"]) <= 1e-5 * abs(ss["E"]), (st[1], ss["E"])
     assert st[5] < 1e-5
     assert fro(T, Ts) < 1e-4
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("tau_over_eps,warm", [(2.0, False), (0.5, False), (1.0, True), (3.0, True)])
+@pytest.mark.parametrize("shape,k", [((64, 150), 1), ((150, 64), 2), ((33, 1000), 1)])
+def test_solve_tau_and_warm_start(shape, k, tau_over_eps, warm, dtype):
+    """Mirror descent with the proximal weight tau != eps (Pi = grad E +
+    (eps - tau) ln T, each Sinkhorn solve at tau; eq. "GW sinkhorn") and
+    Sinkhorn solves warm-started from the previous step's potentials."""
+    n, m = shape
+    rng = np.random.default_rng(n + 3 * m + k)
+    eps = 5e-2
+    w = dict(nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=k, eps=eps, n_outer=5, n_inner=40, tau=tau_over_eps * eps,
+             warm=warm, u=I.dirichlet(n, 1.0, rng), v=I.dirichlet(m, 1.0, rng))
+    T, f, g, st = gpu_solve(w, dtype)
+    Ts, fs, gs, ss = oracle_solve(w)
+    if dtype == "f64":
+        assert U.relerr(T, Ts) < 1e-9
+        assert abs(st[1] - ss["E"]) <= 1e-10 * abs(ss["E"])
+        assert abs(st[3] - ss["H"]) <= 1e-9 * abs(ss["H"])
+        assert U.relerr(f, fs) < 1e-9 and U.relerr(g, gs) < 1e-9
+    else:
+        assert abs(st[1] - ss["E"]) <= 1e-5 * abs(ss["E"])
+        assert fro(T, Ts) < 1e-3
+        assert st[5] < 1e-5
 
 
 def test_solve_reflection_and_single_point():
