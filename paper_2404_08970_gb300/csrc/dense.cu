@@ -25,7 +25,12 @@ __global__ void build_dist(Out* __restrict__ D, int n, double hk, int k, int sid
     double v;
     if (side > 0) {
       const double da = (double)llabs(i / side - j / side), db = (double)llabs(i % side - j % side);
-      v = sq ? da * da + db * db : da + db;
+      if (sq) {
+        v = da * da + db * db;
+      } else {  // Manhattan distance to the power k
+        v = 1.0;
+        for (int e = 0; e < k; ++e) v *= da + db;
+      }
     } else {
       const double d = (double)(i > j ? i - j : j - i);
       v = 1.0;
@@ -113,14 +118,20 @@ __global__ void dense_epilogue(Real* __restrict__ G, int n, int m, const Real* _
 // Constant term on a 2D grid, pointwise: c[i] = scale * sum_j d(i,j)^2 w_j
 // with d the Manhattan or squared Euclidean grid distance (one block per i).
 template <typename Real>
-__global__ void dist2_const_2d(const double* __restrict__ w, int side, int sq, double scale, Real* __restrict__ out) {
+__global__ void dist2_const_2d(const double* __restrict__ w, int side, int sq, int k, double scale,
+                               Real* __restrict__ out) {
   const int n = side * side;
   const int i = blockIdx.x;
   const int a = i / side, b = i % side;
   double acc = 0.0;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
     const double da = (double)abs(a - j / side), db = (double)abs(b - j % side);
-    const double d = sq ? da * da + db * db : da + db;
+    double d = 1.0;
+    if (sq) {
+      d = da * da + db * db;
+    } else {
+      for (int e = 0; e < k; ++e) d *= da + db;
+    }
     acc += d * d * w[j];
   }
   __shared__ double sm[32];
@@ -192,7 +203,7 @@ static int ensure_dist(DenseCache& c, int n, double h, int k, int side, int sq, 
     c.D = nullptr;
     return GW_ERR_OOM;
   }
-  const double hk = side > 0 ? (sq ? h * h : h) : std::pow(h, k);
+  const double hk = side > 0 && sq ? h * h : std::pow(h, k);
   if (pitch != n) cudaMemsetAsync(c.D, 0, (size_t)pitch * pitch * esz, st);
   const int tf = prec == GW_DENSE_TC_TF32;
   if (bf)
@@ -296,13 +307,13 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
   }
   if (a.dim == 2) {
     TraceScope ts(a.tracer, "dense_const", st);
-    const double fx = sq ? a.hx * a.hx : a.hx, fy = sq ? a.hy * a.hy : a.hy;
+    const double fx = sq ? a.hx * a.hx : std::pow(a.hx, a.k), fy = sq ? a.hy * a.hy : std::pow(a.hy, a.k);
     if (dbl) {
-      dist2_const_2d<double><<<n, 256, 0, st>>>(wx, a.sx, sq, fx * fx, (double*)cx);
-      dist2_const_2d<double><<<m, 256, 0, st>>>(wy, a.sy, sq, fy * fy, (double*)cy);
+      dist2_const_2d<double><<<n, 256, 0, st>>>(wx, a.sx, sq, a.k, fx * fx, (double*)cx);
+      dist2_const_2d<double><<<m, 256, 0, st>>>(wy, a.sy, sq, a.k, fy * fy, (double*)cy);
     } else {
-      dist2_const_2d<float><<<n, 256, 0, st>>>(wx, a.sx, sq, fx * fx, (float*)cx);
-      dist2_const_2d<float><<<m, 256, 0, st>>>(wy, a.sy, sq, fy * fy, (float*)cy);
+      dist2_const_2d<float><<<n, 256, 0, st>>>(wx, a.sx, sq, a.k, fx * fx, (float*)cx);
+      dist2_const_2d<float><<<m, 256, 0, st>>>(wy, a.sy, sq, a.k, fy * fy, (float*)cy);
     }
   } else {
     rc = marg_const2_launch(wx, n, std::pow(a.hx, 2 * a.k), cx, wy, m, std::pow(a.hy, 2 * a.k), cy, a.k,

@@ -566,9 +566,13 @@ int grad2d_dispatch(const Grad2DArgs& A, void* ws, size_t ws_bytes) {
 
 }  // namespace
 
-size_t grad2d_workspace_bytes(int sx, int sy, int dtype) { return g2_layout(sx, sy, dtype).total + 4096; }
+size_t grad2d_workspace_bytes(int sx, int sy, int dtype, int cost, int k) {
+  if (cost == GW_COST_POW && k >= 2) return grad2d_powk_workspace_bytes(sx, sy, k, dtype);
+  return g2_layout(sx, sy, dtype).total + 4096;
+}
 
 int grad2d_launch(const Grad2DArgs& a, void* ws, size_t ws_bytes) {
+  if (a.cost == GW_COST_POW && a.k >= 2) return grad2d_powk_launch(a, ws, ws_bytes);
   if (a.sx < 1 || a.sy < 1 || a.sx > kMax2DSide || a.sy > kMax2DSide) return GW_ERR_INVALID;
   if (a.cost != GW_COST_POW && a.cost != GW_COST_SQEUCLID) return GW_ERR_INVALID;
   if (a.dtype == GW_F32) return grad2d_dispatch<float>(a, ws, ws_bytes);

@@ -224,10 +224,12 @@ gw_status check_grid(gw_ctx* c, const gw_problem* p) {
   } else {
     if (p->cost != GW_COST_POW && p->cost != GW_COST_SQEUCLID)
       return fail(c, GW_ERR_INVALID, "2D cost must be GW_COST_POW or GW_COST_SQEUCLID (got %d)", p->cost);
-    if (p->cost == GW_COST_POW && p->k != 1)
-      return fail(c, GW_ERR_INVALID, "2D Manhattan cost is available for k = 1 only (got %d)", p->k);
     if (p->nx > gw::kMax2DSide || p->ny > gw::kMax2DSide)
       return fail(c, GW_ERR_INVALID, "2D grid sides must be <= %d (got %d, %d)", gw::kMax2DSide, p->nx, p->ny);
+    if (p->cost == GW_COST_POW && p->k > 1 && !gw::grad2d_powk_supported(p->nx, p->ny, p->k, p->dtype))
+      return fail(c, GW_ERR_INVALID,
+                  "2D Manhattan^k with k = %d needs k <= 3 and grid sides <= 128 (float) or a smaller double "
+                  "image (got %d, %d)", p->k, p->nx, p->ny);
   }
   return GW_OK;
 }
@@ -384,6 +386,7 @@ gw_status grad_device(gw_ctx* c, const gw_problem* p, const double* d_u, const d
     a.sx = p->nx;
     a.sy = p->ny;
     a.cost = p->cost;
+    a.k = p->k;
     a.hx = p->hx;
     a.hy = p->hy;
     a.dtype = p->dtype;
@@ -397,11 +400,11 @@ gw_status grad_device(gw_ctx* c, const gw_problem* p, const double* d_u, const d
     a.status = c->status;
     a.num_sms = c->num_sms;
     a.tracer = c->tr();
-    s = ensure_ws(c, gw::grad2d_workspace_bytes(a.sx, a.sy, a.dtype));
+    s = ensure_ws(c, gw::grad2d_workspace_bytes(a.sx, a.sy, a.dtype, a.cost, a.k));
     if (s != GW_OK) return s;
     char key[384];
-    snprintf(key, sizeof key, "grad2 %d %d %d %.17g %.17g %d %p %p %p %p %d %p %zu", a.sx, a.sy, a.cost, a.hx, a.hy,
-             a.dtype, a.T, a.G, (void*)a.u, (void*)a.v, a.exact, c->ws, c->ws_bytes);
+    snprintf(key, sizeof key, "grad2 %d %d %d %d %.17g %.17g %d %p %p %p %p %d %p %zu", a.sx, a.sy, a.cost, a.k, a.hx,
+             a.hy, a.dtype, a.T, a.G, (void*)a.u, (void*)a.v, a.exact, c->ws, c->ws_bytes);
     return run_graph(
         c, key, a.stream,
         [&](cudaStream_t st) {

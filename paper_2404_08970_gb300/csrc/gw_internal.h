@@ -122,7 +122,8 @@ int marg_const2_launch(const double* wx, int n, double fx, void* outx, const dou
 constexpr int kMax2DSide = 256;
 struct Grad2DArgs {
   int sx, sy;           // grid sides; n = sx^2 points of X, m = sy^2 points of Y
-  int cost;             // GW_COST_POW (k = 1) or GW_COST_SQEUCLID
+  int cost;             // GW_COST_POW (Manhattan^k) or GW_COST_SQEUCLID
+  int k;                // exponent of the Manhattan distance (GW_COST_POW)
   double hx, hy;
   int dtype;
   const void* T;        // n x m row-major, dtype
@@ -136,8 +137,14 @@ struct Grad2DArgs {
   int num_sms;
   Tracer* tracer;
 };
-size_t grad2d_workspace_bytes(int sx, int sy, int dtype);
+// Workspace of the 2D gradient for this cost and exponent (the separable
+// costs, or Manhattan^k with k >= 2).
+size_t grad2d_workspace_bytes(int sx, int sy, int dtype, int cost, int k);
 int grad2d_launch(const Grad2DArgs& a, void* ws, size_t ws_bytes);
+// Manhattan^k, k = 2, 3 (grad2d_powk.cu): supported grid sides and dtype.
+bool grad2d_powk_supported(int sx, int sy, int k, int dtype);
+size_t grad2d_powk_workspace_bytes(int sx, int sy, int k, int dtype);
+int grad2d_powk_launch(const Grad2DArgs& a, void* ws, size_t ws_bytes);
 
 // Dense comparison gradient through cuBLAS (dense.cu).
 struct DenseArgs {

@@ -324,8 +324,9 @@ gw_status gw_submit(gw_server* s, const gw_problem* p, const double* h_u, const 
       !(q.theta >= 0.0 && q.theta <= 1.0))
     return GW_ERR_INVALID;
   if (q.dim == 1 && (q.k > 3 || q.ny > 16384)) return GW_ERR_INVALID;
-  if (q.dim == 2 && ((q.cost != GW_COST_POW && q.cost != GW_COST_SQEUCLID) || (q.cost == GW_COST_POW && q.k != 1) ||
-                     q.nx > gw::kMax2DSide || q.ny > gw::kMax2DSide))
+  if (q.dim == 2 && ((q.cost != GW_COST_POW && q.cost != GW_COST_SQEUCLID) || q.nx > gw::kMax2DSide ||
+                     q.ny > gw::kMax2DSide ||
+                     (q.cost == GW_COST_POW && q.k > 1 && !gw::grad2d_powk_supported(q.nx, q.ny, q.k, q.dtype))))
     return GW_ERR_INVALID;
   if (points_y(q) > 16384) return GW_ERR_INVALID;
   if (q.theta != 1.0 && (q.feat_dim < 1 || q.feat_dim > 64 || !h_phi || !h_psi)) return GW_ERR_INVALID;

@@ -880,6 +880,7 @@ int gradient(const SolveState<Real>& S, int exact, double out_scale, cudaStream_
     g2.sx = A.nx;
     g2.sy = A.ny;
     g2.cost = A.cost;
+    g2.k = A.k;
     g2.hx = A.hx;
     g2.hy = A.hy;
     g2.dtype = A.dtype;
@@ -1184,7 +1185,7 @@ size_t solve_workspace_bytes(const SolveArgs& A) {
   add((size_t)2 * bands.B * 8);
   add(kDots * 8);
   add(kDots * 8);
-  const size_t g = A.dim == 2 ? grad2d_workspace_bytes(A.nx, A.ny, A.dtype)
+  const size_t g = A.dim == 2 ? grad2d_workspace_bytes(A.nx, A.ny, A.dtype, A.cost, A.k)
                               : grad1d_workspace_bytes(n, m, A.k, A.dtype, A.num_sms);
   return b + g + 4096;
 }

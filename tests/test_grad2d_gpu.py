@@ -24,7 +24,7 @@ def make(sx, sy, seed=0):
     return u, v, T
 
 
-def gpu_grad_2d(T, u, v, sx, sy, cost, hx, hy, dtype, marginals):
+def gpu_grad_2d(T, u, v, sx, sy, cost, hx, hy, dtype, marginals, k=1):
     import torch
     from paper_2404_08970_gb300 import _lib as L
     c = U.ctx()
@@ -33,7 +33,7 @@ def gpu_grad_2d(T, u, v, sx, sy, cost, hx, hy, dtype, marginals):
     dG = torch.empty_like(dT)
     du = None if u is None else torch.from_numpy(np.asarray(u, dtype=np.float64)).cuda()
     dv = None if v is None else torch.from_numpy(np.asarray(v, dtype=np.float64)).cuda()
-    prob = L.problem(dim=2, nx=sx, ny=sy, hx=hx, hy=hy, k=1, cost=COSTS[cost],
+    prob = L.problem(dim=2, nx=sx, ny=sy, hx=hx, hy=hy, k=k, cost=COSTS[cost],
                      dtype=L.GW_F32 if dtype == "f32" else L.GW_F64)
     mg = L.GW_MARG_TARGET if marginals == "target" else L.GW_MARG_EXACT
     c.gw_grad(prob, du, dv, dT, dG, mg)
@@ -41,8 +41,8 @@ def gpu_grad_2d(T, u, v, sx, sy, cost, hx, hy, dtype, marginals):
     return dG.double().cpu().numpy()
 
 
-def oracle_grad_2d(T64, u, v, sx, sy, cost, hx, hy, marginals):
-    DX, DY = O.grid_dist_2d(sx, hx, cost), O.grid_dist_2d(sy, hy, cost)
+def oracle_grad_2d(T64, u, v, sx, sy, cost, hx, hy, marginals, k=1):
+    DX, DY = O.grid_dist_2d(sx, hx, cost, k), O.grid_dist_2d(sy, hy, cost, k)
     if marginals == "target":
         return O.grad(DX, DY, T64, u, v)
     return O.grad_exact(DX, DY, T64)
@@ -108,7 +108,7 @@ def test_grad2d_rejects_unsupported():
     T = torch.zeros(16, 16, device="cuda")
     G = torch.zeros_like(T)
     u = torch.full((16,), 1 / 16, dtype=torch.float64, device="cuda")
-    for kw in (dict(k=2, cost=0), dict(k=1, cost=5), dict(k=1, cost=1, nx=300)):
+    for kw in (dict(k=4, cost=0), dict(k=1, cost=5), dict(k=1, cost=1, nx=300), dict(k=2, cost=0, nx=129)):
         args = dict(dim=2, nx=4, ny=4, hx=0.1, hy=0.1)
         args.update(kw)
         prob = L.problem(**args)
@@ -139,3 +139,65 @@ def test_grad2d_dense_matches_oracle(cost, precision, tol):
     c.gw_ctx_check()
     Gs = oracle_grad_2d(Td.astype(np.float64), u, v, sx, sy, cost, hx, hy, "target")
     assert U.relerr(dG.double().cpu().numpy(), Gs) < tol
+
+
+# ---------------------------------------------------------------------------
+# Manhattan distance to the power k >= 2 (Sec. 3.1, eq. "2D kronecker"): the
+# two-pass image-transform path.
+# ---------------------------------------------------------------------------
+
+POWK_SHAPES = [(1, 1), (1, 4), (2, 3), (5, 4), (8, 10), (16, 12), (24, 32), (13, 7)]
+
+
+@pytest.mark.parametrize("sx,sy", POWK_SHAPES)
+@pytest.mark.parametrize("k", [2, 3])
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_grad2d_powk_matches_oracle(sx, sy, k, dtype):
+    u, v, T = make(sx, sy, seed=sx * 100 + sy + 7 * k)
+    hx, hy = 1.0 / max(sx - 1, 1), 1.0 / max(sy - 1, 1)
+    Td = T.astype(np.float32) if dtype == "f32" else T
+    tol = 1e-6 if dtype == "f32" else 1e-12
+    for marg in ("target", "exact"):
+        G = gpu_grad_2d(Td, u, v, sx, sy, "manhattan", hx, hy, dtype, marg, k=k)
+        Gs = oracle_grad_2d(Td.astype(np.float64), u, v, sx, sy, "manhattan", hx, hy, marg, k=k)
+        assert U.relerr(G, Gs) < tol, (marg, U.relerr(G, Gs))
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_grad2d_powk_full_size_sampled(k):
+    """64 x 64 against 96 x 96 grids, Manhattan^k: 24 sampled rows against the
+    oracle's row formula, all columns."""
+    sx, sy = 64, 96
+    u, v, T = make(sx, sy, seed=5 + k)
+    hx, hy = 1.0 / (sx - 1), 1.0 / (sy - 1)
+    T32 = T.astype(np.float32)
+    G = gpu_grad_2d(T32, u, v, sx, sy, "manhattan", hx, hy, "f32", "target", k=k)
+    assert np.all(np.isfinite(G))
+    rng = np.random.default_rng(12)
+    rows = np.unique(np.concatenate([[0, sx * sx - 1, sx - 1, sx * (sx - 1)], rng.integers(0, sx * sx, 20)]))
+    DX = O.grid_dist_2d(sx, hx, "manhattan", k)
+    DY = O.grid_dist_2d(sy, hy, "manhattan", k)
+    cx = (DX * DX) @ u
+    cy = (DY * DY) @ v
+    Gs = O.grad_rows(DX[rows], DY, T32.astype(np.float64), cx[rows], cy)
+    err = float(np.max(np.abs(G[rows] - Gs)) / np.max(np.abs(Gs)))
+    assert err < 1e-6, err
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_grad2d_powk_dense_path(k):
+    """The dense comparison path with Manhattan^k distance matrices."""
+    import torch
+    from paper_2404_08970_gb300 import _lib as L
+    sx, sy = 9, 11
+    u, v, T = make(sx, sy, seed=30 + k)
+    hx, hy = 1.0 / (sx - 1), 1.0 / (sy - 1)
+    c = U.ctx()
+    dT = torch.from_numpy(T).cuda()
+    dG = torch.empty_like(dT)
+    prob = L.problem(dim=2, nx=sx, ny=sy, hx=hx, hy=hy, k=k, cost=0, dtype=L.GW_F64)
+    c.gw_grad_dense(prob, torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), dT, dG, L.GW_MARG_TARGET,
+                    L.GW_DENSE_FP64)
+    c.gw_ctx_check()
+    Gs = oracle_grad_2d(T, u, v, sx, sy, "manhattan", hx, hy, "target", k=k)
+    assert U.relerr(dG.cpu().numpy(), Gs) < 1e-12
