@@ -62,6 +62,7 @@ __device__ __forceinline__ void line_pow(const Real* x, int step, int L, Real* o
   Real S[Q + 1];
 #pragma unroll
   for (int s = 0; s <= Q; ++s) S[s] = 0;
+#pragma unroll 4
   for (int i = 0; i < L; ++i) {
     const Real xi = x[i * step];
     Real* o = out + i * ostep;
@@ -76,6 +77,7 @@ __device__ __forceinline__ void line_pow(const Real* x, int step, int L, Real* o
   }
 #pragma unroll
   for (int s = 0; s <= Q; ++s) S[s] = 0;
+#pragma unroll 4
   for (int i = L - 1; i >= 0; --i) {
     const Real xi = x[i * step];
     Real* o = out + i * ostep;
@@ -97,6 +99,7 @@ __device__ __forceinline__ Real line_orders(const Real* x, int step, int L, Real
   Real S[Q + 1];
 #pragma unroll
   for (int s = 0; s <= Q; ++s) S[s] = 0;
+#pragma unroll 4
   for (int i = 0; i < L; ++i) {
     const Real xi = x[i * step];
 #pragma unroll
@@ -112,6 +115,7 @@ __device__ __forceinline__ Real line_orders(const Real* x, int step, int L, Real
   const Real total = S[0];
 #pragma unroll
   for (int s = 0; s <= Q; ++s) S[s] = 0;
+#pragma unroll 4
   for (int i = L - 1; i >= 0; --i) {
     const Real xi = x[i * step];
 #pragma unroll
@@ -134,10 +138,17 @@ struct PowKIO {
   int L;                 // image side: sy (pass 1) or sx (pass 2)
   int P;                 // images per CTA iteration (pass 1: 1)
   double* rowsum;        // pass 1, exact marginals: T 1 (double) or nullptr
-  const double* cx;      // pass 2: constant terms (double)
-  const double* cy;
+  const void* cxh;       // pass 2: constant terms, high and low parts (Real;
+  const void* cxl;       // the low parts are zero for double)
+  const void* cyh;
+  const void* cyl;
   double scale;          // pass 2: 2 h_X^k h_Y^k
 };
+
+// i / L for 0 <= i < 2^20 and 1 <= L <= 256 without an integer division:
+// (i + 1/2) / L is at least 1/(2L) away from an integer, far more than the
+// float product's rounding error.
+__device__ __forceinline__ int div_small(int i, float invL) { return __float2int_rz(((float)i + 0.5f) * invL); }
 
 // MODE 0: pass 1 over rows of T; MODE 1: pass 2 over column tiles of W.
 template <int K, typename Real, int MODE>
@@ -155,6 +166,8 @@ __global__ void __launch_bounds__(512) g2k_images(PowKIO io) {
   Real* ek = e0 + PL;                        // [P][L] A_K cs
   const int tid = threadIdx.x, NT = blockDim.x;
   const int img_elems = L * L;
+  const float invL = 1.0f / (float)L;
+  const int lp = P == 1 ? 0 : (P == 2 ? 1 : (P == 4 ? 2 : 3));  // P is a power of two
   const int units = MODE == 0 ? io.n : (io.m + P - 1) / P;
 
   for (int unit = blockIdx.x; unit < units; unit += gridDim.x) {
@@ -162,13 +175,13 @@ __global__ void __launch_bounds__(512) g2k_images(PowKIO io) {
     // ---- load the P images
     if (MODE == 0) {
       const Real* src = reinterpret_cast<const Real*>(io.in) + (size_t)unit * io.m;
-      for (int e = tid; e < img_elems; e += NT) Y[(e / L) * (L + 1) + e % L] = src[e];
+      for (int e = tid; e < img_elems; e += NT) Y[e + div_small(e, invL)] = src[e];
     } else {
       const Real* src = reinterpret_cast<const Real*>(io.in);
       for (int e = tid; e < P * img_elems; e += NT) {
-        const int q = e % P, i = e / P;
+        const int q = e & (P - 1), i = e >> lp;
         const int p = p0 + q;
-        Y[(size_t)q * IS + (i / L) * (L + 1) + i % L] = p < io.m ? src[(size_t)i * io.m + p] : (Real)0;
+        Y[q * IS + i + div_small(i, invL)] = p < io.m ? src[(size_t)i * io.m + p] : (Real)0;
       }
     }
     __syncthreads();
@@ -214,8 +227,8 @@ __global__ void __launch_bounds__(512) g2k_images(PowKIO io) {
     if (MODE == 0) {
       Real* dst = reinterpret_cast<Real*>(io.out) + (size_t)unit * io.m;
       for (int e = tid; e < img_elems; e += NT) {
-        const int c = e / L, d = e % L;
-        dst[e] = Y[c * (L + 1) + d] + e0[c] + ek[d];
+        const int c = div_small(e, invL), d = e - c * L;
+        dst[e] = Y[e + c] + e0[c] + ek[d];
       }
       if (io.rowsum && tid == 0) {
         double r = 0.0;
@@ -225,16 +238,17 @@ __global__ void __launch_bounds__(512) g2k_images(PowKIO io) {
     } else {
       Real* dst = reinterpret_cast<Real*>(io.out);
       const Real s = (Real)io.scale;
+      const Real* cxh = reinterpret_cast<const Real*>(io.cxh);
+      const Real* cxl = reinterpret_cast<const Real*>(io.cxl);
+      const Real* cyh = reinterpret_cast<const Real*>(io.cyh);
+      const Real* cyl = reinterpret_cast<const Real*>(io.cyl);
       for (int e = tid; e < P * img_elems; e += NT) {
-        const int q = e % P, i = e / P;
+        const int q = e & (P - 1), i = e >> lp;
         const int p = p0 + q;
         if (p >= io.m) continue;
-        const int a = i / L, b = i % L;
-        const Real z = Y[(size_t)q * IS + a * (L + 1) + b] + e0[q * L + a] + ek[q * L + b];
-        const double cc = io.cx[i] + io.cy[p];
-        const Real hi = (Real)cc;
-        const Real lo = (Real)(cc - (double)hi);
-        dst[(size_t)i * io.m + p] = fma(-s, z, hi) + lo;
+        const int a = div_small(i, invL), b = i - a * L;
+        const Real z = Y[q * IS + i + a] + e0[q * L + a] + ek[q * L + b];
+        dst[(size_t)i * io.m + p] = fma(-s, z, cxh[i] + cyh[p]) + (cxl[i] + cyl[p]);
       }
     }
     __syncthreads();
@@ -259,7 +273,8 @@ struct ConstJob {
   const double* w;
   int L;
   double* M;    // [2K + 1][L][L]
-  double* out;  // [L * L]
+  void* hi;     // [L * L] constant term, rounded to the compute type,
+  void* lo;     // and the rounding remainder (zero for double)
   double factor;
   int pad, pad2;  // first job's thread range, rounded to whole blocks (stage 1, stage 2)
 };
@@ -293,6 +308,7 @@ __global__ void g2k_const1(ConstJob X, ConstJob Yj, int P2) {
   J.M[t] = acc;
 }
 // Stage 2: c[a L + b] = factor sum_r C(2K, r) sum_a' |a - a'|^{2K - r} M[r][a'][b].
+template <typename Real>
 __global__ void g2k_const2(ConstJob X, ConstJob Yj, int P2) {
   __shared__ double tab[(kMaxPow + 1) * kMaxConstSide];
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -311,22 +327,28 @@ __global__ void g2k_const2(ConstJob X, ConstJob Yj, int P2) {
     for (int ap = 0; ap < L; ++ap) inner = fma(pw[abs(a - ap)], M[(size_t)ap * L], inner);
     acc = fma((double)binom_c(P2, r), inner, acc);
   }
-  J.out[t] = J.factor * acc;
+  const double c = J.factor * acc;
+  const Real h = (Real)c;
+  reinterpret_cast<Real*>(J.hi)[t] = h;
+  reinterpret_cast<Real*>(J.lo)[t] = (Real)(c - (double)h);
 }
 
 size_t images_smem(int K, int L, int P, size_t rb) {
   return ((size_t)K * P * img_stride(L) + 4 * (size_t)P * L) * rb;
 }
 
-// Column-tile width of pass 2: the widest of 8, 4, 2, 1 whose images fit.
+// Column-tile width of pass 2: the widest of 8, 4, 2, 1 whose images leave
+// room for two blocks per SM, else the widest that fits at all.
 int pass2_tile(int K, int L, size_t rb) {
+  for (int P : {8, 4, 2, 1})
+    if (images_smem(K, L, P, rb) <= kPowKSmemLimit / 2 && 2 * P * L <= 512) return P;
   for (int P : {8, 4, 2, 1})
     if (images_smem(K, L, P, rb) <= kPowKSmemLimit && 2 * P * L <= 512) return P;
   return 0;
 }
 
 struct PowKLayout {
-  size_t W, cx, cy, rowsum, colsum, Mx, My, total;
+  size_t W, cxh, cxl, cyh, cyl, rowsum, colsum, Mx, My, total;
 };
 
 PowKLayout powk_layout(int sx, int sy, int k, int dtype) {
@@ -340,8 +362,10 @@ PowKLayout powk_layout(int sx, int sy, int k, int dtype) {
     return o;
   };
   l.W = take(n * m * rb);
-  l.cx = take(n * 8);
-  l.cy = take(m * 8);
+  l.cxh = take(n * rb);
+  l.cxl = take(n * rb);
+  l.cyh = take(m * rb);
+  l.cyl = take(m * rb);
   l.rowsum = take(n * 8);
   l.colsum = take(m * 8);
   l.Mx = take((size_t)(2 * k + 1) * n * 8);
@@ -357,8 +381,6 @@ int powk_typed(const Grad2DArgs& A, char* ws) {
   const int n = sx * sx, m = sy * sy;
   const size_t rb = sizeof(Real);
   const PowKLayout lay = powk_layout(sx, sy, K, A.dtype);
-  double* cx = (double*)(ws + lay.cx);
-  double* cy = (double*)(ws + lay.cy);
   double* rowsum = (double*)(ws + lay.rowsum);
   double* colsum = (double*)(ws + lay.colsum);
 
@@ -370,7 +392,7 @@ int powk_typed(const Grad2DArgs& A, char* ws) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
     const int grid = std::max(1, std::min(n, std::max(1, per_sm) * A.num_sms));
-    PowKIO io{A.T, ws + lay.W, n, m, sy, 1, A.exact ? rowsum : nullptr, nullptr, nullptr, 0.0};
+    PowKIO io{A.T, ws + lay.W, n, m, sy, 1, A.exact ? rowsum : nullptr, nullptr, nullptr, nullptr, nullptr, 0.0};
     TraceScope ts(A.tracer, "g2k_rows", st);
     kern<<<grid, 256, smem, st>>>(io);
   }
@@ -391,10 +413,11 @@ int powk_typed(const Grad2DArgs& A, char* ws) {
     TraceScope ts(A.tracer, "g2k_const", st);
     const int P2 = 2 * K;
     const int pad1 = ((P2 + 1) * n + 255) / 256 * 256, pad2 = (n + 255) / 256 * 256;
-    ConstJob jx{wx, sx, (double*)(ws + lay.Mx), cx, std::pow(A.hx, 2 * K) * A.out_scale, pad1, pad2};
-    ConstJob jy{wy, sy, (double*)(ws + lay.My), cy, std::pow(A.hy, 2 * K) * A.out_scale, 0, 0};
+    ConstJob jx{wx, sx, (double*)(ws + lay.Mx), ws + lay.cxh, ws + lay.cxl, std::pow(A.hx, 2 * K) * A.out_scale,
+                pad1, pad2};
+    ConstJob jy{wy, sy, (double*)(ws + lay.My), ws + lay.cyh, ws + lay.cyl, std::pow(A.hy, 2 * K) * A.out_scale, 0, 0};
     g2k_const1<<<(pad1 + (P2 + 1) * m + 255) / 256, 256, 0, st>>>(jx, jy, P2);
-    g2k_const2<<<(pad2 + m + 255) / 256, 256, 0, st>>>(jx, jy, P2);
+    g2k_const2<Real><<<(pad2 + m + 255) / 256, 256, 0, st>>>(jx, jy, P2);
   }
   // Pass 2 with the epilogue.
   {
@@ -408,7 +431,7 @@ int powk_typed(const Grad2DArgs& A, char* ws) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     const int tiles = (m + P - 1) / P;
     const int grid = std::max(1, std::min(tiles, std::max(1, per_sm) * A.num_sms));
-    PowKIO io{ws + lay.W, A.G, n, m, sx, P, nullptr, cx, cy,
+    PowKIO io{ws + lay.W, A.G, n, m, sx, P, nullptr, ws + lay.cxh, ws + lay.cxl, ws + lay.cyh, ws + lay.cyl,
               2.0 * std::pow(A.hx, K) * std::pow(A.hy, K) * A.out_scale};
     TraceScope ts(A.tracer, "g2k_cols", st);
     kern<<<grid, threads, smem, st>>>(io);
