@@ -250,6 +250,34 @@ bool encode_rows_tmap(void* tmap, const void* base, int n, int m, int elem_bytes
   return r == CUDA_SUCCESS;
 }
 
+bool encode_rows_tmap_box(void* tmap, const void* base, int n, int m, int elem_bytes, int box_cols) {
+  // Same shape as encode_rows_tmap ({128-byte chunk, chunks per row, rows},
+  // 128-byte swizzle) with a given box height, for tensor stores.
+  int dummy = 0;
+  if (!encode_rows_tmap(tmap, base, n, m, elem_bytes, &dummy)) return false;  // checks shape and driver
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &qr) == cudaSuccess &&
+        qr == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+    else
+      cudaGetLastError();
+  });
+  const int E = 128 / elem_bytes;
+  if (!fn || box_cols < 1 || box_cols > 256 || box_cols > m / E) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)E, (cuuint64_t)(m / E), (cuuint64_t)n};
+  cuuint64_t strides[2] = {128, (cuuint64_t)m * (cuuint64_t)elem_bytes};
+  cuuint32_t box[3] = {(cuuint32_t)E, (cuuint32_t)box_cols, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = fn((CUtensorMap*)tmap, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                  3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 namespace {
 thread_local char g_failure[256] = "";
 }

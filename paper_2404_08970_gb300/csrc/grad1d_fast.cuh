@@ -57,7 +57,8 @@ struct FastSmem {
 
 template <int K, int NW, int VPT, typename Real>
 __global__ void __launch_bounds__(32 * (NW + 1), 1)
-    k1c_fast_rows(const __grid_constant__ CUtensorMap tmT, const Real* __restrict__ T, Real* __restrict__ G, int n,
+    k1c_fast_rows(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmG,
+                  int use_tma_store, const Real* __restrict__ T, Real* __restrict__ G, int n,
                   int m, int R, const Real* __restrict__ q, const Real* __restrict__ cxh,
                   const Real* __restrict__ cxl, const Real* __restrict__ cyh, const Real* __restrict__ cyl, Real scale,
                   int use_tma, int stages, int slot_bytes, int vec_bytes, int box_cols, int ncopies,
@@ -353,6 +354,12 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
 #pragma unroll
       for (int e = 1; e <= K; ++e) LC[e] = -scale * ZT[e];
       const Real cks = -scale * CK;
+      // The staging segment is free once the previous row's tensor store has
+      // read it.
+      if (use_tma_store) {
+        if (lane == 0) bulk_wait_read();
+        __syncwarp();
+      }
       // Four (float) or two (double) columns at a time: their constant term
       // from swizzled shared memory, the outputs into the warp's staging
       // segment at the same swizzled offsets.
@@ -386,27 +393,38 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
         for (int w = 0; w < PER; ++w) op[w] = out[w];
         *reinterpret_cast<float4*>(stg + swz128(b)) = ov;
       }
-      __syncwarp();
-      // Store pass: lane `lane` takes the 16 bytes at lane * 16 of each
-      // 512-byte piece of the warp's segment.
-      Real* grow = G + (size_t)i * m;
-      const bool row_vec = ((((uintptr_t)grow) & 15) == 0);
-#pragma unroll 2
-      for (int j = 0; j < VPT / PER; ++j) {
-        const int col = warp * SEG + (j * 32 + lane) * PER;
-        const float4 ov = *reinterpret_cast<const float4*>(stg + swz128((uint32_t)(col * sizeof(Real))));
-        if (row_vec && col + PER <= m) {
-          *reinterpret_cast<float4*>(grow + col) = ov;
-        } else {
-          const Real* op = reinterpret_cast<const Real*>(&ov);
-#pragma unroll
-          for (int w = 0; w < PER; ++w)
-            if (col + w < m) grow[col + w] = op[w];
+      if (use_tma_store) {
+        // One tensor store of the warp's segment (the tensor map's 128-byte
+        // swizzle matches the staging layout; columns past m are clipped).
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0 && warp * SEG < m) {
+          tma_store_3d(&tmG, 0, warp * (SEG * (int)sizeof(Real) / 128), i, stg + (size_t)warp * SEG * sizeof(Real));
+          bulk_commit();
         }
+      } else {
+        __syncwarp();
+        // Store pass: lane `lane` takes the 16 bytes at lane * 16 of each
+        // 512-byte piece of the warp's segment.
+        Real* grow = G + (size_t)i * m;
+        const bool row_vec = ((((uintptr_t)grow) & 15) == 0);
+#pragma unroll 2
+        for (int j = 0; j < VPT / PER; ++j) {
+          const int col = warp * SEG + (j * 32 + lane) * PER;
+          const float4 ov = *reinterpret_cast<const float4*>(stg + swz128((uint32_t)(col * sizeof(Real))));
+          if (row_vec && col + PER <= m) {
+            *reinterpret_cast<float4*>(grow + col) = ov;
+          } else {
+            const Real* op = reinterpret_cast<const Real*>(&ov);
+#pragma unroll
+            for (int w = 0; w < PER; ++w)
+              if (col + w < m) grow[col + w] = op[w];
+          }
+        }
+        // The next row's outputs overwrite the segment only after every lane
+        // has read it.
+        __syncwarp();
       }
-      // The next row's outputs overwrite the segment only after every lane
-      // has read it.
-      __syncwarp();
     }
     if (t < Ra) {
       if constexpr (FL_SMEM) {
@@ -428,6 +446,8 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
       cxl_prev = cxl_new;
     }
   }
+  // The last tensor stores complete before the block's shared memory goes.
+  if (use_tma_store && lane == 0) bulk_wait_all();
 }
 
 }  // namespace gw

@@ -31,6 +31,7 @@
 
 #include "gw_common.cuh"
 #include "gw_internal.h"
+#include "gw_tma.cuh"
 
 namespace gw {
 
@@ -259,6 +260,90 @@ __global__ void __launch_bounds__(1024) k1a_band_moments(const Real* __restrict_
         for (int r = 0; r < K; ++r) base[(size_t)(r + 2) * m] = mr[g][r][v];
       }
     }
+}
+
+// ---------------------------------------------------------------------------
+// k1a, streamed form (float, target marginals, m a multiple of 32 up to 8192):
+// the band's rows come into a shared-memory ring of kA_STAGES whole rows by
+// TMA tensor copies (128-byte swizzle), bottom-up like k1a_band_moments, so
+// the loads in flight no longer depend on registers.  Thread t owns the 8
+// consecutive columns 8t .. 8t+7.  Same moments and layout as
+// k1a_band_moments.
+// ---------------------------------------------------------------------------
+constexpr int kA_STAGES = 4;
+constexpr int kA_VPT = 8;
+
+template <int K>
+__global__ void __launch_bounds__(1024, 1)
+    k1a_band_moments_tma(const __grid_constant__ CUtensorMap tmT, int n, int m, int R, int slot_bytes,
+                         int box_cols, int ncopies, float* __restrict__ mu, unsigned* status) {
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  unsigned char* ring = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)kA_STAGES * slot_bytes);
+  const int a = blockIdx.x;
+  const int s = a * R;
+  const int Ra = min(R, n - s);
+  const int tid = threadIdx.x;
+  const int c0 = tid * kA_VPT;
+  auto issue = [&](int j) {  // j-th row from the bottom of the band
+    const int slot = j % kA_STAGES;
+    mbar_arrive_expect_tx(&bars[slot], (unsigned)(m * sizeof(float)));
+    for (int c = 0; c < ncopies; ++c)
+      tma_load_3d(ring + (size_t)slot * slot_bytes + (size_t)c * box_cols * 128, &tmT, 0, c * box_cols,
+                  s + Ra - 1 - j, &bars[slot]);
+  };
+  if (tid == 0) {
+    for (int st = 0; st < kA_STAGES; ++st) mbar_init(&bars[st], 1);
+    fence_mbar_init();
+    for (int j = 0; j < kA_STAGES && j < Ra; ++j) issue(j);
+  }
+  __syncthreads();
+  float m0[kA_VPT], c0k[kA_VPT], mr[K][kA_VPT];
+#pragma unroll
+  for (int v = 0; v < kA_VPT; ++v) {
+    m0[v] = 0.f;
+    c0k[v] = 0.f;
+#pragma unroll
+    for (int r = 0; r < K; ++r) mr[r][v] = 0.f;
+  }
+  const bool active = c0 < m;
+  for (int j = 0; j < Ra; ++j) {
+    const int slot = j % kA_STAGES;
+    mbar_wait_bounded(&bars[slot], (unsigned)((j / kA_STAGES) & 1), status);
+    if (active) {
+      float x[kA_VPT];
+      lds_swz<float, kA_VPT>(ring + (size_t)slot * slot_bytes, c0, x);
+      const float tr = (float)(Ra - 1 - j);
+#pragma unroll
+      for (int v = 0; v < kA_VPT; ++v) {
+        kahan_add(m0[v], c0k[v], x[v]);
+        float tp = tr;
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+          mr[r][v] = fmaf(tp, x[v], mr[r][v]);
+          tp *= tr;
+        }
+      }
+    }
+    __syncthreads();  // every thread has read the slot
+    if (tid == 0 && j + kA_STAGES < Ra) {
+      fence_proxy_async_smem();
+      issue(j + kA_STAGES);
+    }
+  }
+  if (!active) return;
+  float* base = mu + (size_t)a * (K + 2) * m + c0;
+  auto put = [&](float* dst, const float (&v)[kA_VPT]) {
+    *reinterpret_cast<float4*>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+    *reinterpret_cast<float4*>(dst + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  };
+  float negc[kA_VPT];
+#pragma unroll
+  for (int v = 0; v < kA_VPT; ++v) negc[v] = -c0k[v];
+  put(base, m0);
+  put(base + (size_t)m, negc);
+#pragma unroll
+  for (int r = 0; r < K; ++r) put(base + (size_t)(r + 2) * m, mr[r]);
 }
 
 // ---------------------------------------------------------------------------
@@ -769,10 +854,19 @@ int launch_k1c(const Grad1DArgs& g, const K1Layout& L, char* ws, int use_tma, cu
 
 template <int K, int NW, int VPT, typename Real>
 int launch_k1c_fast(const Grad1DArgs& g, const K1Layout& L, char* ws, cudaStream_t st) {
-  CUtensorMap tm;
+  CUtensorMap tm, tmg;
   memset(&tm, 0, sizeof tm);
+  memset(&tmg, 0, sizeof tmg);
   int box_cols = 0;
   const int use_tma = ((((uintptr_t)g.T) & 15) == 0) && encode_rows_tmap(&tm, g.T, g.n, g.m, sizeof(Real), &box_cols);
+  // G leaves by one tensor store per warp segment (32 VPT reals) when its
+  // rows fit the same 128-byte-chunk tensor shape.
+  const int seg_chunks = 32 * VPT * (int)sizeof(Real) / 128;
+  // The segments must start on 1024-byte boundaries of the staging buffer so
+  // that the swizzle pattern (address bits 4-9) is the staging layout's.
+  const int use_tma_store = use_tma && seg_chunks % 8 == 0 && ((((uintptr_t)g.G) & 15) == 0) &&
+                            (g.m * (int)sizeof(Real)) % 128 == 0 &&
+                            encode_rows_tmap_box(&tmg, g.G, g.n, g.m, sizeof(Real), std::min(seg_chunks, g.m * (int)sizeof(Real) / 128));
   const int cover = 32 * NW * VPT;
   const int vec_bytes = (int)align_up((size_t)cover * sizeof(Real), 1024);
   const int slot_bytes = vec_bytes;
@@ -787,7 +881,8 @@ int launch_k1c_fast(const Grad1DArgs& g, const K1Layout& L, char* ws, cudaStream
   const Real scale = (Real)(2.0 * g.out_scale * std::pow(g.hx, g.k) * std::pow(g.hy, g.k));
   const Real* cx = (const Real*)(ws + L.cx_off);
   const Real* cy = (const Real*)(ws + L.cy_off);
-  kern<<<L.bands.B, 32 * (NW + 1), smem, st>>>(tm, (const Real*)g.T, (Real*)g.G, g.n, g.m, L.bands.R,
+  kern<<<L.bands.B, 32 * (NW + 1), smem, st>>>(tm, tmg, use_tma_store, (const Real*)g.T, (Real*)g.G, g.n, g.m,
+                                                L.bands.R,
                                                 (const Real*)(ws + L.q_off), cx, cx + g.n, cy, cy + g.m, scale,
                                                 use_tma, stages, slot_bytes, vec_bytes, box_cols, 1, g.status);
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
@@ -831,7 +926,29 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
   int vec_used = 1;
   {
     TraceScope ts(g.tracer, "k1a_band_moments", st);
+    bool done = false;
     if constexpr (sizeof(Real) == 4) {
+      // Streamed form: target marginals (no row partials), m a multiple of 32
+      // up to 1024 threads x 8 columns, a row tensor map for T.
+      if (!g.exact && m % 32 == 0 && m <= 1024 * kA_VPT && vec_ok) {
+        CUtensorMap tm;
+        memset(&tm, 0, sizeof tm);
+        int box_cols = 0;
+        if (encode_rows_tmap(&tm, g.T, n, m, 4, &box_cols)) {
+          const int slot_bytes = (int)align_up((size_t)m * 4, 1024);
+          const size_t smem = 1024 + (size_t)kA_STAGES * slot_bytes + 8 * kA_STAGES;
+          auto kern = k1a_band_moments_tma<K>;
+          if (allow_dynamic_smem((const void*)kern, smem)) {
+            const int nt = std::max(32, (m / kA_VPT + 31) / 32 * 32);
+            kern<<<B, nt, smem, st>>>(tm, n, m, R, slot_bytes, box_cols, (m / 32) / box_cols, (float*)mu,
+                                      g.status);
+            done = true;
+          }
+        }
+      }
+    }
+    if (done) {
+    } else if constexpr (sizeof(Real) == 4) {
       if (vec_ok) {
         vec_used = 4;
         if (m <= 4096) launch_k1a<K, Real, 4, 1>(g, B, R, mu, rowpart, st);

@@ -95,6 +95,7 @@ bool allow_dynamic_smem(const void* func, size_t need);
 // m / E up to 256.  False if m is not a multiple of E or the driver rejects
 // the map.
 bool encode_rows_tmap(void* tmap, const void* base, int n, int m, int elem_bytes, int* box_cols);
+bool encode_rows_tmap_box(void* tmap, const void* base, int n, int m, int elem_bytes, int box_cols);
 
 // Bytes of workspace the structured 1D gradient needs.
 size_t grad1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms);

@@ -25,6 +25,19 @@ __device__ __forceinline__ void tma_load_3d(void* dst_smem, const CUtensorMap* t
       : "memory");
 }
 
+// Shared -> global tensor store of one box (bulk async-group completion).
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* tm, int c0, int c1, int c2, const void* src_smem) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(tm), "r"(c0),
+               "r"(c1), "r"(c2), "r"(smem_u32(src_smem))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// Waits until the shared-memory sources of this thread's committed bulk
+// stores have been read (they may be overwritten afterwards).
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Waits until this thread's committed bulk stores have completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 template <typename Real, int VPT>
 __device__ __forceinline__ void lds_swz(const unsigned char* base, int c0, Real (&out)[VPT]) {
   constexpr int PER = 16 / sizeof(Real);
