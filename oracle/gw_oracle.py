@@ -22,7 +22,11 @@ direct, each function citing the part of the paper it follows:
   warm-started Sinkhorn solves, including the fused-GW cost (Remark "FGW"),
 * the paper's O(N) recursion for y = L x (Sec. 3, eqs. "1d y" and "1d
   recursive relation"), kept here as an independently pinned statement of
-  the method's core step.
+  the method's core step,
+* entropic unbalanced GW (Remark "Entropic algorithm for UGW"): its
+  objective, the step cost (1/2) grad E plus the scalar g, log-domain
+  unbalanced Sinkhorn with KL-relaxed marginals, and the alternate
+  minimisation with mass rescaling.
 
 Parity pins for every function live in tests/test_oracle_*.py.
 """
@@ -308,3 +312,83 @@ def fgc_grad_1d(T: np.ndarray, hx: float, hy: float, k: int,
     DXsq = grid_dist_1d(n, hx, k) ** 2
     DYsq = grid_dist_1d(m, hy, k) ** 2
     return (DXsq @ r)[:, None] + (DYsq @ c)[None, :] - 2.0 * (hx ** k) * (hy ** k) * Z
+
+
+# ---------------------------------------------------------------------------
+# Unbalanced GW (Sec. 2.1, Remark "Entropic algorithm for UGW")
+# ---------------------------------------------------------------------------
+
+
+def kl(a: np.ndarray, b: np.ndarray) -> float:
+    """KL(a|b) = sum a ln(a/b) - sum a + sum b for positive measures (0 ln 0 = 0)."""
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    pos = a > 0
+    return float(np.sum(a[pos] * np.log(a[pos] / b[pos])) - a.sum() + b.sum())
+
+
+def kl_tensor(a: np.ndarray, b: np.ndarray) -> float:
+    """KL(a (x) a | b (x) b) of the tensor-product measures, written out:
+    2 m(a) sum a ln(a/b) - m(a)^2 + m(b)^2."""
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    pos = a > 0
+    return float(2.0 * a.sum() * np.sum(a[pos] * np.log(a[pos] / b[pos])) - a.sum() ** 2 + b.sum() ** 2)
+
+
+def ugw_value(DX, DY, T, u, v, rho: float, eps: float) -> float:
+    """The entropic UGW objective of the Remark:
+    E(T) + rho KLx(T 1 | u) + rho KLx(T^T 1 | v) + eps KLx(T | u v^T),
+    KLx the KL of tensor products (kl_tensor)."""
+    return (value(DX, DY, T) + rho * kl_tensor(T.sum(axis=1), u) + rho * kl_tensor(T.sum(axis=0), v)
+            + eps * kl_tensor(T, np.outer(u, v)))
+
+
+def ugw_cost(DX, DY, Th, u, v, rho: float, eps: float) -> np.ndarray:
+    """Cost of one UGW step at the current plan Th: (1/2) grad E(Th) = the
+    gradient with Th's own marginals, plus the scalar g(Th) = rho KL(Th 1|u)'
+    + ... written as the three KL divergences' first-order terms:
+      g = rho sum_j r_j ln(r_j/u_j) + rho sum_q c_q ln(c_q/v_q)
+          + eps sum_jq Th_jq ln(Th_jq/(u_j v_q)),
+    r = Th 1, c = Th^T 1."""
+    r, c = Th.sum(axis=1), Th.sum(axis=0)
+    g = (rho * float(np.sum(r * np.log(r / u))) + rho * float(np.sum(c * np.log(c / v)))
+         + eps * float(np.sum(Th * np.log(Th / np.outer(u, v)))))
+    return grad_exact(DX, DY, Th) + g
+
+
+def sinkhorn_unbalanced(C: np.ndarray, u: np.ndarray, v: np.ndarray, eps: float, rho: float,
+                        n_iter: int):
+    """min <C, T> + rho KL(T 1|u) + rho KL(T^T 1|v) + eps KL(T|u v^T) in the log
+    domain, from f = g = 0, f then g each iteration:
+      f_i = -(rho/(rho+eps)) eps LSE_p((g_p - C_ip)/eps + ln v_p)
+      g_p = -(rho/(rho+eps)) eps LSE_i((f_i - C_ip)/eps + ln u_i)
+    and the plan T_ip = exp((f_i + g_p - C_ip)/eps) u_i v_p."""
+    n, m = C.shape
+    f = np.zeros(n)
+    g = np.zeros(m)
+    kappa = rho / (rho + eps)
+    lu, lv = np.log(u), np.log(v)
+    for _ in range(n_iter):
+        f = -kappa * eps * _lse((g[None, :] - C) / eps + lv[None, :], axis=1)
+        g = -kappa * eps * _lse((f[:, None] - C) / eps + lu[:, None], axis=0)
+    T = np.exp((f[:, None] + g[None, :] - C) / eps) * np.outer(u, v)
+    return T, f, g
+
+
+def ugw_solve(DX, DY, u, v, eps: float, rho: float, n_outer: int, n_inner: int):
+    """Entropic UGW by the alternate minimisation the Remark describes: at the
+    current plan Th (mass m = sum Th), solve the unbalanced entropic OT
+    problem with cost ugw_cost(Th) and penalties scaled by m, i.e. with cost
+    C / m and the fixed eps, rho; then rescale the new plan to mass
+    sqrt(m(Th) m(T)) (T <- sqrt(m(Th)/m(T)) T).  T starts at
+    u v^T / sqrt(m(u) m(v)).  Returns (T, f, g) of the last step."""
+    T = np.outer(u, v) / math.sqrt(u.sum() * v.sum())
+    f = np.zeros(u.size)
+    g = np.zeros(v.size)
+    for _ in range(n_outer):
+        mh = float(T.sum())
+        C = ugw_cost(DX, DY, T, u, v, rho, eps) / mh
+        Tn, f, g = sinkhorn_unbalanced(C, u, v, eps, rho, n_inner)
+        T = math.sqrt(mh / float(Tn.sum())) * Tn
+    return T, f, g

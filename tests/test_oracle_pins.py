@@ -589,3 +589,117 @@ def test_warm_start_converged_inner_loop_matches_cold():
     Tc, _, _ = O.mirror_descent(DX, DY, u, v, 0.1, 5, 2000)
     Tw, _, _ = O.mirror_descent(DX, DY, u, v, 0.1, 5, 2000, warm_start=True)
     assert relerr(Tw, Tc) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Unbalanced GW (Remark "Entropic algorithm for UGW")
+# ---------------------------------------------------------------------------
+
+def _ugw_problem(n=9, m=7, seed=3, mass_u=1.3, mass_v=0.8):
+    rng = np.random.default_rng(seed)
+    u, v = I.dirichlet(n, 1.0, rng) * mass_u, I.dirichlet(m, 1.0, rng) * mass_v
+    return u, v, O.grid_dist_1d(n, 1.0 / n, 1), O.grid_dist_1d(m, 1.0 / m, 1)
+
+
+def test_kl_tensor_is_kl_of_products():
+    """KL(a (x) a | b (x) b) summed over all pairs equals the closed form."""
+    rng = np.random.default_rng(61)
+    a, b = rng.uniform(0.1, 1.0, 5), rng.uniform(0.1, 1.0, 5)
+    brute = sum(a[i] * a[j] * math.log(a[i] * a[j] / (b[i] * b[j])) - a[i] * a[j] + b[i] * b[j]
+                for i in range(5) for j in range(5))
+    assert abs(O.kl_tensor(a, b) - brute) < 1e-13
+    assert abs(O.kl(a, b) - sum(a[i] * math.log(a[i] / b[i]) - a[i] + b[i] for i in range(5))) < 1e-14
+
+
+def test_ugw_value_brute_force():
+    """The objective of the Remark summed term by term over (i, j, p, q)."""
+    u, v, DX, DY = _ugw_problem(4, 3, 62)
+    rng = np.random.default_rng(63)
+    T = rng.uniform(0.01, 0.2, size=(4, 3))
+    rho, eps = 0.7, 0.05
+    r, c = T.sum(axis=1), T.sum(axis=0)
+    E = sum((DX[i, j] - DY[p, q]) ** 2 * T[i, p] * T[j, q]
+            for i in range(4) for j in range(4) for p in range(3) for q in range(3))
+    klx = lambda a, b: sum(a[i] * a[j] * math.log(a[i] * a[j] / (b[i] * b[j])) - a[i] * a[j] + b[i] * b[j]
+                           for i in range(len(a)) for j in range(len(a)))
+    uv = np.outer(u, v).ravel()
+    want = E + rho * klx(r, u) + rho * klx(c, v) + eps * klx(T.ravel(), uv)
+    assert abs(O.ugw_value(DX, DY, T, u, v, rho, eps) - want) <= 1e-12 * abs(want)
+
+
+def test_unbalanced_sinkhorn_kkt():
+    """At convergence the relaxed-marginal conditions hold:
+    T 1 = u exp(-f / rho) and T^T 1 = v exp(-g / rho)."""
+    u, v, _, _ = _ugw_problem(8, 6, 64)
+    C = np.random.default_rng(65).uniform(0.0, 1.0, size=(8, 6))
+    rho, eps = 0.4, 0.1
+    T, f, g = O.sinkhorn_unbalanced(C, u, v, eps, rho, 3000)
+    assert relerr(T.sum(axis=1), u * np.exp(-f / rho)) < 1e-10
+    assert relerr(T.sum(axis=0), v * np.exp(-g / rho)) < 1e-10
+
+
+def test_ugw_large_rho_is_balanced_gw():
+    """rho -> infinity with unit-mass marginals: the marginal penalties become
+    constraints and each step is the balanced entropic step with cost
+    (1/2) grad E (mirror descent with grad_scale = 1)."""
+    u, v, DX, DY = _ugw_problem(mass_u=1.0, mass_v=1.0)
+    Tu, _, _ = O.ugw_solve(DX, DY, u, v, 0.05, 1e7, 5, 100)
+    Tb, _, _ = O.mirror_descent(DX, DY, u, v, 0.05, 5, 100, grad_scale=1.0)
+    assert relerr(Tu, Tb) < 1e-7
+
+
+def test_ugw_stationarity_and_monotone_objective():
+    """The UGW objective decreases step by step, and the limit is a
+    stationary point of the objective: with a = T 1, b = T^T 1, m = sum T,
+    setting the derivative of E + rho KLx + rho KLx + eps KLx to zero gives
+      G(T)_ip + g(T) + m [rho ln(a_i/u_i) + rho ln(b_p/v_p) + eps ln(T_ip/(u_i v_p))] = 0
+    with G the gradient with T's marginals and g the scalar of ugw_cost."""
+    u, v, DX, DY = _ugw_problem()
+    rho, eps = 0.5, 0.05
+    vals = []
+    T = np.outer(u, v) / math.sqrt(u.sum() * v.sum())
+    for _ in range(400):
+        vals.append(O.ugw_value(DX, DY, T, u, v, rho, eps))
+        mh = float(T.sum())
+        Tn, _, _ = O.sinkhorn_unbalanced(O.ugw_cost(DX, DY, T, u, v, rho, eps) / mh, u, v, eps, rho, 500)
+        T = math.sqrt(mh / float(Tn.sum())) * Tn
+    assert np.all(np.diff(vals) <= 1e-12)
+    a, b, m = T.sum(axis=1), T.sum(axis=0), float(T.sum())
+    gsc = rho * np.sum(a * np.log(a / u)) + rho * np.sum(b * np.log(b / v)) + eps * np.sum(T * np.log(T / np.outer(u, v)))
+    res = (O.grad_exact(DX, DY, T) + gsc
+           + m * (rho * np.log(a / u)[:, None] + rho * np.log(b / v)[None, :] + eps * np.log(T / np.outer(u, v))))
+    assert np.max(np.abs(res)) < 1e-8
+    # The solver's own loop is the same iteration.
+    T2, _, _ = O.ugw_solve(DX, DY, u, v, eps, rho, 400, 500)
+    assert relerr(T2, T) < 1e-12
+
+
+def test_ugw_planted_mistakes():
+    """A flipped sign of the scalar g or a missing rho/(rho+eps) factor makes
+    the objective increase."""
+    u, v, DX, DY = _ugw_problem()
+    rho, eps = 0.5, 0.05
+
+    def run(gsign, kappa_rho):
+        T = np.outer(u, v) / math.sqrt(u.sum() * v.sum())
+        vals = [O.ugw_value(DX, DY, T, u, v, rho, eps)]
+        for _ in range(15):
+            mh = float(T.sum())
+            a, b = T.sum(axis=1), T.sum(axis=0)
+            g = rho * np.sum(a * np.log(a / u)) + rho * np.sum(b * np.log(b / v)) + eps * np.sum(T * np.log(T / np.outer(u, v)))
+            C = (O.grad_exact(DX, DY, T) + gsign * g) / mh
+            Tn, _, _ = O.sinkhorn_unbalanced(C, u, v, eps, kappa_rho, 500)
+            T = math.sqrt(mh / float(Tn.sum())) * Tn
+            vals.append(O.ugw_value(DX, DY, T, u, v, rho, eps))
+        return np.max(np.diff(vals))
+
+    assert run(1.0, rho) <= 1e-12
+    assert run(-1.0, rho) > 1e-4
+    assert run(1.0, 1e12) > 1e-4
+
+
+def test_ugw_reflection():
+    u, v, DX, DY = _ugw_problem(8, 6, 66)
+    T, _, _ = O.ugw_solve(DX, DY, u, v, 0.05, 0.5, 5, 50)
+    Tr, _, _ = O.ugw_solve(DX, DY, u, v[::-1].copy(), 0.05, 0.5, 5, 50)
+    assert relerr(Tr[:, ::-1], T) < 1e-11
