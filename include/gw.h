@@ -92,6 +92,9 @@ typedef struct gw_problem {
   int warm_start; /* solver only: 1 starts each mirror-descent step's Sinkhorn
                     iteration from the previous step's potentials, 0 from
                     f = g = 0 */
+  double rho;    /* solver only: 0 for balanced (F)GW; > 0 solves entropic
+                    unbalanced GW with marginal relaxation rho (Remark
+                    "Entropic algorithm for UGW") */
 } gw_problem;
 
 typedef struct gw_ctx gw_ctx;
@@ -251,7 +254,8 @@ gw_status gw_grad_dense(gw_ctx* ctx, const gw_problem* prob, const double* d_u, 
  * T_ip = exp((f_i + g_p - Pi_ip) / tau).
  *
  *   prob         dim 1 or 2; nx, ny, hx, hy, k, cost as for gw_grad, with at
- *                most 16384 points in Y (ny, or ny^2 in 2D); eps > 0;
+ *                most 16384 points in Y (ny, or ny^2 in 2D; 10240 with
+ *                GW_F64); eps > 0;
  *                tau = 0 (tau = eps) or > 0; warm_start 0 or 1;
  *                n_outer >= 0; n_inner >= 1; theta in [0, 1]; feat_dim in
  *                [1, 64] when theta < 1; dtype GW_F32 or GW_F64 (the

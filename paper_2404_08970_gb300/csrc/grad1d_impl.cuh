@@ -10,7 +10,8 @@
 // GB300 layout of the work (one read of T for the band statistics, one read
 // of T and one write of G for the output):
 //   k1a  per row band a (rows s_a .. s_a+R_a-1) and column p, the band
-//        moments mu_r = sum_t t^r T[s_a+t, p]  (mu_0 compensated).
+//        moments about the band's end nu_r = sum_t (R_a - t)^r T[s_a+t, p]
+//        (nu_0 compensated).
 //   k1b  per column, scans the band moments in float-float across bands and
 //        turns them into, for every band, a degree-k polynomial Q_a,p(t) with
 //        Q(t) = sum_{j < s_a} (i-j)^k x_j + sum_{j >= s_a} (j-i)^k x_j,
@@ -149,8 +150,9 @@ __device__ __forceinline__ void shift_acc_pow2(A (&S)[K + 1], Real d) {
 // owns CPT groups of VEC consecutive columns, group g starting at column
 // (g*NT + t)*VEC.  Rows are read bottom-up so that the rows the main kernel
 // reads first (each band's top rows) are the most recently cached in L2.
-// mu layout [band][K+2][m]: slot 0 = mu_0, slot 1 = its compensation (true
-// mu_0 = slot0 + slot1), slots 2.. = mu_1..mu_K, mu_r = sum_t t^r T[s_a+t, p].
+// mu layout [band][K+2][m]: slot 0 = nu_0, slot 1 = its compensation (true
+// nu_0 = slot0 + slot1), slots 2.. = nu_1..nu_K,
+// nu_r = sum_t (R_a - t)^r T[s_a+t, p] (moments about the band's end).
 // rowpart (exact marginals only) layout [wchunk][n][2]: (hi, lo) partial row
 // sums over the 32*VEC columns of warp-chunk wchunk = g*(NT/32) + warp.
 // ---------------------------------------------------------------------------
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(1024) k1a_band_moments(const Real* __restrict_
         for (int v = 0; v < VEC; ++v) x[g][v] = (p0 + v < m) ? __ldg(row + p0 + v) : (Real)0;
       }
     }
-    const Real tr = (Real)t;
+    const Real tr = (Real)(Ra - t);
 #pragma unroll
     for (int g = 0; g < CPT; ++g)
 #pragma unroll
@@ -313,7 +315,7 @@ __global__ void __launch_bounds__(1024, 1)
     if (active) {
       float x[kA_VPT];
       lds_swz<float, kA_VPT>(ring + (size_t)slot * slot_bytes, c0, x);
-      const float tr = (float)(Ra - 1 - j);
+      const float tr = (float)(j + 1);  // R_a - t for row t = R_a - 1 - j
 #pragma unroll
       for (int v = 0; v < kA_VPT; ++v) {
         kahan_add(m0[v], c0k[v], x[v]);
@@ -352,11 +354,11 @@ __global__ void __launch_bounds__(1024, 1)
 //   Bk_r(a) = sum_{j >= s_a} (j - s_a)^r x_j     (from the band start on)
 //   q_e(a)  = C(K, K-e) [A_{K-e}(a) + (-1)^e Bk_{K-e}(a)],  Q(t) = sum_e q_e t^e
 // in one kernel, all in float-float (double for double data).  A block
-// covers 32 columns (one per lane); its 8 warps split the bands into 8
-// consecutive groups:
+// covers 32 columns (one per lane); its kGroups warps split the bands into
+// kGroups consecutive groups:
 //   1. each warp: its group's moments about the group's end;
-//   2. each warp: the exclusive prefix over the groups before it (A at its
-//      group's start) and the column's moments about row n (all groups);
+//   2. warp 0: the exclusive prefix over the groups (A at each group's start)
+//      and the column's moments about row n (all groups), via shared memory;
 //   3. each warp walks its bands with A, takes Bk from the column moments,
 //      writes q.
 // q layout [band][K+1][m].
@@ -370,28 +372,9 @@ struct K1bOps {
 #pragma unroll
     for (int r = 1; r <= K; ++r) M[r] = acc_of(base[(size_t)(r + 1) * m]);
   }
-  // End-relative band moments nu_r = sum_t (R_a - t)^r x = sum_u C(r,u) R^{r-u} (-1)^u mu_u,
-  // by Horner in R.
-  static __device__ __forceinline__ void nu_of(const A (&M)[K + 1], int Ra, A (&N)[K + 1]) {
-    using F = typename AccReal<A>::type;
-    const F rf = (F)Ra;
-    N[0] = M[0];
-#pragma unroll
-    for (int r = 1; r <= K; ++r) {
-      A acc = M[0];
-#pragma unroll
-      for (int u = 1; u <= r; ++u) {
-        acc = acc_mulf(acc, rf);
-        const int c = binom(r, u);
-        const A term = c == 1 ? M[u] : acc_mulf(M[u], (F)c);
-        acc = (u & 1) ? acc_sub(acc, term) : acc_add(acc, term);
-      }
-      N[r] = acc;
-    }
-  }
 };
 
-constexpr int kGroups = 16;
+constexpr int kGroups = 32;
 
 template <int K, typename Real>
 __global__ void __launch_bounds__(32 * kGroups) k1b_carries(const Real* __restrict__ mu, int n, int m, int R, int B,
@@ -399,7 +382,8 @@ __global__ void __launch_bounds__(32 * kGroups) k1b_carries(const Real* __restri
   using A = typename AccT<Real>::type;
   using O = K1bOps<K, Real>;
   using F = typename AccReal<A>::type;
-  __shared__ A gagg[kGroups][K + 1][32];
+  __shared__ A gagg[kGroups][K + 1][32];  // group aggregates, then exclusive prefixes
+  __shared__ A gtot[K + 1][32];           // the column's moments about row n
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int p = blockIdx.x * 32 + lane;
   const int per = (B + kGroups - 1) / kGroups;
@@ -409,7 +393,7 @@ __global__ void __launch_bounds__(32 * kGroups) k1b_carries(const Real* __restri
   };
   int a0, a1;
   group_bands(w, a0, a1);
-  A M[K + 1], N[K + 1];
+  A N[K + 1];
   // 1. group aggregate about the group's end
   A FA[K + 1];
 #pragma unroll
@@ -418,8 +402,7 @@ __global__ void __launch_bounds__(32 * kGroups) k1b_carries(const Real* __restri
 #pragma unroll 4
     for (int a = a0; a < a1; ++a) {
       const int Ra = min(R, n - a * R);
-      O::load_mu(mu, m, a, p, M);
-      O::nu_of(M, Ra, N);
+      O::load_mu(mu, m, a, p, N);  // moments about the band's end
       shift_acc<K>(FA, Ra);
 #pragma unroll
       for (int r = 0; r <= K; ++r) FA[r] = acc_add(FA[r], N[r]);
@@ -428,21 +411,35 @@ __global__ void __launch_bounds__(32 * kGroups) k1b_carries(const Real* __restri
 #pragma unroll
   for (int r = 0; r <= K; ++r) gagg[w][r][lane] = FA[r];
   __syncthreads();
-  // 2. exclusive prefix at the group start (Af) and the column total (Nt)
+  // 2. warp 0: exclusive prefixes at each group's start (in place) and the
+  // column total.
+  if (w == 0) {
+    A Nt[K + 1];
+#pragma unroll
+    for (int r = 0; r <= K; ++r) Nt[r] = acc_zero((A*)nullptr);
+    for (int g = 0; g < kGroups; ++g) {
+      int g0, g1;
+      group_bands(g, g0, g1);
+      const int L = g1 > g0 ? min(n, g1 * R) - g0 * R : 0;
+      A ag[K + 1];
+#pragma unroll
+      for (int r = 0; r <= K; ++r) {
+        ag[r] = gagg[g][r][lane];
+        gagg[g][r][lane] = Nt[r];
+      }
+      shift_acc<K>(Nt, L);
+#pragma unroll
+      for (int r = 0; r <= K; ++r) Nt[r] = acc_add(Nt[r], ag[r]);
+    }
+#pragma unroll
+    for (int r = 0; r <= K; ++r) gtot[r][lane] = Nt[r];
+  }
+  __syncthreads();
   A Nt[K + 1], Af[K + 1];
 #pragma unroll
-  for (int r = 0; r <= K; ++r) Nt[r] = acc_zero((A*)nullptr);
-  for (int g = 0; g < kGroups; ++g) {
-    if (g == w) {
-#pragma unroll
-      for (int r = 0; r <= K; ++r) Af[r] = Nt[r];
-    }
-    int g0, g1;
-    group_bands(g, g0, g1);
-    const int L = g1 > g0 ? min(n, g1 * R) - g0 * R : 0;
-    shift_acc<K>(Nt, L);
-#pragma unroll
-    for (int r = 0; r <= K; ++r) Nt[r] = acc_add(Nt[r], gagg[g][r][lane]);
+  for (int r = 0; r <= K; ++r) {
+    Nt[r] = gtot[r][lane];
+    Af[r] = gagg[w][r][lane];
   }
   if (p >= m) return;
   if (colsum && w == 0) {
@@ -478,8 +475,7 @@ __global__ void __launch_bounds__(32 * kGroups) k1b_carries(const Real* __restri
       q[((size_t)a * (K + 1) + e) * m + p] = (Real)acc_round(t);
     }
     const int Ra = min(R, n - a * R);
-    O::load_mu(mu, m, a, p, M);
-    O::nu_of(M, Ra, N);
+    O::load_mu(mu, m, a, p, N);
     shift_acc<K>(Af, Ra);
 #pragma unroll
     for (int r = 0; r <= K; ++r) Af[r] = acc_add(Af[r], N[r]);

@@ -609,6 +609,10 @@ gw_status check_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const d
   if (!(p->tau == 0.0 || finite_pos(p->tau)))
     return fail(c, GW_ERR_INVALID, "%s: tau must be 0 (tau = eps) or finite and > 0", who);
   if (p->warm_start != 0 && p->warm_start != 1) return fail(c, GW_ERR_INVALID, "%s: warm_start must be 0 or 1", who);
+  if (!(p->rho == 0.0 || finite_pos(p->rho)))
+    return fail(c, GW_ERR_INVALID, "%s: rho must be 0 (balanced) or finite and > 0", who);
+  if (p->rho > 0.0 && (p->theta != 1.0 || (p->tau != 0.0 && p->tau != p->eps)))
+    return fail(c, GW_ERR_INVALID, "%s: unbalanced GW (rho > 0) takes theta = 1 and tau = eps", who);
   if (p->n_outer < 0 || p->n_inner < 1)
     return fail(c, GW_ERR_INVALID, "%s: need n_outer >= 0 and n_inner >= 1", who);
   if (!(p->theta >= 0.0 && p->theta <= 1.0)) return fail(c, GW_ERR_INVALID, "%s: theta must be in [0, 1]", who);
@@ -618,6 +622,9 @@ gw_status check_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const d
   if (!d_u || !d_v || !d_T) return fail(c, GW_ERR_INVALID, "%s: d_u, d_v and d_T must not be NULL", who);
   if (points_y(p) > 16384)
     return fail(c, GW_ERR_INVALID, "%s: the solver takes at most 16384 points in Y (got %zu)", who, points_y(p));
+  if (p->dtype == GW_F64 && points_y(p) > gw::kMaxSolveF64Y)
+    return fail(c, GW_ERR_INVALID, "%s: double-precision solves take at most %d points in Y (got %zu)", who,
+                gw::kMaxSolveF64Y, points_y(p));
   return GW_OK;
 }
 
@@ -637,6 +644,7 @@ gw::SolveArgs solve_args(gw_ctx* c, const gw_problem* p, const double* d_u, cons
   a.eps = p->eps;
   a.tau = p->tau > 0.0 ? p->tau : p->eps;
   a.warm_start = p->warm_start;
+  a.rho = p->rho;
   a.theta = p->theta;
   a.n_outer = p->n_outer;
   a.n_inner = p->n_inner;
@@ -673,9 +681,9 @@ gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const doub
   if (s != GW_OK) return s;
   char key[512];
   snprintf(key, sizeof key,
-           "solve %d %d %d %d %d %d %.17g %.17g %.17g %.17g %.17g %d %d %d %d %p %p %p %p %p %p %p %p %p %zu", a.dim,
-           a.cost, a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.tau, a.theta, a.warm_start, a.n_outer, a.n_inner,
-           a.feat_dim,
+           "solve %d %d %d %d %d %d %.17g %.17g %.17g %.17g %.17g %.17g %d %d %d %d %p %p %p %p %p %p %p %p %p %zu",
+           a.dim, a.cost, a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.tau, a.rho, a.theta, a.warm_start, a.n_outer,
+           a.n_inner, a.feat_dim,
            (void*)a.u, (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.f, (void*)a.g, (void*)a.stats, c->ws,
            c->ws_bytes);
   return run_graph(
@@ -789,9 +797,10 @@ gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const do
     key += buf;
     for (int i = 0; i < count; ++i) {
       const gw::SolveArgs& a = args[i];
-      snprintf(buf, sizeof buf, "%d %d %d %d %d %d %.17g %.17g %.17g %.17g %.17g %d %d %d %d %p %p %p %p %p %p|",
-               a.dim, a.cost, a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.tau, a.theta, a.warm_start, a.n_outer,
-               a.n_inner, a.feat_dim, (void*)a.u, (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.stats);
+      snprintf(buf, sizeof buf,
+               "%d %d %d %d %d %d %.17g %.17g %.17g %.17g %.17g %.17g %d %d %d %d %p %p %p %p %p %p|", a.dim, a.cost,
+               a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.tau, a.rho, a.theta, a.warm_start, a.n_outer, a.n_inner,
+               a.feat_dim, (void*)a.u, (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.stats);
       key += buf;
     }
     if (!c->batch_exec || c->batch_key != key) {

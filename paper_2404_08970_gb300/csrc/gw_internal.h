@@ -121,6 +121,8 @@ int marg_const2_launch(const double* wx, int n, double fx, void* outx, const dou
 // Structured gradient on side x side grids with an axis-separable cost
 // (grad2d.cu): Manhattan with k = 1, or squared Euclidean.
 constexpr int kMax2DSide = 256;
+// Longest row a double-precision Sinkhorn pass holds in shared memory.
+constexpr int kMaxSolveF64Y = 10240;
 struct Grad2DArgs {
   int sx, sy;           // grid sides; n = sx^2 points of X, m = sy^2 points of Y
   int cost;             // GW_COST_POW (Manhattan^k) or GW_COST_SQEUCLID
@@ -184,6 +186,7 @@ struct SolveArgs {
   double hx, hy, eps, theta;
   double tau;      // Sinkhorn regularisation of each step (= eps unless set)
   int warm_start;  // 1: Sinkhorn starts from the previous step's potentials
+  double rho;      // > 0: entropic unbalanced GW with marginal relaxation rho
   int n_outer, n_inner, feat_dim;
   const double *u, *v, *phi, *psi;
   void* T;

@@ -99,6 +99,7 @@ gw::SolveArgs args_for(const gw_server* s, const gw_problem& p) {
   a.eps = p.eps;
   a.tau = p.tau > 0.0 ? p.tau : p.eps;
   a.warm_start = p.warm_start;
+  a.rho = p.rho;
   a.theta = p.theta;
   a.n_outer = p.n_outer;
   a.n_inner = p.n_inner;
@@ -320,7 +321,8 @@ gw_status gw_submit(gw_server* s, const gw_problem* p, const double* h_u, const 
   const gw_problem& q = *p;
   if ((q.dim != 1 && q.dim != 2) || q.nx < 1 || q.ny < 1 || !(q.hx > 0) || !(q.hy > 0) || q.k < 1 ||
       (q.dtype != GW_F32 && q.dtype != GW_F64) || !(q.eps > 0) || !(q.tau == 0.0 || q.tau > 0) ||
-      (q.warm_start != 0 && q.warm_start != 1) || q.n_outer < 0 || q.n_inner < 1 ||
+      (q.warm_start != 0 && q.warm_start != 1) || !(q.rho == 0.0 || q.rho > 0) ||
+      (q.rho > 0 && (q.theta != 1.0 || (q.tau != 0.0 && q.tau != q.eps))) || q.n_outer < 0 || q.n_inner < 1 ||
       !(q.theta >= 0.0 && q.theta <= 1.0))
     return GW_ERR_INVALID;
   if (q.dim == 1 && (q.k > 3 || q.ny > 16384)) return GW_ERR_INVALID;
@@ -328,7 +330,7 @@ gw_status gw_submit(gw_server* s, const gw_problem* p, const double* h_u, const 
                      q.ny > gw::kMax2DSide ||
                      (q.cost == GW_COST_POW && q.k > 1 && !gw::grad2d_powk_supported(q.nx, q.ny, q.k, q.dtype))))
     return GW_ERR_INVALID;
-  if (points_y(q) > 16384) return GW_ERR_INVALID;
+  if (points_y(q) > 16384 || (q.dtype == GW_F64 && points_y(q) > (size_t)gw::kMaxSolveF64Y)) return GW_ERR_INVALID;
   if (q.theta != 1.0 && (q.feat_dim < 1 || q.feat_dim > 64 || !h_phi || !h_psi)) return GW_ERR_INVALID;
   auto r = std::make_shared<Request>();
   r->prob = q;

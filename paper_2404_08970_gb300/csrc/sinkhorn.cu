@@ -177,6 +177,7 @@ struct SkProb {
   double* cta_stats;    // [B][2] entropy and row-error partials
   int n, m, R, B;
   Real c;
+  Real kappa;  // unbalanced GW: new potentials = kappa * balanced update (1 when balanced)
 };
 template <typename Real, int MAXP>
 struct SkBatch {
@@ -228,7 +229,7 @@ __device__ __forceinline__ void group_sync(int g) {
 // across the group barrier.
 template <int NW, int VPT, typename Real>
 __device__ __forceinline__ Real row_redo(const Real* row, int gt, int g, int m, Real c, const Real (&Gv)[VPT],
-                                         Real Fo, Real lut, Real (&acc)[VPT], Real* sfb) {
+                                         Real Fo, Real lut, Real kappa, Real (&acc)[VPT], Real* sfb) {
   const int lane = gt & 31, wig = gt >> 5;
   Real x[VPT];
   load_vals<VPT, 32 * NW>(row, gt, m, x);
@@ -255,7 +256,8 @@ __device__ __forceinline__ Real row_redo(const Real* row, int gt, int g, int m, 
   Real S2 = 0;
 #pragma unroll
   for (int q = 0; q < NW; ++q) S2 += sfb[q];
-  const Real Fn = Fo + lut - (M + lg2(S2));
+  Real Fn = Fo + lut - (M + lg2(S2));
+  if (kappa != (Real)1) Fn *= kappa;
 #pragma unroll
   for (int v = 0; v < VPT; ++v) acc[v] += ex2(Fn + e[v] - Fo);
   group_sync<NW>(g);
@@ -376,12 +378,22 @@ __global__ void __launch_bounds__(32 * NW * NG, 1)
         fence_proxy_async_smem();
         issue(k + S);
       }
-      const Real r = scale_of(lut, St);
+      if (pr.kappa == (Real)1) {
+        const Real r = scale_of(lut, St);
 #pragma unroll
-      for (int v = 0; v < VPT; ++v) acc[v] = fma(r, w[v], acc[v]);
-      if (gt == 0) F[s + t] = Fo + lut - lg2(St);
+        for (int v = 0; v < VPT; ++v) acc[v] = fma(r, w[v], acc[v]);
+        if (gt == 0) F[s + t] = Fo + lut - lg2(St);
+      } else {
+        // Unbalanced GW: the balanced update scaled by kappa; the column sums
+        // take 2^(F_new + G - c Pi) = 2^(F_new - F_old) w.
+        const Real Fn = pr.kappa * (Fo + lut - lg2(St));
+        const Real r = ex2(Fn - Fo);
+#pragma unroll
+        for (int v = 0; v < VPT; ++v) acc[v] = fma(r, w[v], acc[v]);
+        if (gt == 0) F[s + t] = Fn;
+      }
     } else {
-      const Real Fn = row_redo<NW, VPT, Real>(row, gt, g, m, c, Gv, Fo, lut, acc, gsfb);
+      const Real Fn = row_redo<NW, VPT, Real>(row, gt, g, m, c, Gv, Fo, lut, pr.kappa, acc, gsfb);
       if (gt == 0) {
         F[s + t] = Fn;
         if (more) {
@@ -458,8 +470,12 @@ __global__ void __launch_bounds__(256) sk_cols(const __grid_constant__ SkBatch<R
   double St = 0.0;
   for (int g = 0; g < 8; ++g) St += sS[g][lane];
   const bool bad = p < m && !(St >= (double)tiny_sum<Real>() && St <= 1e30);
+  const double kap = (double)pr.kappa;
   if (!__syncthreads_or(bad)) {
-    if (grp == 0 && p < m) G[p] = (Real)((double)G[p] + (double)lv[p] - log2(St));
+    if (grp == 0 && p < m) {
+      const double gn = (double)G[p] + (double)lv[p] - log2(St);
+      G[p] = (Real)(kap == 1.0 ? gn : kap * gn);
+    }
     return;
   }
   // Recompute: log2 sum_i 2^(F_i + G_p - c Pi_ip) with a running max.
@@ -498,7 +514,8 @@ __global__ void __launch_bounds__(256) sk_cols(const __grid_constant__ SkBatch<R
     double St2 = 0.0;
     for (int g = 0; g < 8; ++g)
       if (sS[g][lane] > 0.0) St2 += sS[g][lane] * exp2((double)(sM[g][lane] - Mt));
-    G[p] = (Real)((double)Gp + (double)lv[p] - ((double)Mt + log2(St2)));
+    const double gn = (double)Gp + (double)lv[p] - ((double)Mt + log2(St2));
+    G[p] = (Real)(kap == 1.0 ? gn : kap * gn);
   }
 }
 
@@ -777,6 +794,167 @@ __global__ void finish_stats(const double* __restrict__ dotE, int nE, const doub
   }
 }
 
+// ---------------------------------------------------------------------------
+// Unbalanced GW (Remark "Entropic algorithm for UGW").  The scalars of the
+// current plan T (mass m = sum T, row sums a = T 1, column sums b = T^T 1):
+//   scal[0] g = rho sum a ln(a/u) + rho sum b ln(b/v) + eps sum T ln(T/(u v))
+//   scal[1] m
+//   scal[2] KL(a (x) a | u (x) u) = 2 m sum a ln(a/u) - m^2 + (sum u)^2
+//   scal[3] the same for b and v
+//   scal[4] KL(T (x) T | (u v) (x) (u v)) = 2 m sum T ln(T/(u v)) - m^2 + (sum u sum v)^2
+//   scal[5] sum |a - u|, scal[6] sum |b - v|
+//   scal[8] 1 / sqrt(sum u sum v) (the starting plan's scale)
+//   scal[9] sqrt(m_prev / m) (the rescale after each step's plan)
+// ---------------------------------------------------------------------------
+constexpr int kUgwScal = 16;
+
+// Per row: a_i = sum_p T_ip, e_i = sum_p T_ip ln T_ip (0 ln 0 = 0), in double.
+template <typename Real>
+__global__ void ugw_rowstats(const Real* __restrict__ T, int n, int m, double* __restrict__ a,
+                             double* __restrict__ e) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  const Real* row = T + (size_t)i * m;
+  double s = 0.0, t = 0.0;
+  for (int p = threadIdx.x & 31; p < m; p += 32) {
+    const double x = (double)row[p];
+    s += x;
+    if (x > 0.0) t += x * log(x);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    t += __shfl_xor_sync(0xffffffffu, t, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    a[i] = s;
+    e[i] = t;
+  }
+}
+
+// Per band of R rows: column sums in double, colpart[band][p].
+template <typename Real>
+__global__ void ugw_colsums(const Real* __restrict__ T, int n, int m, int R, double* __restrict__ colpart) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m) return;
+  const int b = blockIdx.y, i0 = b * R, i1 = min(n, i0 + R);
+  double s = 0.0;
+  for (int i = i0; i < i1; ++i) s += (double)T[(size_t)i * m + p];
+  colpart[(size_t)b * m + p] = s;
+}
+
+__device__ __forceinline__ double block_sum_d(double x, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = x;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  return t;
+}
+
+// One block: the scalars above from the row statistics and column partials.
+__global__ void ugw_finish(const double* __restrict__ a, const double* __restrict__ e,
+                           const double* __restrict__ colpart, int B, int n, int m, const double* __restrict__ u,
+                           const double* __restrict__ v, double rho, double eps, double* __restrict__ scal) {
+  __shared__ double sh[32];
+  double mass = 0.0, sa = 0.0, se = 0.0, su = 0.0, ra = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    mass += a[i];
+    su += u[i];
+    if (a[i] > 0.0) sa += a[i] * log(a[i] / u[i]);
+    se += e[i] - a[i] * log(u[i]);
+    ra += fabs(a[i] - u[i]);
+  }
+  double sb = 0.0, sv = 0.0, cb = 0.0;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) {
+    double b = 0.0;
+    for (int q = 0; q < B; ++q) b += colpart[(size_t)q * m + p];
+    sv += v[p];
+    if (b > 0.0) sb += b * log(b / v[p]);
+    se -= b * log(v[p]);
+    cb += fabs(b - v[p]);
+  }
+  mass = block_sum_d(mass, sh);
+  sa = block_sum_d(sa, sh);
+  se = block_sum_d(se, sh);
+  su = block_sum_d(su, sh);
+  ra = block_sum_d(ra, sh);
+  sb = block_sum_d(sb, sh);
+  sv = block_sum_d(sv, sh);
+  cb = block_sum_d(cb, sh);
+  if (threadIdx.x == 0) {
+    scal[0] = rho * sa + rho * sb + eps * se;
+    scal[1] = mass;
+    scal[2] = 2.0 * mass * sa - mass * mass + su * su;
+    scal[3] = 2.0 * mass * sb - mass * mass + sv * sv;
+    scal[4] = 2.0 * mass * se - mass * mass + (su * sv) * (su * sv);
+    scal[5] = ra;
+    scal[6] = cb;
+  }
+}
+
+// scal[8] = 1 / sqrt(sum u sum v).
+__global__ void ugw_start_scale(const double* __restrict__ u, int n, const double* __restrict__ v, int m,
+                                double* __restrict__ scal) {
+  __shared__ double sh[32];
+  double su = 0.0, sv = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) su += u[i];
+  for (int p = threadIdx.x; p < m; p += blockDim.x) sv += v[p];
+  su = block_sum_d(su, sh);
+  sv = block_sum_d(sv, sh);
+  if (threadIdx.x == 0) scal[8] = 1.0 / sqrt(su * sv);
+}
+
+// scal[9] = sqrt(scal[1] / m_new), m_new the plan's mass from its column
+// partials (colpart, written by the plan pass).
+__global__ void ugw_rescale_factor(const double* __restrict__ colpart, int B, int m, double* __restrict__ scal) {
+  __shared__ double sh[32];
+  double t = 0.0;
+  for (size_t k = threadIdx.x; k < (size_t)B * m; k += blockDim.x) t += colpart[k];
+  t = block_sum_d(t, sh);
+  if (threadIdx.x == 0) scal[9] = sqrt(scal[1] / t);
+}
+
+// x *= *factor elementwise.
+template <typename Real>
+__global__ void scale_by(Real* __restrict__ x, size_t N, const double* __restrict__ factor) {
+  const Real f = (Real)*factor;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+    x[i] *= f;
+}
+
+// The unbalanced step's cost in the Sinkhorn kernels' form:
+//   Pi_ip <- (Pi_ip + g) / m - eps (ln u_i + ln v_p)
+// with Pi = the gradient with T's own marginals on entry; lu, lv are log2 u,
+// log2 v.  The balanced update on this cost, scaled by rho / (rho + eps), is
+// the unbalanced update with reference measure u v^T.
+template <typename Real>
+__global__ void ugw_cost_kernel(Real* __restrict__ Pi, int n, int m, const Real* __restrict__ lu,
+                                const Real* __restrict__ lv, const double* __restrict__ scal, double eps) {
+  const Real g = (Real)scal[0], inv_m = (Real)(1.0 / scal[1]);
+  const Real el = (Real)(eps * 0.6931471805599453);
+  const size_t N = (size_t)n * m;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = k / m, p = k % m;
+    Pi[k] = fma(Pi[k] + g, inv_m, -el * (lu[i] + lv[p]));
+  }
+}
+
+// Final UGW statistics (after finish_stats has written E and the rest):
+// [0] UGW objective, [2] rho (KLx(a|u) + KLx(b|v)), [3] eps KLx(T|u v),
+// [4] sum |a - u|, [5] sum |b - v|, [7] mass of T.
+__global__ void ugw_stats(const double* __restrict__ scal, double rho, double eps, double* __restrict__ stats) {
+  const double E = stats[1];
+  stats[2] = rho * (scal[2] + scal[3]);
+  stats[3] = eps * scal[4];
+  stats[0] = E + stats[2] + stats[3];
+  stats[4] = scal[5];
+  stats[5] = scal[6];
+  stats[7] = scal[1];
+}
+
 // Pi += coef * ln T elementwise; an entry of T that underflowed to zero
 // counts as the smallest normal number of the type.
 template <typename Real>
@@ -825,6 +1003,7 @@ struct SolveState {
   const SolveArgs* A;
   SkProb<Real> sk;
   double *dotE, *dotC;
+  double *ugw_a, *ugw_e, *ugw_scal;  // unbalanced GW: row statistics and scalars
   char* gws;
   size_t gws_bytes;
   size_t smem_pass, smem_plan;
@@ -848,6 +1027,7 @@ int prepare(const SolveArgs& A, void* wsv, size_t ws_bytes, SolveState<Real>* S)
   k.B = bands.B;
   k.R = bands.R;
   k.c = (Real)(1.4426950408889634 / A.tau);  // each step's Sinkhorn regularisation is tau
+  k.kappa = A.rho > 0.0 ? (Real)(A.rho / (A.rho + A.eps)) : (Real)1;
   k.Pi = (Real*)take((size_t)n * m * sizeof(Real));
   k.F = (Real*)take((size_t)n * sizeof(Real));
   k.G = (Real*)take((size_t)m * sizeof(Real));
@@ -858,6 +1038,9 @@ int prepare(const SolveArgs& A, void* wsv, size_t ws_bytes, SolveState<Real>* S)
   k.cta_stats = (double*)take((size_t)2 * bands.B * sizeof(double));
   S->dotE = (double*)take((size_t)kDots * sizeof(double));
   S->dotC = (double*)take((size_t)kDots * sizeof(double));
+  S->ugw_a = (double*)take((size_t)n * sizeof(double));
+  S->ugw_e = (double*)take((size_t)n * sizeof(double));
+  S->ugw_scal = (double*)take((size_t)kUgwScal * sizeof(double));
   S->gws = take(0);
   if (off > ws_bytes) return GW_ERR_OOM;
   S->gws_bytes = ws_bytes - off;
@@ -932,6 +1115,22 @@ void step_setup(const SolveState<Real>& S, cudaStream_t st) {
   log2_scaled<Real><<<(A.n + 255) / 256, 256, 0, st>>>(A.u, A.n, (Real*)S.sk.lu);
   log2_scaled<Real><<<(A.m + 255) / 256, 256, 0, st>>>(A.v, A.m, (Real*)S.sk.lv);
   fill_product<Real><<<4 * A.num_sms, 256, 0, st>>>(A.u, A.v, A.n, A.m, (Real*)A.T);
+  if (A.rho > 0.0) {
+    // Unbalanced GW starts at u v^T / sqrt(m(u) m(v)).
+    ugw_start_scale<<<1, 256, 0, st>>>(A.u, A.n, A.v, A.m, S.ugw_scal);
+    scale_by<Real><<<4 * A.num_sms, 256, 0, st>>>((Real*)A.T, (size_t)A.n * A.m, S.ugw_scal + 8);
+  }
+}
+
+// Unbalanced GW: the scalars of the plan T (ugw_finish's list).
+template <typename Real>
+void ugw_scalars(const SolveState<Real>& S, cudaStream_t st) {
+  const SolveArgs& A = *S.A;
+  ugw_rowstats<Real><<<(A.n + 7) / 8, 256, 0, st>>>((const Real*)A.T, A.n, A.m, S.ugw_a, S.ugw_e);
+  ugw_colsums<Real><<<dim3((A.m + 255) / 256, S.sk.B), 256, 0, st>>>((const Real*)A.T, A.n, A.m, S.sk.R,
+                                                                      S.sk.colpart);
+  ugw_finish<<<1, 256, 0, st>>>(S.ugw_a, S.ugw_e, S.sk.colpart, S.sk.B, A.n, A.m, A.u, A.v, A.rho, A.eps,
+                                S.ugw_scal);
 }
 
 // Pi for mirror-descent step l, then f = g = 0 (or, warm-started after the
@@ -939,6 +1138,20 @@ void step_setup(const SolveState<Real>& S, cudaStream_t st) {
 template <typename Real>
 int step_cost(const SolveState<Real>& S, cudaStream_t st, int l) {
   const SolveArgs& A = *S.A;
+  if (A.rho > 0.0) {
+    // Unbalanced GW: cost ((1/2) grad E(T) + g(T)) / m(T) - eps ln(u v), the
+    // gradient taken with T's own marginals.
+    TraceScope ts(A.tracer, "ugw_cost", st);
+    ugw_scalars(S, st);
+    int rc = gradient(S, 1, 1.0, st);
+    if (rc != GW_OK) return rc;
+    ugw_cost_kernel<Real><<<4 * A.num_sms, 256, 0, st>>>((Real*)S.sk.Pi, A.n, A.m, S.sk.lu, S.sk.lv, S.ugw_scal,
+                                                         A.eps);
+    if (A.warm_start && l > 0) return GW_OK;
+    fill_val<Real><<<(A.n + 255) / 256, 256, 0, st>>>(S.sk.F, A.n, (Real)0);
+    fill_val<Real><<<(A.m + 255) / 256, 256, 0, st>>>(S.sk.G, A.m, (Real)0);
+    return GW_OK;
+  }
   int rc = gradient(S, 0, 2.0 * A.theta, st);
   if (rc != GW_OK) return rc;
   if (fused<Real>(A)) {
@@ -957,6 +1170,16 @@ int step_cost(const SolveState<Real>& S, cudaStream_t st, int l) {
   fill_val<Real><<<(A.n + 255) / 256, 256, 0, st>>>(S.sk.F, A.n, (Real)0);
   fill_val<Real><<<(A.m + 255) / 256, 256, 0, st>>>(S.sk.G, A.m, (Real)0);
   return GW_OK;
+}
+
+// After a step's plan: unbalanced GW rescales it to mass sqrt(m(T_prev) m(T)).
+template <typename Real>
+void step_after_plan(const SolveState<Real>& S, cudaStream_t st) {
+  const SolveArgs& A = *S.A;
+  if (!(A.rho > 0.0)) return;
+  TraceScope ts(A.tracer, "ugw_rescale", st);
+  ugw_rescale_factor<<<1, 256, 0, st>>>(S.sk.colpart, S.sk.B, A.m, S.ugw_scal);
+  scale_by<Real><<<4 * A.num_sms, 256, 0, st>>>((Real*)A.T, (size_t)A.n * A.m, S.ugw_scal + 9);
 }
 
 // Potentials out and the statistics of the final plan.
@@ -985,6 +1208,10 @@ int step_finish(const SolveState<Real>& S, cudaStream_t st) {
     fill_val<double><<<1, 256, 0, st>>>(S.dotC, kDots, 0.0);
   finish_stats<<<1, 256, 0, st>>>(S.dotE, kDots, S.dotC, kDots, S.sk.cta_stats, S.sk.B, S.sk.colpart, m, A.v, A.eps,
                                   A.theta, A.n_outer, A.stats);
+  if (A.rho > 0.0) {
+    ugw_scalars(S, st);
+    ugw_stats<<<1, 1, 0, st>>>(S.ugw_scal, A.rho, A.eps, A.stats);
+  }
   return GW_OK;
 }
 
@@ -1045,6 +1272,7 @@ int solve_typed(const SolveArgs& A, void* ws, size_t ws_bytes) {
     }
     rc = launch_rows<NW, VPT, NG, Real, 1>(list, 1, true, st, A.status, A.tracer);
     if (rc != GW_OK) return rc;
+    step_after_plan(S, st);
   }
   rc = step_finish(S, st);
   if (rc != GW_OK) return rc;
@@ -1077,6 +1305,7 @@ int solve_group(const SolveArgs* const* A, void* const* ws, const size_t* ws_byt
     }
     int rc = launch_rows<NW, VPT, NG, Real, 32>(list.data(), count, true, st, status, tracer);
     if (rc != GW_OK) return rc;
+    for (auto& s : S) step_after_plan(s, st);
   }
   for (auto& s : S) {
     int rc = step_finish(s, st);
@@ -1185,6 +1414,9 @@ size_t solve_workspace_bytes(const SolveArgs& A) {
   add((size_t)2 * bands.B * 8);
   add(kDots * 8);
   add(kDots * 8);
+  add((size_t)n * 8);
+  add((size_t)n * 8);
+  add(kUgwScal * 8);
   const size_t g = A.dim == 2 ? grad2d_workspace_bytes(A.nx, A.ny, A.dtype, A.cost, A.k)
                               : grad1d_workspace_bytes(n, m, A.k, A.dtype, A.num_sms);
   return b + g + 4096;

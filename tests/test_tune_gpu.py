@@ -3,6 +3,8 @@ gives the oracle's result.  For each row length, every candidate that is not
 the built-in choice is installed for exactly that row length (gw_tune_set),
 a small solve runs under it, and its plan and value are compared with the
 FP64 oracle's mirror descent and with the solve under the built-in choice."""
+import os
+
 import numpy as np
 import pytest
 
@@ -13,6 +15,50 @@ from tests import gwtest_util as U
 pytestmark = pytest.mark.gpu
 
 ROWS = {"f32": [300, 1000, 2000, 4000, 8000], "f64": [200, 1000, 4000]}
+TABLE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2404_08970_gb300",
+                     "tune_table.txt")
+
+
+def _reload_committed_table(L):
+    """The table the library loads at start-up (beside the library)."""
+    if os.path.exists(TABLE):
+        L.gw_tune_load(TABLE)
+
+
+def _table_entries():
+    out = []
+    for line in open(TABLE):
+        body = line.split("#")[0].split()
+        if len(body) == 5:
+            out.append(tuple(int(x) for x in body))
+    return out
+
+
+def test_committed_table_is_in_effect_and_solves_match_oracle():
+    """The committed tuning table is loaded at context creation; a solve in
+    each tuned range runs under the table's configuration and matches the
+    FP64 oracle."""
+    from paper_2404_08970_gb300 import _lib as L
+    U.ctx()
+    L.gw_tune_clear()
+    _reload_committed_table(L)
+    entries = _table_entries()
+    assert entries
+    for kernel, dt, lo, hi, cfg in entries:
+        assert L.gw_tune_config(kernel, dt, hi) == cfg
+    for kernel, dt, lo, hi, cfg in entries:
+        if dt != L.GW_F32 or hi > 4096 or cfg == L.gw_tune_candidates(kernel, dt, hi)[0]:
+            continue
+        m = hi
+        rng = np.random.default_rng(m + 1)
+        n = 16
+        w = dict(nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=1, eps=5e-2, n_outer=3, n_inner=30,
+                 u=I.dirichlet(n, 1.0, rng), v=I.dirichlet(m, 1.0, rng))
+        DX, DY = O.grid_dist_1d(n, w["hx"], 1), O.grid_dist_1d(m, w["hy"], 1)
+        Ts, _, _ = O.mirror_descent(DX, DY, w["u"], w["v"], w["eps"], w["n_outer"], w["n_inner"])
+        T, st = _solve(w, "f32")
+        assert np.linalg.norm(T - Ts) <= 1e-3 * np.linalg.norm(Ts), (m, cfg)
+        assert abs(st[1] - O.value(DX, DY, Ts)) <= 1e-5 * O.value(DX, DY, Ts), (m, cfg)
 
 
 def _solve(w, dtype):
@@ -63,6 +109,7 @@ def test_every_alternative_configuration_matches_oracle(dtype):
                     assert st[5] < 1e-5, (m, cfg)
     finally:
         L.gw_tune_clear()
+        _reload_committed_table(L)
     # Every alternative configuration of this dtype ran at least once.
     alts = {20, 21, 22, 23, 24} if dtype == "f32" else {30, 31, 32}
     assert alts <= seen, alts - seen
