@@ -346,6 +346,7 @@ size_t grad1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms) {
 }
 
 int grad1d_launch(const Grad1DArgs& a, void* ws, size_t ws_bytes) {
+  if (a.ky != 0 && a.ky != a.k) return grad1d_launch_mixed(a, ws, ws_bytes);
   switch (a.k) {
     case 1: return grad1d_launch_k1(a, ws, ws_bytes);
     case 2: return grad1d_launch_k2(a, ws, ws_bytes);

@@ -55,7 +55,8 @@ struct FastSmem {
   }
 };
 
-template <int K, int NW, int VPT, typename Real>
+// KX: exponent of the column transform (X); K: of the row transform (Y).
+template <int KX, int K, int NW, int VPT, typename Real>
 __global__ void __launch_bounds__(32 * (NW + 1), 1)
     k1c_fast_rows(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmG,
                   int use_tma_store, const Real* __restrict__ T, Real* __restrict__ G, int n,
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
   constexpr int ALL = NT + 32;       // + scan warp
   constexpr int SEG = 32 * VPT;      // columns per compute warp
   constexpr Real CK = (K & 1) ? (Real)2 : (Real)0;
-  static_assert(K == 1 || K == 2, "fast row kernel handles k = 1, 2");
+  static_assert((K == 1 || K == 2) && (KX == 1 || KX == 2), "fast row kernel handles k = 1, 2");
 
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   // 1024-byte aligned start (the 128-byte swizzle repeats every 1 KB); the
@@ -185,13 +186,13 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
   // ---------------- compute warps ----------------
   const int c0 = tid * VPT;
   const int o0 = lane * VPT;  // offset inside the warp segment
-  // Column state: K = 1 difference form (y_t, b_t); K = 2 Horner (q0, q1, q2).
-  Real cst[VPT][K + 1];
+  // Column state: KX = 1 difference form (y_t, b_t); KX = 2 Horner (q0, q1, q2).
+  Real cst[VPT][KX + 1];
 #pragma unroll
   for (int v = 0; v < VPT; ++v) {
     const int p = c0 + v;
 #pragma unroll
-    for (int e = 0; e <= K; ++e) cst[v][e] = (p < m) ? q[((size_t)a * (K + 1) + e) * m + p] : (Real)0;
+    for (int e = 0; e <= KX; ++e) cst[v][e] = (p < m) ? q[((size_t)a * (KX + 1) + e) * m + p] : (Real)0;
   }
   constexpr int PER = 16 / sizeof(Real);
   Real ex_prev[K + 1];
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
         for (int w = 0; w < PER; ++w) {
           const int v = j * PER + w;
           Real y;
-          if constexpr (K == 1) {
+          if constexpr (KX == 1) {
             y = cst[v][0];
             cst[v][1] = fma((Real)2, x[w], cst[v][1]);
             cst[v][0] += cst[v][1];

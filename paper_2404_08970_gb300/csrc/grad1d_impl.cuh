@@ -815,7 +815,7 @@ inline K1Layout k1_layout(int n, int m, int k, size_t real_bytes, int target_ban
   L.cx_off = off;      off = align_up(off + (size_t)2 * n * real_bytes, 256);  // hi, lo
   L.cy_off = off;      off = align_up(off + (size_t)2 * m * real_bytes, 256);
   L.partx_off = off;   off = align_up(off + marg_part_doubles(n, k) * 8, 256);
-  L.party_off = off;   off = align_up(off + marg_part_doubles(m, k) * 8, 256);
+  L.party_off = off;   off = align_up(off + marg_part_doubles(m, 3) * 8, 256);
   L.end = off;
   return L;
 }
@@ -848,7 +848,7 @@ int launch_k1c(const Grad1DArgs& g, const K1Layout& L, char* ws, int use_tma, cu
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }
 
-template <int K, int NW, int VPT, typename Real>
+template <int KX, int K, int NW, int VPT, typename Real>
 int launch_k1c_fast(const Grad1DArgs& g, const K1Layout& L, char* ws, cudaStream_t st) {
   CUtensorMap tm, tmg;
   memset(&tm, 0, sizeof tm);
@@ -870,11 +870,11 @@ int launch_k1c_fast(const Grad1DArgs& g, const K1Layout& L, char* ws, cudaStream
   const int fl_bytes = (int)FastSmem<K, NW, VPT, Real>::fl_bytes;
   if (use_tma) stages = std::max(2, std::min(4, (200 * 1024 - 3 * vec_bytes - fl_bytes) / slot_bytes));
   const size_t smem = FastSmem<K, NW, VPT, Real>::bytes(slot_bytes, vec_bytes, stages);
-  auto kern = k1c_fast_rows<K, NW, VPT, Real>;
+  auto kern = k1c_fast_rows<KX, K, NW, VPT, Real>;
   TraceScope ts(g.tracer, "k1c_fast_rows", st);
   if (!allow_dynamic_smem((const void*)kern, smem))
     return GW_ERR_CUDA;
-  const Real scale = (Real)(2.0 * g.out_scale * std::pow(g.hx, g.k) * std::pow(g.hy, g.k));
+  const Real scale = (Real)(2.0 * g.out_scale * std::pow(g.hx, KX) * std::pow(g.hy, K));
   const Real* cx = (const Real*)(ws + L.cx_off);
   const Real* cy = (const Real*)(ws + L.cy_off);
   kern<<<L.bands.B, 32 * (NW + 1), smem, st>>>(tm, tmg, use_tma_store, (const Real*)g.T, (Real*)g.G, g.n, g.m,
@@ -892,10 +892,27 @@ void launch_k1a(const Grad1DArgs& g, int B, int R, Real* mu, Real* rowpart, cuda
   k1a_band_moments<K, Real, VEC, CPT><<<grid, nt, 0, st>>>((const Real*)g.T, g.n, g.m, R, mu, rowpart, g.exact);
 }
 
-template <int K, typename Real>
+// Constant terms c_x (exponent 2 KX) and c_y (exponent 2 KY) as hi/lo
+// pairs on `st`; one launch pair for equal exponents, one per vector else.
+template <int KX, int KY>
+int const_terms(const Grad1DArgs& g, const double* wx, const double* wy, char* ws, const K1Layout& L, int dt,
+                cudaStream_t st) {
+  const double fx = std::pow(g.hx, 2 * KX) * g.out_scale, fy = std::pow(g.hy, 2 * KY) * g.out_scale;
+  if constexpr (KX == KY)
+    return marg_const2_launch(wx, g.n, fx, ws + L.cx_off, wy, g.m, fy, ws + L.cy_off, KX, dt,
+                              (double*)(ws + L.partx_off), st, g.tracer);
+  int rc = marg_const_launch(wx, g.n, KX, fx, ws + L.cx_off, dt, (double*)(ws + L.partx_off), st, g.tracer);
+  if (rc != GW_OK) return rc;
+  return marg_const_launch(wy, g.m, KY, fy, ws + L.cy_off, dt, (double*)(ws + L.party_off), st, g.tracer);
+}
+
+// KX: the exponent of X's distance (column transform, band moments, c_x);
+// KY: Y's (row transform, c_y).  Mixed exponents run the warp-specialised
+// row kernel only (KX, KY <= 2, rows of at most 8192 columns).
+template <int KX, typename Real, int KY = KX>
 int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
   const int n = g.n, m = g.m;
-  const K1Layout L = k1_layout(n, m, K, sizeof(Real), g.num_sms);
+  const K1Layout L = k1_layout(n, m, KX, sizeof(Real), g.num_sms);
   if (L.end > ws_bytes) return GW_ERR_OOM;
   char* ws = (char*)wsv;
   cudaStream_t st = g.stream;
@@ -910,9 +927,7 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
   if (overlap) {
     if (cudaEventRecord(g.ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(g.side, g.ev_fork, 0) != cudaSuccess)
       return GW_ERR_CUDA;
-    int rc = marg_const2_launch(g.u, n, std::pow(g.hx, 2 * K) * g.out_scale, ws + L.cx_off, g.v, m,
-                                std::pow(g.hy, 2 * K) * g.out_scale, ws + L.cy_off, K, dt,
-                                (double*)(ws + L.partx_off), g.side, g.tracer);
+    int rc = const_terms<KX, KY>(g, g.u, g.v, ws, L, dt, g.side);
     if (rc != GW_OK) return rc;
     if (cudaEventRecord(g.ev_join, g.side) != cudaSuccess) return GW_ERR_CUDA;
   }
@@ -933,7 +948,7 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
         if (encode_rows_tmap(&tm, g.T, n, m, 4, &box_cols)) {
           const int slot_bytes = (int)align_up((size_t)m * 4, 1024);
           const size_t smem = 1024 + (size_t)kA_STAGES * slot_bytes + 8 * kA_STAGES;
-          auto kern = k1a_band_moments_tma<K>;
+          auto kern = k1a_band_moments_tma<KX>;
           if (allow_dynamic_smem((const void*)kern, smem)) {
             const int nt = std::max(32, (m / kA_VPT + 31) / 32 * 32);
             kern<<<B, nt, smem, st>>>(tm, n, m, R, slot_bytes, box_cols, (m / 32) / box_cols, (float*)mu,
@@ -947,24 +962,24 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
     } else if constexpr (sizeof(Real) == 4) {
       if (vec_ok) {
         vec_used = 4;
-        if (m <= 4096) launch_k1a<K, Real, 4, 1>(g, B, R, mu, rowpart, st);
-        else if (m <= 8192) launch_k1a<K, Real, 4, 2>(g, B, R, mu, rowpart, st);
-        else launch_k1a<K, Real, 4, 4>(g, B, R, mu, rowpart, st);
+        if (m <= 4096) launch_k1a<KX, Real, 4, 1>(g, B, R, mu, rowpart, st);
+        else if (m <= 8192) launch_k1a<KX, Real, 4, 2>(g, B, R, mu, rowpart, st);
+        else launch_k1a<KX, Real, 4, 4>(g, B, R, mu, rowpart, st);
       } else {
-        if (m <= 1024) launch_k1a<K, Real, 1, 1>(g, B, R, mu, rowpart, st);
-        else if (m <= 4096) launch_k1a<K, Real, 1, 4>(g, B, R, mu, rowpart, st);
-        else launch_k1a<K, Real, 1, 16>(g, B, R, mu, rowpart, st);
+        if (m <= 1024) launch_k1a<KX, Real, 1, 1>(g, B, R, mu, rowpart, st);
+        else if (m <= 4096) launch_k1a<KX, Real, 1, 4>(g, B, R, mu, rowpart, st);
+        else launch_k1a<KX, Real, 1, 16>(g, B, R, mu, rowpart, st);
       }
     } else {
       if (vec_ok) {
         vec_used = 2;
-        if (m <= 2048) launch_k1a<K, Real, 2, 1>(g, B, R, mu, rowpart, st);
-        else if (m <= 8192) launch_k1a<K, Real, 2, 4>(g, B, R, mu, rowpart, st);
-        else launch_k1a<K, Real, 2, 8>(g, B, R, mu, rowpart, st);
+        if (m <= 2048) launch_k1a<KX, Real, 2, 1>(g, B, R, mu, rowpart, st);
+        else if (m <= 8192) launch_k1a<KX, Real, 2, 4>(g, B, R, mu, rowpart, st);
+        else launch_k1a<KX, Real, 2, 8>(g, B, R, mu, rowpart, st);
       } else {
-        if (m <= 1024) launch_k1a<K, Real, 1, 1>(g, B, R, mu, rowpart, st);
-        else if (m <= 4096) launch_k1a<K, Real, 1, 4>(g, B, R, mu, rowpart, st);
-        else launch_k1a<K, Real, 1, 16>(g, B, R, mu, rowpart, st);
+        if (m <= 1024) launch_k1a<KX, Real, 1, 1>(g, B, R, mu, rowpart, st);
+        else if (m <= 4096) launch_k1a<KX, Real, 1, 4>(g, B, R, mu, rowpart, st);
+        else launch_k1a<KX, Real, 1, 16>(g, B, R, mu, rowpart, st);
       }
     }
   }
@@ -976,7 +991,7 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
   double* c = (double*)(ws + L.c_off);
   {
     TraceScope ts(g.tracer, "k1b_band_carries", st);
-    k1b_carries<K, Real><<<(m + 31) / 32, 32 * kGroups, 0, st>>>(mu, n, m, R, B, (Real*)(ws + L.q_off),
+    k1b_carries<KX, Real><<<(m + 31) / 32, 32 * kGroups, 0, st>>>(mu, n, m, R, B, (Real*)(ws + L.q_off),
                                                                 g.exact ? c : nullptr);
   }
   if (cudaPeekAtLastError() != cudaSuccess) return GW_ERR_CUDA;
@@ -993,27 +1008,30 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
   if (overlap) {
     if (cudaStreamWaitEvent(st, g.ev_join, 0) != cudaSuccess) return GW_ERR_CUDA;
   } else {
-    int rc = marg_const2_launch(wx, n, std::pow(g.hx, 2 * K) * g.out_scale, ws + L.cx_off, wy, m,
-                                std::pow(g.hy, 2 * K) * g.out_scale, ws + L.cy_off, K, dt,
-                                (double*)(ws + L.partx_off), st, g.tracer);
+    int rc = const_terms<KX, KY>(g, wx, wy, ws, L, dt, st);
     if (rc != GW_OK) return rc;
   }
 
   // k1c
-  if constexpr (K <= 2) {
+  if constexpr (KX <= 2 && KY <= 2) {
     if (!g.force_generic) {
       if constexpr (sizeof(Real) == 4) {
-        if (m <= 512) return launch_k1c_fast<K, 4, 4, Real>(g, L, ws, st);
-        if (m <= 1024) return launch_k1c_fast<K, 8, 4, Real>(g, L, ws, st);
-        if (m <= 2048) return launch_k1c_fast<K, 8, 8, Real>(g, L, ws, st);
-        if (m <= 4096) return launch_k1c_fast<K, 16, 8, Real>(g, L, ws, st);
-        if (m <= 8192) return launch_k1c_fast<K, 16, 16, Real>(g, L, ws, st);
+        if (m <= 512) return launch_k1c_fast<KX, KY, 4, 4, Real>(g, L, ws, st);
+        if (m <= 1024) return launch_k1c_fast<KX, KY, 8, 4, Real>(g, L, ws, st);
+        if (m <= 2048) return launch_k1c_fast<KX, KY, 8, 8, Real>(g, L, ws, st);
+        if (m <= 4096) return launch_k1c_fast<KX, KY, 16, 8, Real>(g, L, ws, st);
+        if (m <= 8192) return launch_k1c_fast<KX, KY, 16, 16, Real>(g, L, ws, st);
       } else {
-        if (m <= 1024) return launch_k1c_fast<K, 8, 4, Real>(g, L, ws, st);
-        if (m <= 4096) return launch_k1c_fast<K, 16, 8, Real>(g, L, ws, st);
+        if (m <= 1024) return launch_k1c_fast<KX, KY, 8, 4, Real>(g, L, ws, st);
+        if (m <= 4096) return launch_k1c_fast<KX, KY, 16, 8, Real>(g, L, ws, st);
       }
     }
   }
+  if constexpr (KX != KY) {
+    note_failure("mixed distance exponents need rows of at most 8192 columns (4096 in double)");
+    return GW_ERR_INVALID;
+  } else {
+  constexpr int K = KX;
   const int use_tma = ((m * sizeof(Real)) % 16 == 0) && ((((uintptr_t)g.T) & 15) == 0);
   if constexpr (sizeof(Real) == 4) {
     if (m <= 512) return launch_k1c<K, 128, 4, Real>(g, L, ws, use_tma, st);
@@ -1026,6 +1044,7 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
     if (m <= 1024) return launch_k1c<K, 256, 4, Real>(g, L, ws, use_tma, st);
     if (m <= 4096) return launch_k1c<K, 512, 8, Real>(g, L, ws, use_tma, st);
     return launch_k1c<K, 1024, 16, Real>(g, L, ws, use_tma, st);
+  }
   }
 }
 

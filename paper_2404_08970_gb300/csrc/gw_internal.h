@@ -59,6 +59,7 @@ Bands choose_bands(int n, int target);
 
 struct Grad1DArgs {
   int n, m, k;
+  int ky;               // exponent of Y's distance when it differs from k (0: same as k)
   double hx, hy;
   int dtype;            // GW_F32 or GW_F64
   const void* T;        // n x m row-major, dtype
@@ -106,6 +107,7 @@ int grad1d_launch(const Grad1DArgs& a, void* ws, size_t ws_bytes);
 int grad1d_launch_k1(const Grad1DArgs& a, void* ws, size_t ws_bytes);
 int grad1d_launch_k2(const Grad1DArgs& a, void* ws, size_t ws_bytes);
 int grad1d_launch_k3(const Grad1DArgs& a, void* ws, size_t ws_bytes);
+int grad1d_launch_mixed(const Grad1DArgs& a, void* ws, size_t ws_bytes);  // k != ky (1 and 2)
 
 // c[i] = h^{2k} sum_j |i - j|^{2k} w_j for i < len (the constant term of the
 // gradient), from a double vector w on the device.  part must hold
