@@ -95,6 +95,10 @@ typedef struct gw_problem {
   double rho;    /* solver only: 0 for balanced (F)GW; > 0 solves entropic
                     unbalanced GW with marginal relaxation rho (Remark
                     "Entropic algorithm for UGW") */
+  int ky;        /* 1D: exponent of Y's distance when it differs from X's
+                    (Sec. 2 allows k_X != k_Y); 0 means ky = k.  Mixed pairs
+                    (k, ky) = (1, 2) or (2, 1), rows of at most 8192 columns
+                    (4096 in double) */
 } gw_problem;
 
 typedef struct gw_ctx gw_ctx;

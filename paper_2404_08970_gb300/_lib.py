@@ -62,6 +62,7 @@ class gw_problem(ctypes.Structure):
         ("tau", ctypes.c_double),
         ("warm_start", ctypes.c_int),
         ("rho", ctypes.c_double),
+        ("ky", ctypes.c_int),
     ]
 
 
@@ -203,9 +204,9 @@ def gw_grad_noalloc(prob: gw_problem, u, v, T, G, marginals=GW_MARG_TARGET, stre
 
 
 def problem(dim=1, nx=1, ny=1, hx=1.0, hy=1.0, k=1, cost=GW_COST_POW, eps=1e-2, n_outer=1, n_inner=1,
-            theta=1.0, feat_dim=0, dtype=GW_F32, tau=0.0, warm_start=0, rho=0.0) -> gw_problem:
+            theta=1.0, feat_dim=0, dtype=GW_F32, tau=0.0, warm_start=0, rho=0.0, ky=0) -> gw_problem:
     return gw_problem(dim, nx, ny, hx, hy, k, cost, eps, n_outer, n_inner, theta, feat_dim, dtype, tau,
-                      warm_start, rho)
+                      warm_start, rho, ky)
 
 
 class Context:

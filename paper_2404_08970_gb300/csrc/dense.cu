@@ -258,7 +258,8 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
   const int sq = a.dim == 2 && a.cost == GW_COST_SQEUCLID;
   int rc = ensure_dist(S->X, n, a.hx, a.k, a.dim == 2 ? a.sx : 0, sq, a.prec, st);
   if (rc != GW_OK) return rc;
-  rc = ensure_dist(S->Y, m, a.hy, a.k, a.dim == 2 ? a.sy : 0, sq, a.prec, st);
+  const int ky = a.ky > 0 ? a.ky : a.k;
+  rc = ensure_dist(S->Y, m, a.hy, ky, a.dim == 2 ? a.sy : 0, sq, a.prec, st);
   if (rc != GW_OK) return rc;
   char* ws = (char*)wsv;
   size_t off = 0;
@@ -288,7 +289,7 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
   void* cy = take((size_t)2 * m * rb);
   double* r = (double*)take((size_t)n * 8);
   double* cc = (double*)take((size_t)m * 8);
-  double* part = (double*)take((marg_part_doubles(n, a.k) + marg_part_doubles(m, a.k)) * 8 + 512);
+  double* part = (double*)take((marg_part_doubles(n, 3) + marg_part_doubles(m, 3)) * 8 + 512);
   if (off > ws_bytes) return GW_ERR_OOM;
 
   const double* wx = a.u;
@@ -316,8 +317,15 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
       dist2_const_2d<float><<<m, 256, 0, st>>>(wy, a.sy, sq, a.k, fy * fy, (float*)cy);
     }
   } else {
-    rc = marg_const2_launch(wx, n, std::pow(a.hx, 2 * a.k), cx, wy, m, std::pow(a.hy, 2 * a.k), cy, a.k,
-                            dbl ? GW_F64 : GW_F32, part, st, a.tracer);
+    if (ky == a.k) {
+      rc = marg_const2_launch(wx, n, std::pow(a.hx, 2 * a.k), cx, wy, m, std::pow(a.hy, 2 * a.k), cy, a.k,
+                              dbl ? GW_F64 : GW_F32, part, st, a.tracer);
+    } else {
+      rc = marg_const_launch(wx, n, a.k, std::pow(a.hx, 2 * a.k), cx, dbl ? GW_F64 : GW_F32, part, st, a.tracer);
+      if (rc == GW_OK)
+        rc = marg_const_launch(wy, m, ky, std::pow(a.hy, 2 * ky), cy, dbl ? GW_F64 : GW_F32,
+                               part + marg_part_doubles(n, a.k), st, a.tracer);
+    }
     if (rc != GW_OK) return rc;
   }
 

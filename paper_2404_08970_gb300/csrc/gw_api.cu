@@ -221,7 +221,13 @@ gw_status check_grid(gw_ctx* c, const gw_problem* p) {
   if (p->dim == 1) {
     if (p->k > 3) return fail(c, GW_ERR_INVALID, "k must be <= 3 (got %d)", p->k);
     if (p->ny > 16384) return fail(c, GW_ERR_INVALID, "ny must be <= 16384 (got %d)", p->ny);
+    if (!gw::mixed_k_supported(p->k, p->ky, p->ny, p->dtype))
+      return fail(c, GW_ERR_INVALID,
+                  "mixed exponents (k, ky) = (%d, %d): supported are (1, 2) and (2, 1) with ny <= 8192 "
+                  "(4096 in double)", p->k, p->ky);
   } else {
+    if (p->ky != 0 && p->ky != p->k)
+      return fail(c, GW_ERR_INVALID, "2D grids take one distance exponent (ky = 0 or k)");
     if (p->cost != GW_COST_POW && p->cost != GW_COST_SQEUCLID)
       return fail(c, GW_ERR_INVALID, "2D cost must be GW_COST_POW or GW_COST_SQEUCLID (got %d)", p->cost);
     if (p->nx > gw::kMax2DSide || p->ny > gw::kMax2DSide)
@@ -419,6 +425,7 @@ gw_status grad_device(gw_ctx* c, const gw_problem* p, const double* d_u, const d
   a.n = p->nx;
   a.m = p->ny;
   a.k = p->k;
+  a.ky = p->ky == p->k ? 0 : p->ky;
   a.hx = p->hx;
   a.hy = p->hy;
   a.dtype = p->dtype;
@@ -445,8 +452,8 @@ gw_status grad_device(gw_ctx* c, const gw_problem* p, const double* d_u, const d
   a.ev_fork = c->ev_fork;
   a.ev_join = c->ev_join;
   char key[384];
-  snprintf(key, sizeof key, "grad1 %d %d %d %.17g %.17g %d %p %p %p %p %d %d %p %zu", a.n, a.m, a.k, a.hx, a.hy,
-           a.dtype, a.T, a.G, (void*)a.u, (void*)a.v, a.exact, a.force_generic, c->ws, c->ws_bytes);
+  snprintf(key, sizeof key, "grad1 %d %d %d %d %.17g %.17g %d %p %p %p %p %d %d %p %zu", a.n, a.m, a.k, a.ky, a.hx,
+           a.hy, a.dtype, a.T, a.G, (void*)a.u, (void*)a.v, a.exact, a.force_generic, c->ws, c->ws_bytes);
   return run_graph(
       c, key, a.stream,
       [&](cudaStream_t st) {
@@ -574,6 +581,7 @@ gw_status gw_grad_dense(gw_ctx* c, const gw_problem* p, const double* d_u, const
   a.n = (int)points_x(p);
   a.m = (int)points_y(p);
   a.k = p->k;
+  a.ky = p->ky == p->k ? 0 : p->ky;
   a.prec = precision;
   a.exact = marginals == GW_MARG_EXACT;
   a.hx = p->hx;
@@ -645,6 +653,7 @@ gw::SolveArgs solve_args(gw_ctx* c, const gw_problem* p, const double* d_u, cons
   a.tau = p->tau > 0.0 ? p->tau : p->eps;
   a.warm_start = p->warm_start;
   a.rho = p->rho;
+  a.ky = p->ky == p->k ? 0 : p->ky;
   a.theta = p->theta;
   a.n_outer = p->n_outer;
   a.n_inner = p->n_inner;
@@ -681,8 +690,8 @@ gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const doub
   if (s != GW_OK) return s;
   char key[512];
   snprintf(key, sizeof key,
-           "solve %d %d %d %d %d %d %.17g %.17g %.17g %.17g %.17g %.17g %d %d %d %d %p %p %p %p %p %p %p %p %p %zu",
-           a.dim, a.cost, a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.tau, a.rho, a.theta, a.warm_start, a.n_outer,
+           "solve %d %d %d %d %d %d %d %.17g %.17g %.17g %.17g %.17g %.17g %d %d %d %d %p %p %p %p %p %p %p %p %p %zu",
+           a.dim, a.cost, a.n, a.m, a.k, a.ky, a.dtype, a.hx, a.hy, a.eps, a.tau, a.rho, a.theta, a.warm_start, a.n_outer,
            a.n_inner, a.feat_dim,
            (void*)a.u, (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.f, (void*)a.g, (void*)a.stats, c->ws,
            c->ws_bytes);
@@ -798,8 +807,8 @@ gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const do
     for (int i = 0; i < count; ++i) {
       const gw::SolveArgs& a = args[i];
       snprintf(buf, sizeof buf,
-               "%d %d %d %d %d %d %.17g %.17g %.17g %.17g %.17g %.17g %d %d %d %d %p %p %p %p %p %p|", a.dim, a.cost,
-               a.n, a.m, a.k, a.dtype, a.hx, a.hy, a.eps, a.tau, a.rho, a.theta, a.warm_start, a.n_outer, a.n_inner,
+               "%d %d %d %d %d %d %d %.17g %.17g %.17g %.17g %.17g %.17g %d %d %d %d %p %p %p %p %p %p|", a.dim,
+               a.cost, a.n, a.m, a.k, a.ky, a.dtype, a.hx, a.hy, a.eps, a.tau, a.rho, a.theta, a.warm_start, a.n_outer, a.n_inner,
                a.feat_dim, (void*)a.u, (void*)a.v, (void*)a.phi, (void*)a.psi, a.T, (void*)a.stats);
       key += buf;
     }

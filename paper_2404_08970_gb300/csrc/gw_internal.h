@@ -123,6 +123,12 @@ int marg_const2_launch(const double* wx, int n, double fx, void* outx, const dou
 // Structured gradient on side x side grids with an axis-separable cost
 // (grad2d.cu): Manhattan with k = 1, or squared Euclidean.
 constexpr int kMax2DSide = 256;
+// Mixed distance exponents (1D): supported pairs and row lengths.
+inline bool mixed_k_supported(int k, int ky, int m, int dtype) {
+  if (ky == 0 || ky == k) return true;
+  if (!((k == 1 && ky == 2) || (k == 2 && ky == 1))) return false;
+  return m <= (dtype == GW_F32 ? 8192 : 4096);
+}
 // Longest row a double-precision Sinkhorn pass holds in shared memory.
 constexpr int kMaxSolveF64Y = 10240;
 struct Grad2DArgs {
@@ -155,6 +161,7 @@ int grad2d_powk_launch(const Grad2DArgs& a, void* ws, size_t ws_bytes);
 struct DenseArgs {
   int dim, cost, sx, sy;  // dim 2: sx, sy grid sides, n = sx^2, m = sy^2
   int n, m, k, prec, exact;
+  int ky;                 // 1D: exponent of Y's distance (0: same as k)
   double hx, hy;
   const double *u, *v;
   const void* T;
@@ -189,6 +196,7 @@ struct SolveArgs {
   double tau;      // Sinkhorn regularisation of each step (= eps unless set)
   int warm_start;  // 1: Sinkhorn starts from the previous step's potentials
   double rho;      // > 0: entropic unbalanced GW with marginal relaxation rho
+  int ky;          // 1D: exponent of Y's distance (0: same as k)
   int n_outer, n_inner, feat_dim;
   const double *u, *v, *phi, *psi;
   void* T;

@@ -75,6 +75,7 @@ extern "C" gw_status gw_grad_noalloc(const gw_problem* p, const double* d_u, con
       !(std::isfinite(p->hx) && p->hx > 0.0) || !(std::isfinite(p->hy) && p->hy > 0.0) || (p->dtype != GW_F32 && p->dtype != GW_F64))
     return GW_ERR_INVALID;
   if (marginals != GW_MARG_TARGET && marginals != GW_MARG_EXACT) return GW_ERR_INVALID;
+  if (!gw::mixed_k_supported(p->k, p->ky, p->ny, p->dtype)) return GW_ERR_INVALID;
   if (!d_T || !d_G || (marginals == GW_MARG_TARGET && (!d_u || !d_v))) return GW_ERR_INVALID;
   const size_t esz = p->dtype == GW_F32 ? 4 : 8;
   const size_t nm = (size_t)p->nx * (size_t)p->ny;
@@ -93,6 +94,7 @@ extern "C" gw_status gw_grad_noalloc(const gw_problem* p, const double* d_u, con
   a.n = p->nx;
   a.m = p->ny;
   a.k = p->k;
+  a.ky = p->ky == p->k ? 0 : p->ky;
   a.hx = p->hx;
   a.hy = p->hy;
   a.dtype = p->dtype;

@@ -100,6 +100,7 @@ gw::SolveArgs args_for(const gw_server* s, const gw_problem& p) {
   a.tau = p.tau > 0.0 ? p.tau : p.eps;
   a.warm_start = p.warm_start;
   a.rho = p.rho;
+  a.ky = p.ky == p.k ? 0 : p.ky;
   a.theta = p.theta;
   a.n_outer = p.n_outer;
   a.n_inner = p.n_inner;
@@ -325,7 +326,9 @@ gw_status gw_submit(gw_server* s, const gw_problem* p, const double* h_u, const 
       (q.rho > 0 && (q.theta != 1.0 || (q.tau != 0.0 && q.tau != q.eps))) || q.n_outer < 0 || q.n_inner < 1 ||
       !(q.theta >= 0.0 && q.theta <= 1.0))
     return GW_ERR_INVALID;
-  if (q.dim == 1 && (q.k > 3 || q.ny > 16384)) return GW_ERR_INVALID;
+  if (q.dim == 1 && (q.k > 3 || q.ny > 16384 || !gw::mixed_k_supported(q.k, q.ky, q.ny, q.dtype)))
+    return GW_ERR_INVALID;
+  if (q.dim == 2 && q.ky != 0 && q.ky != q.k) return GW_ERR_INVALID;
   if (q.dim == 2 && ((q.cost != GW_COST_POW && q.cost != GW_COST_SQEUCLID) || q.nx > gw::kMax2DSide ||
                      q.ny > gw::kMax2DSide ||
                      (q.cost == GW_COST_POW && q.k > 1 && !gw::grad2d_powk_supported(q.nx, q.ny, q.k, q.dtype))))

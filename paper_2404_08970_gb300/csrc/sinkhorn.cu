@@ -1083,6 +1083,7 @@ int gradient(const SolveState<Real>& S, int exact, double out_scale, cudaStream_
   ga.n = A.n;
   ga.m = A.m;
   ga.k = A.k;
+  ga.ky = A.ky;
   ga.hx = A.hx;
   ga.hy = A.hy;
   ga.dtype = A.dtype;

@@ -101,3 +101,26 @@ def test_dense_tc_2d(prec):
     DY = O.grid_dist_2d(sy, 1 / (sy - 1), "sqeuclid")
     Gs = O.grad(DX, DY, T.astype(np.float64), u, v)
     assert U.relerr(dG.double().cpu().numpy(), Gs) <= BOUND[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tc_bf16"])
+def test_dense_mixed_exponents(prec):
+    """Dense path with k_X = 1, k_Y = 2."""
+    import torch
+    from oracle import gw_oracle as O
+    from paper_2404_08970_gb300 import _lib as L
+    n, m = 96, 130
+    rng = np.random.default_rng(55)
+    u, v = I.dirichlet(n, 1.0, rng), I.dirichlet(m, 1.0, rng)
+    T = I.random_coupling(u, v, rng)
+    Tc = T if prec == "fp64" else T.astype(np.float32)
+    c = U.ctx()
+    dT = torch.from_numpy(np.ascontiguousarray(Tc)).cuda()
+    dG = torch.empty_like(dT)
+    prob = L.problem(dim=1, nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=1, ky=2,
+                     dtype=L.GW_F64 if prec == "fp64" else L.GW_F32)
+    P = L.GW_DENSE_FP64 if prec == "fp64" else L.GW_DENSE_TC_BF16
+    c.gw_grad_dense(prob, torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), dT, dG, L.GW_MARG_TARGET, P)
+    c.gw_ctx_check()
+    Gs = O.grad(O.grid_dist_1d(n, 1.0 / n, 1), O.grid_dist_1d(m, 1.0 / m, 2), Tc.astype(np.float64), u, v)
+    assert U.relerr(dG.double().cpu().numpy(), Gs) <= BOUND[prec]

@@ -144,3 +144,48 @@ def test_grad1d_peaked_late_iterate_plan(n, m, k):
         Gs = U.oracle_grad_1d(Tc.astype(np.float64), u, v, k, hx, hy, marg)
         err = U.relerr(G, Gs)
         assert err <= TOL["f32"], f"{marg} rel err {err:.3e}"
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("k,ky", [(1, 2), (2, 1)])
+@pytest.mark.parametrize("shape", [(1, 5), (37, 61), (300, 257), (1000, 1024), (150, 4096), (40, 8192)],
+                         ids=lambda s: f"{s[0]}x{s[1]}")
+def test_grad1d_mixed_exponents(shape, k, ky, dtype):
+    """k_X != k_Y (Sec. 2 takes separate exponents): D_X = h_X^k |i-j|^k,
+    D_Y = h_Y^ky |p-q|^ky."""
+    import torch
+    from oracle import gw_oracle as O
+    from paper_2404_08970_gb300 import _lib as L
+    n, m = shape
+    if dtype == "f64" and m > 4096:
+        pytest.skip("mixed exponents in double take rows of at most 4096 columns")
+    u, v, T = _case(n, m, 500 + n + m + k)
+    hx, hy = 1.0 / n, 1.0 / m
+    Tc = T.astype(np.float32) if dtype == "f32" else T
+    c = U.ctx()
+    tdt = torch.float32 if dtype == "f32" else torch.float64
+    dT = torch.from_numpy(np.ascontiguousarray(Tc)).to("cuda", tdt)
+    dG = torch.empty_like(dT)
+    prob = L.problem(dim=1, nx=n, ny=m, hx=hx, hy=hy, k=k, ky=ky, dtype=L.GW_F32 if dtype == "f32" else L.GW_F64)
+    DX, DY = O.grid_dist_1d(n, hx, k), O.grid_dist_1d(m, hy, ky)
+    for marg in ("target", "exact"):
+        mg = L.GW_MARG_TARGET if marg == "target" else L.GW_MARG_EXACT
+        c.gw_grad(prob, torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(), dT, dG, mg)
+        c.gw_ctx_check()
+        T64 = Tc.astype(np.float64)
+        Gs = O.grad(DX, DY, T64, u, v) if marg == "target" else O.grad_exact(DX, DY, T64)
+        err = U.relerr(dG.double().cpu().numpy(), Gs)
+        assert err <= TOL[dtype], f"{marg} rel err {err:.3e}"
+
+
+def test_grad1d_mixed_exponents_rejected_where_unsupported():
+    import torch
+    from paper_2404_08970_gb300 import _lib as L
+    c = U.ctx()
+    T = torch.zeros(4, 9000, device="cuda")
+    G = torch.zeros_like(T)
+    for kw in (dict(k=1, ky=3, ny=16), dict(k=1, ky=2, ny=9000), dict(k=3, ky=1, ny=16)):
+        prob = L.problem(dim=1, nx=4, hx=0.25, hy=0.1, **kw)
+        with pytest.raises(L.GWError) as e:
+            c.gw_grad(prob, None, None, T, G, L.GW_MARG_EXACT)
+        assert e.value.status == L.GW_ERR_INVALID

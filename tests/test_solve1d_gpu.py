@@ -36,7 +36,7 @@ def gpu_solve(w, dtype, theta=1.0, phi=None, psi=None):
     prob = L.problem(dim=1, nx=n, ny=m, hx=w["hx"], hy=w["hy"], k=w["k"], eps=w["eps"], n_outer=w["n_outer"],
                      n_inner=w["n_inner"], theta=theta, feat_dim=D,
                      dtype=L.GW_F32 if dtype == "f32" else L.GW_F64, tau=w.get("tau", 0.0),
-                     warm_start=int(w.get("warm", False)))
+                     warm_start=int(w.get("warm", False)), ky=w.get("ky", 0))
     c.gw_solve(prob, du, dv, T, f, g, stats, dphi, dpsi)
     c.gw_ctx_check()
     return T.double().cpu().numpy(), f.cpu().numpy(), g.cpu().numpy(), stats.cpu().numpy()
@@ -44,7 +44,7 @@ def gpu_solve(w, dtype, theta=1.0, phi=None, psi=None):
 
 def oracle_solve(w, theta=1.0, phi=None, psi=None):
     n, m, k = w["nx"], w["ny"], w["k"]
-    DX, DY = O.grid_dist_1d(n, w["hx"], k), O.grid_dist_1d(m, w["hy"], k)
+    DX, DY = O.grid_dist_1d(n, w["hx"], k), O.grid_dist_1d(m, w["hy"], w.get("ky") or k)
     CC = None if phi is None else O.fgw_feature_cost(phi, psi)
     T, f, g = O.mirror_descent(DX, DY, w["u"], w["v"], w["eps"], w["n_outer"], w["n_inner"], theta=theta, CC=CC,
                                tau=w.get("tau"), warm_start=w.get("warm", False))
@@ -156,6 +156,23 @@ def test_solve_tau_and_warm_start(shape, k, tau_over_eps, warm, dtype):
         assert abs(st[1] - ss["E"]) <= 1e-5 * abs(ss["E"])
         assert fro(T, Ts) < 1e-3
         assert st[5] < 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("k,ky", [(1, 2), (2, 1)])
+def test_solve_mixed_exponents(k, ky, dtype):
+    n, m = 70, 300
+    rng = np.random.default_rng(n + m + 10 * k)
+    w = dict(nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=k, ky=ky, eps=5e-2, n_outer=5, n_inner=40,
+             u=I.dirichlet(n, 1.0, rng), v=I.dirichlet(m, 1.0, rng))
+    T, f, g, st = gpu_solve(w, dtype)
+    Ts, fs, gs, ss = oracle_solve(w)
+    if dtype == "f64":
+        assert U.relerr(T, Ts) < 1e-9
+        assert abs(st[1] - ss["E"]) <= 1e-10 * abs(ss["E"])
+    else:
+        assert abs(st[1] - ss["E"]) <= 1e-5 * abs(ss["E"])
+        assert fro(T, Ts) < 1e-3
 
 
 def test_solve_reflection_and_single_point():
