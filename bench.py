@@ -36,6 +36,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--m", type=int, default=0, help="columns of the gradient workload (default: n)")
     ap.add_argument("--k", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", dest="solve", action="store_false")
@@ -74,21 +75,30 @@ def dist_env():
     return rank, world, local
 
 
-def workload(n, k):
+def workload(n, k, m=None):
+    """The gradient workload: n x m grids (m = n unless given), uniform
+    marginals, the random positive coupling, h = 1/n and 1/m."""
     from paper_2404_08970_gb300 import inputs as I
-    return I.workload_1d_grad(n, k, "uniform", seed=0)
+    if m is None or m == n:
+        return I.workload_1d_grad(n, k, "uniform", seed=0)
+    import numpy as np
+    rng = np.random.default_rng(0)
+    u, v = I.uniform_weights(n), I.uniform_weights(m)
+    return dict(T=I.random_coupling(u, v, rng), u=u, v=v, hx=1.0 / n, hy=1.0 / m, k=k)
 
 
 L2_BYTES = 126 * 2 ** 20
 
 
-def config(n, k, extra=None):
-    mb = 4 * n * n / 1e6
-    l2 = (f"inputs larger than L2 ({mb:.0f} MB T, {mb:.0f} MB G)" if 4 * n * n > L2_BYTES else
+def config(n, k, extra=None, m=None):
+    m = n if m is None else m
+    mb = 4 * n * m / 1e6
+    l2 = (f"inputs larger than L2 ({mb:.0f} MB T, {mb:.0f} MB G)" if 4 * n * m > L2_BYTES else
           f"inputs fit in L2 ({mb:.1f} MB T, {mb:.1f} MB G): not a valid bench size, for profiling only")
-    c = {"workload": f"1D uniform grids n=m={n}, k={k}, uniform marginals, random positive coupling, h=1/n; "
+    shape = f"n=m={n}" if m == n else f"n={n}, m={m}"
+    c = {"workload": f"1D uniform grids {shape}, k={k}, uniform marginals, random positive coupling, h=1/n; "
                      f"one structured gradient evaluation per step",
-         "n": n, "m": n, "k": k, "marginals": "target (uniform)", "l2": l2,
+         "n": n, "m": m, "k": k, "marginals": "target (uniform)", "l2": l2,
          "global_batch": 1, "parallelism": "replicas"}
     if extra:
         c.update(extra)
@@ -512,7 +522,8 @@ def run_ours(args):
     from paper_2404_08970_gb300 import _lib as L
 
     n, k = args.n, args.k
-    w = workload(n, k)
+    m = args.m or n
+    w = workload(n, k, m)
     ctx = L.Context(local)
     dev = torch.device("cuda", local)
     T32 = torch.from_numpy(w["T"].astype(np.float32))
@@ -520,7 +531,7 @@ def run_ours(args):
     dG = torch.empty_like(dT)
     du = torch.from_numpy(w["u"]).to(dev)
     dv = torch.from_numpy(w["v"]).to(dev)
-    prob = L.problem(dim=1, nx=n, ny=n, hx=w["hx"], hy=w["hy"], k=k, dtype=L.GW_F32)
+    prob = L.problem(dim=1, nx=n, ny=m, hx=w["hx"], hy=w["hy"], k=k, dtype=L.GW_F32)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -574,7 +585,7 @@ def run_ours(args):
     hbm_peak, bf16_peak, peak_kind = measured_peaks()
     dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
     launches = sum(v["launches"] for v in prof.values()) if prof else 0
-    nm = n * n
+    nm = n * m
     roof = None
     if dom[0]:
         avg_ms = dom[1]["ms"] / max(1, dom[1]["launches"])
@@ -582,7 +593,7 @@ def run_ours(args):
         achieved = alg_bytes / (avg_ms / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": dom[0], "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "peak_kind": f"hbm_gbs of {peak_kind}",
-                "traffic": kernel_traffic(dom[0]) if n == 8192 and k == 1 else None,
+                "traffic": kernel_traffic(dom[0]) if n == 8192 and m == 8192 and k == 1 else None,
                 "alg_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_ms,
                 "timing": "kernel durations from CUDA events in a second region of the same K gradients "
                           f"launched eagerly ({ms_profiled / args.steps:.4f} ms per gradient there)"}
@@ -627,14 +638,14 @@ def run_ours(args):
             barrier()
             dms = e0.elapsed_time(e1) / ds
             dense[name] = {"evals_per_s": 1e3 / dms, "ms": dms,
-                           "tflops": 2.0 * 2.0 * n * n * n / (dms / 1e3) / 1e12}
+                           "tflops": 2.0 * n * m * (n + m) / (dms / 1e3) / 1e12}
         except Exception as ex:  # reported, not hidden
             dense[name] = {"error": str(ex)[:200]}
     # The structured gradient in FP64 on the same T (the paper's precision).
     try:
         dT64 = dT.double()
         dG64 = torch.empty_like(dT64)
-        prob64 = L.problem(dim=1, nx=n, ny=n, hx=w["hx"], hy=w["hy"], k=k, dtype=L.GW_F64)
+        prob64 = L.problem(dim=1, nx=n, ny=m, hx=w["hx"], hy=w["hy"], k=k, dtype=L.GW_F64)
         for _ in range(3):
             ctx.gw_grad(prob64, du, dv, dT64, dG64, L.GW_MARG_TARGET, stream)
         barrier()
@@ -676,10 +687,10 @@ def run_ours(args):
     # Full entropic GW solve on the same grids (20 outer x 100 Sinkhorn), one run.
     solve = None
     if args.solve:
-        w_s = workload(n, k)
+        w_s = workload(n, k, m)
         dTs = torch.empty_like(dT)
         stats = torch.zeros(8, dtype=torch.float64, device=dev)
-        sprob = L.problem(dim=1, nx=n, ny=n, hx=w_s["hx"], hy=w_s["hy"], k=k, eps=1e-2, n_outer=20,
+        sprob = L.problem(dim=1, nx=n, ny=m, hx=w_s["hx"], hy=w_s["hy"], k=k, eps=1e-2, n_outer=20,
                           n_inner=100, dtype=L.GW_F32)
         ctx.gw_solve(sprob, du, dv, dTs, None, None, stats, stream=stream)  # captures the graph
         barrier()
@@ -736,7 +747,7 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(n, k),
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(n, k, m=m),
                 "roofline": roof, "whole_gradient_gbs": whole_gbs, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clk, "gpu_launches": launches, "kernels": prof, "dense": dense,
                 "structured_f64": structured_f64,
