@@ -7,9 +7,9 @@ calls it and shares no code with it.
 Everything here is the textbook definition written out in float64, slow and
 direct, each function citing the part of the paper it follows:
 
-* distance matrices on uniform 1D grids (Sec. 2, eq. "1d distance matrices")
-  and 2D grids (Sec. 3.1, eq. "2d Dx"; squared-Euclidean added for the 2D
-  workload),
+* distance matrices on uniform 1D grids (Sec. 2, eq. "1d distance matrices"),
+  2D grids (Sec. 3.1, eq. "2d Dx"; squared-Euclidean added for the 2D
+  workload) and 3D grids (the same construction with a third axis),
 * the gradient decomposition grad E = C1 - 4 D_X Gamma D_Y (Sec. 2.1); this
   module returns G = grad E / 2 = c_x 1^T + 1 c_y^T - 2 D_X T D_Y,
 * the brute-force gradient entry (Sec. 2.1, eq. "gradient entry"),
@@ -64,6 +64,28 @@ def grid_dist_2d(side: int, h: float, cost: str, k: int = 1) -> np.ndarray:
         return (h ** k) * (da + db) ** k
     if cost == "sqeuclid":
         return (h ** 2) * (da ** 2 + db ** 2)
+    raise ValueError(cost)
+
+
+def grid_dist_3d(side: int, h: float, cost: str, k: int = 1) -> np.ndarray:
+    """Distance matrix of a side x side x side uniform grid, points flattened
+    row-major (index (a*side + b)*side + c); the 3D case of the grids of
+    Sec. 3.1 ("no essential difference" from 2D).
+
+    cost = "manhattan": h^k (|a-a'| + |b-b'| + |c-c'|)^k.
+    cost = "sqeuclid":  h^2 ((a-a')^2 + (b-b')^2 + (c-c')^2).
+    """
+    idx = np.arange(side ** 3)
+    a = (idx // (side * side)).astype(np.float64)
+    b = ((idx // side) % side).astype(np.float64)
+    c = (idx % side).astype(np.float64)
+    da = np.abs(a[:, None] - a[None, :])
+    db = np.abs(b[:, None] - b[None, :])
+    dc = np.abs(c[:, None] - c[None, :])
+    if cost == "manhattan":
+        return (h ** k) * (da + db + dc) ** k
+    if cost == "sqeuclid":
+        return (h ** 2) * (da ** 2 + db ** 2 + dc ** 2)
     raise ValueError(cost)
 
 

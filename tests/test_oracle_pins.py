@@ -703,3 +703,61 @@ def test_ugw_reflection():
     T, _, _ = O.ugw_solve(DX, DY, u, v, 0.05, 0.5, 5, 50)
     Tr, _, _ = O.ugw_solve(DX, DY, u, v[::-1].copy(), 0.05, 0.5, 5, 50)
     assert relerr(Tr[:, ::-1], T) < 1e-11
+
+
+# ---------------------------------------------------------------------------
+# 3D grids
+# ---------------------------------------------------------------------------
+
+def test_grid_dist_3d_entries():
+    """Points (0,0,0), (1,1,1), (0,1,1) of a 2 x 2 x 2 grid (indices 0, 7, 3)."""
+    D = O.grid_dist_3d(2, 0.5, "manhattan")
+    assert D[0, 7] == 1.5 and D[0, 3] == 1.0 and D[3, 7] == 0.5 and D[7, 7] == 0.0
+    S = O.grid_dist_3d(3, 2.0, "sqeuclid")
+    i, j = (0 * 3 + 1) * 3 + 2, (2 * 3 + 0) * 3 + 0   # (0,1,2) and (2,0,0)
+    assert S[i, j] == 4.0 * (4 + 1 + 4)
+    D2 = O.grid_dist_3d(3, 1.0, "manhattan", 2)
+    assert D2[i, j] == (2 + 1 + 2) ** 2
+
+
+@pytest.mark.parametrize("cost", ["manhattan", "sqeuclid"])
+def test_3d_kronecker_sum(cost):
+    """Separable 3D cost: D-hat = A (x) J (x) J + J (x) A (x) J + J (x) J (x) A with
+    A the 1D |i-j| (Manhattan) or (i-j)^2 (squared Euclidean) matrix."""
+    s = 4
+    A = O.grid_dist_1d(s, 1.0, 1 if cost == "manhattan" else 2)
+    J = np.ones((s, s))
+    want = np.kron(np.kron(A, J), J) + np.kron(np.kron(J, A), J) + np.kron(np.kron(J, J), A)
+    assert np.array_equal(O.grid_dist_3d(s, 1.0, cost), want)
+
+
+@pytest.mark.parametrize("cost", ["manhattan", "sqeuclid"])
+def test_3d_nine_marginal_identity(cost):
+    """The form the 3D GPU path computes: D_X T D_Y = sum over X axes alpha and
+    Y axes beta of (A_X M_ab A_Y)[i_alpha, p_beta], M_ab the sums of T over all
+    other axes (side x side matrices)."""
+    sx, sy = 3, 4
+    rng = np.random.default_rng(71)
+    T = rng.uniform(0.0, 1.0, size=(sx ** 3, sy ** 3))
+    e = 1 if cost == "manhattan" else 2
+    AX, AY = O.grid_dist_1d(sx, 1.0, e), O.grid_dist_1d(sy, 1.0, e)
+    T6 = T.reshape(sx, sx, sx, sy, sy, sy)
+    Z = np.zeros((sx, sx, sx, sy, sy, sy))
+    for al in range(3):
+        for be in range(3):
+            keep = [al, 3 + be]
+            M = T6.sum(axis=tuple(q for q in range(6) if q not in keep))   # sx x sy
+            Zab = AX @ M @ AY
+            shape = [1] * 6
+            shape[al], shape[3 + be] = sx, sy
+            Z = Z + Zab.reshape(shape)
+    want = O.grid_dist_3d(sx, 1.0, cost) @ T @ O.grid_dist_3d(sy, 1.0, cost)
+    assert relerr(Z.reshape(sx ** 3, sy ** 3), want) < 1e-13
+
+
+def test_3d_gradient_matches_brute_force():
+    sx, sy = 2, 3
+    rng = np.random.default_rng(72)
+    T = rng.uniform(0.1, 1.0, size=(sx ** 3, sy ** 3))
+    DX, DY = O.grid_dist_3d(sx, 0.7, "sqeuclid"), O.grid_dist_3d(sy, 0.4, "sqeuclid")
+    assert relerr(O.grad_exact(DX, DY, T), O.grad_brute(DX, DY, T)) < 1e-12
