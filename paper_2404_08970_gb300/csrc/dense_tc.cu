@@ -118,6 +118,19 @@ __device__ __forceinline__ void epi_store(const TcEpilogue& e, int row, int col0
   }
 }
 
+// Tile t of the persistent schedule: groups of kGroupRows row tiles, each
+// group walked column tile by column tile, so that the ~152 tiles in flight at
+// once touch few A and B stripes (they stay in L2).
+constexpr int kGroupRows = 8;
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int& tm, int& tn) {
+  const int group = t / (kGroupRows * tiles_n);
+  const int first = group * kGroupRows;
+  const int gsize = min(kGroupRows, tiles_m - first);
+  const int r = t - group * kGroupRows * tiles_n;
+  tm = first + r % gsize;
+  tn = r / gsize;
+}
+
 template <bool TF32>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_abt(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, int M, int N,
@@ -168,7 +181,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t ph = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-        const int tm = t % tiles_m, tn = t / tiles_m;
+        int tm, tn;
+        tile_coords(t, tiles_m, tiles_n, tm, tn);
         for (int kb = 0; kb < kb_count; ++kb) {
           if (!mbar_wait_bounded(&empty[s], ph ^ 1u, status)) {
             ok = false;
@@ -243,7 +257,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       const bool ok = mbar_wait_bounded(&acc_full[a], aph, status);
       if (!__all_sync(0xffffffffu, ok)) break;
       tc::fence_after_sync();
-      const int tm = t % tiles_m, tn = t / tiles_m;
+      int tm, tn;
+        tile_coords(t, tiles_m, tiles_n, tm, tn);
       const int row = tm * kBM + quarter * 32 + lane;
       const uint32_t base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * kBN);
 #pragma unroll 1
