@@ -89,6 +89,19 @@ def grid_dist_3d(side: int, h: float, cost: str, k: int = 1) -> np.ndarray:
     raise ValueError(cost)
 
 
+def grid_dist_3d_rows(side: int, h: float, cost: str, rows, k: int = 1) -> np.ndarray:
+    """Rows `rows` of grid_dist_3d(side, h, cost, k), formed without the whole
+    matrix (the same definition, for grids too large to hold D in full)."""
+    idx = np.arange(side ** 3)
+    co = np.stack([idx // (side * side), (idx // side) % side, idx % side], axis=1).astype(np.float64)
+    d = np.abs(co[np.asarray(rows)][:, None, :] - co[None, :, :])
+    if cost == "manhattan":
+        return (h ** k) * d.sum(axis=-1) ** k
+    if cost == "sqeuclid":
+        return (h ** 2) * (d * d).sum(axis=-1)
+    raise ValueError(cost)
+
+
 # ---------------------------------------------------------------------------
 # Gradient
 # ---------------------------------------------------------------------------

@@ -720,6 +720,19 @@ def test_grid_dist_3d_entries():
     assert D2[i, j] == (2 + 1 + 2) ** 2
 
 
+@pytest.mark.parametrize("cost,k", [("manhattan", 1), ("manhattan", 2), ("sqeuclid", 1)])
+def test_grid_dist_3d_rows_are_rows_of_the_matrix(cost, k):
+    rows = [0, 7, 31, 124, 63]
+    D = O.grid_dist_3d(5, 0.3, cost, k)
+    assert np.array_equal(O.grid_dist_3d_rows(5, 0.3, cost, rows, k), D[rows])
+    R = O.grid_dist_3d_rows(5, 0.3, cost, rows, k)
+    # point 7 = (0, 1, 2) against point 0: coordinate differences 0, 1, 2
+    want = 0.3 ** k * 3 ** k if cost == "manhattan" else 0.09 * 5
+    assert abs(R[1, 0] - want) < 1e-15
+    # planted mistake: rows off by one
+    assert not np.array_equal(R, D[[(r + 1) % 125 for r in rows]])
+
+
 @pytest.mark.parametrize("cost", ["manhattan", "sqeuclid"])
 def test_3d_kronecker_sum(cost):
     """Separable 3D cost: D-hat = A (x) J (x) J + J (x) A (x) J + J (x) J (x) A with
