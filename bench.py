@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", dest="solve", action="store_false")
     ap.add_argument("--no-2d", dest="grid2d", action="store_false")
+    ap.add_argument("--no-3d", dest="grid3d", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--no-serve", dest="serve", action="store_false")
@@ -326,6 +327,85 @@ def bench_2d(ctx, L, dev, stream, barrier, steps, with_solve):
         dTs = torch.empty_like(dT)
         stats = torch.zeros(8, dtype=torch.float64, device=dev)
         sprob = L.problem(dim=2, nx=64, ny=96, hx=w["hx"], hy=w["hy"], k=1, cost=L.GW_COST_SQEUCLID, eps=5e-3,
+                          n_outer=20, n_inner=100, dtype=L.GW_F32)
+        solve = lambda: ctx.gw_solve(sprob, du, dv, dTs, None, None, stats, stream=stream)
+        solve()
+        barrier()
+        sms = timed(solve, 1)
+        ctx.gw_ctx_check(stream)
+        out["solve"] = {"schedule": "eps=5e-3, 20 x 100", "solves_per_s": 1e3 / sms, "ms": sms,
+                        "gw_value": float(stats[1].item()), "col_marginal_err": float(stats[5].item())}
+    return out
+
+
+def bench_3d(ctx, L, dev, stream, barrier, steps, with_solve):
+    """3D grids 16^3 against 21^3 (n = 4096, m = 9261), squared Euclidean cost
+    on the unit cube, |N(0,1)| voxel marginals: structured gradient vs the
+    dense BF16 path, and the solve at eps = 5e-3, 20 x 100."""
+    import numpy as np
+    import torch
+    from paper_2404_08970_gb300 import inputs as I
+    sx, sy = 16, 21
+    w = I.workload_3d(sx, sy, "sqeuclid", seed=0)
+    T = I.random_coupling(w["u"], w["v"], I.rng_for(1)).astype(np.float32)
+    n, m = T.shape
+    dT = torch.from_numpy(T).to(dev)
+    dG = torch.empty_like(dT)
+    du = torch.from_numpy(w["u"]).to(dev)
+    dv = torch.from_numpy(w["v"]).to(dev)
+    prob = L.problem(dim=3, nx=sx, ny=sy, hx=w["hx"], hy=w["hy"], k=1, cost=L.GW_COST_SQEUCLID, dtype=L.GW_F32)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        barrier()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / reps
+
+    grad = lambda: ctx.gw_grad(prob, du, dv, dT, dG, L.GW_MARG_TARGET, stream)
+    gms = timed(grad, steps)
+    ctx.gw_ctx_profile(True)
+    ctx.gw_ctx_profile_report(reset=True)
+    for _ in range(steps):
+        grad()
+    barrier()
+    prof = ctx.gw_ctx_profile_report(reset=True)
+    ctx.gw_ctx_profile(False)
+    ctx.gw_ctx_check(stream)
+    hbm_peak, _, peak_kind = measured_peaks()
+    roof = {}
+    for kname in ("g3_rows", "g3_epi"):
+        if kname in prof:
+            avg = prof[kname]["ms"] / max(1, prof[kname]["launches"])
+            gbs = 4.0 * n * m / (avg / 1e3) / 1e9  # g3_rows reads T, g3_epi writes G: 4 B per element each
+            roof[kname] = {"avg_launch_ms": avg, "achieved_gbs": gbs, "frac": gbs / hbm_peak,
+                           "peak_kind": f"hbm_gbs of {peak_kind}"}
+    # The dense comparison: cuBLAS BF16 and the library's tcgen05 BF16 kernel
+    # (zero-padded rows; 21^3 columns are not a multiple of 8), the better one.
+    dense_ms = {}
+    for name, prec in (("cublas_bf16", L.GW_DENSE_BF16), ("tc_bf16", L.GW_DENSE_TC_BF16)):
+        try:
+            dense_ms[name] = timed(lambda: ctx.gw_grad_dense(prob, du, dv, dT, dG, L.GW_MARG_TARGET, prec, stream), 5)
+        except Exception as ex:
+            roof[f"dense_{name}_error"] = str(ex)[:200]
+    dms = min(dense_ms.values()) if dense_ms else None
+    out = {"workload": f"3D grids {sx}^3 vs {sy}^3 (n={n}, m={m}), squared Euclidean, unit cube, "
+                       "|N(0,1)| voxel marginals, random positive coupling, fp32",
+           "grad_evals_per_s": 1e3 / gms, "grad_ms": gms, "whole_gradient_gbs": 8.0 * n * m / (gms / 1e3) / 1e9,
+           "kernels": prof, "roofline": roof,
+           "dense_ms": dense_ms,
+           "dense_bf16_evals_per_s": (1e3 / dms) if dms else None,
+           "structured_over_dense_bf16": (dms / gms) if dms else None}
+    if with_solve:
+        dTs = torch.empty_like(dT)
+        stats = torch.zeros(8, dtype=torch.float64, device=dev)
+        sprob = L.problem(dim=3, nx=sx, ny=sy, hx=w["hx"], hy=w["hy"], k=1, cost=L.GW_COST_SQEUCLID, eps=5e-3,
                           n_outer=20, n_inner=100, dtype=L.GW_F32)
         solve = lambda: ctx.gw_solve(sprob, du, dv, dTs, None, None, stats, stream=stream)
         solve()
@@ -721,6 +801,7 @@ def run_ours(args):
                          "replaces only the 20 gradients by the best dense gradient time"}
 
     grid2d = bench_2d(ctx, L, dev, stream, barrier, min(args.steps, 20), args.solve) if args.grid2d else None
+    grid3d = bench_3d(ctx, L, dev, stream, barrier, min(args.steps, 20), args.solve) if args.grid3d else None
     batch = bench_batch(ctx, L, dev, stream, barrier, args.batch_count) if args.batch else None
     serve = bench_serve(L, local, args.serve_count, args.serve_slots) if args.serve else None
 
@@ -752,7 +833,7 @@ def run_ours(args):
                 "clocks": clk, "gpu_launches": launches, "kernels": prof, "dense": dense,
                 "structured_f64": structured_f64,
                 "errors_vs_fp64": errs, "solve": solve,
-                "grid2d": grid2d, "batch": batch, "serve": serve}
+                "grid2d": grid2d, "grid3d": grid3d, "batch": batch, "serve": serve}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -76,11 +76,12 @@ typedef enum { GW_MARG_TARGET = 0, GW_MARG_EXACT = 1 } gw_marginals;
 
 /* Problem descriptor, following the paper's problem statement (Sec. 2). */
 typedef struct gw_problem {
-  int dim;       /* 1 or 2 */
-  int nx, ny;    /* 1D: points of X and Y; 2D: grid sides (points = side^2) */
+  int dim;       /* 1, 2 or 3 */
+  int nx, ny;    /* 1D: points of X and Y; 2D, 3D: grid sides (points =
+                    side^dim) */
   double hx, hy; /* grid spacings h_X, h_Y (> 0) */
   int k;         /* distance exponent, integer >= 1 (k_X = k_Y = k) */
-  int cost;      /* gw_cost (2D only; 1D uses GW_COST_POW) */
+  int cost;      /* gw_cost (2D and 3D; 1D uses GW_COST_POW) */
   double eps;    /* entropic regularisation (> 0), solver only */
   int n_outer;   /* mirror-descent iterations, solver only */
   int n_inner;   /* Sinkhorn iterations per mirror-descent step, solver only */
@@ -136,14 +137,21 @@ gw_status gw_ctx_profile_report(gw_ctx* ctx, char* buf, size_t len, int reset);
 /*
  * gw_grad - the structured gradient G = L(C_X, C_Y) (x) T (Sec. 3, eqs. "Dx",
  * "1d y", "1d recursive relation"; Sec. 3.1, eqs. "2d gradient" and
- * "2D kronecker").
+ * "2D kronecker"; 3D grids by the same construction with a third axis, which
+ * Sec. 3.1 says differs in nothing essential).
  *
  *   prob       dim 1: any k >= 1 up to 3, nx, ny >= 1, ny <= 16384.
  *              dim 2: grid sides nx, ny in [1, 256] (n = nx^2, m = ny^2
  *              points, index a * side + b), cost GW_COST_SQEUCLID, or
  *              GW_COST_POW with k = 1 (Manhattan): the costs that split over
  *              the two axes, so that D_X T D_Y reduces to four side x side
- *              partial sums of T (k = 1 case of eq. "2D kronecker").
+ *              partial sums of T (k = 1 case of eq. "2D kronecker");
+ *              GW_COST_POW with k = 2, 3 (Manhattan^k, image transforms by
+ *              the paper's recursion) for sides up to 128 in float.
+ *              dim 3: grid sides nx, ny in [1, 32] (n = nx^3, m = ny^3
+ *              points, index (a * side + b) * side + c), cost
+ *              GW_COST_SQEUCLID or GW_COST_POW with k = 1: D_X T D_Y reduces
+ *              to nine side x side partial sums of T.
  *              Only dim, nx, ny, hx, hy, k, cost, dtype are read.
  *   d_u, d_v   target marginals, double, lengths n and m; read only with
  *              marginals == GW_MARG_TARGET (may be NULL otherwise).
@@ -152,7 +160,7 @@ gw_status gw_ctx_profile_report(gw_ctx* ctx, char* buf, size_t len, int reset);
  *   marginals  GW_MARG_TARGET or GW_MARG_EXACT.
  *
  * Cost O(n m): the DP recursion along columns and rows (1D), or one pass
- * over T plus side x side transforms (2D), replaces the dense products.
+ * over T plus side x side transforms (2D, 3D), replaces the dense products.
  * With dtype GW_F32 the arithmetic is float with compensated sums and
  * carries; GW_F64 computes in double throughout.
  * Errors: GW_ERR_INVALID for a bad descriptor or a NULL required pointer.
@@ -235,8 +243,8 @@ gw_status gw_grad_noalloc(const gw_problem* prob, const double* d_u, const doubl
  *              is never stored); inputs rounded as for the cuBLAS forms
  *              (TF32 keeps the top 19 bits of each float).
  *   prob->dtype must be GW_F64 for GW_DENSE_FP64 and GW_F32 otherwise; the
- *   other arguments are as for gw_grad (dim 1 or 2; in 2D the distance
- *   matrices are n x n and m x m over the grid points).  The dense distance
+ *   other arguments are as for gw_grad (dim 1, 2 or 3; on grids the
+ *   distance matrices are n x n and m x m over the grid points).  The dense distance
  *   matrices are cached in the context between calls.
  */
 gw_status gw_grad_dense(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const double* d_v,
@@ -257,8 +265,8 @@ gw_status gw_grad_dense(gw_ctx* ctx, const gw_problem* prob, const double* d_u, 
  * after the first step), f then g each iteration, then sets
  * T_ip = exp((f_i + g_p - Pi_ip) / tau).
  *
- *   prob         dim 1 or 2; nx, ny, hx, hy, k, cost as for gw_grad, with at
- *                most 16384 points in Y (ny, or ny^2 in 2D; 10240 with
+ *   prob         dim 1, 2 or 3; nx, ny, hx, hy, k, cost as for gw_grad, with
+ *                at most 16384 points in Y (ny, or ny^dim on grids; 10240 with
  *                GW_F64); eps > 0;
  *                tau = 0 (tau = eps) or > 0; warm_start 0 or 1;
  *                n_outer >= 0; n_inner >= 1; theta in [0, 1]; feat_dim in

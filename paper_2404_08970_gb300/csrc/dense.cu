@@ -14,23 +14,41 @@
 
 namespace gw {
 
-// D[i][j] = d(i, j) for n points: 1D grid (side = 0): h^k |i - j|^k; 2D grid
-// of side x side points (i = a * side + b): Manhattan h (|a-a'| + |b-b'|)
-// (sq = 0) or squared Euclidean h^2 ((a-a')^2 + (b-b')^2) (sq = 1).
+// Absolute coordinate differences of grid points i and j on a side^dims grid
+// (row-major, the last axis fastest; dims = 2 or 3).
+__device__ __forceinline__ void grid_deltas(long long i, long long j, int side, int dims, double (&d)[3]) {
+  for (int t = dims - 1; t >= 0; --t) {
+    d[t] = (double)llabs(i % side - j % side);
+    i /= side;
+    j /= side;
+  }
+  if (dims < 3) d[2] = 0.0;
+}
+
+// Grid distance from coordinate differences: Manhattan^k (sq = 0) or squared
+// Euclidean (sq = 1), without the spacing factor.
+__device__ __forceinline__ double grid_metric(const double (&d)[3], int k, int sq) {
+  if (sq) return d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+  const double s = d[0] + d[1] + d[2];
+  double v = 1.0;
+  for (int e = 0; e < k; ++e) v *= s;
+  return v;
+}
+
+// D[i][j] = d(i, j) for n points: 1D grid (side = 0): h^k |i - j|^k; grid of
+// side^dims points (row-major): Manhattan h^k (sum_t |x_t - x'_t|)^k (sq = 0)
+// or squared Euclidean h^2 sum_t (x_t - x'_t)^2 (sq = 1).
 template <typename Out>
-__global__ void build_dist(Out* __restrict__ D, int n, double hk, int k, int side, int sq, int pitch, int tf32) {
+__global__ void build_dist(Out* __restrict__ D, int n, double hk, int k, int side, int dims, int sq, int pitch,
+                           int tf32) {
   const size_t N = (size_t)n * n;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < N; idx += (size_t)gridDim.x * blockDim.x) {
     const long long i = (long long)(idx / n), j = (long long)(idx % n);
     double v;
     if (side > 0) {
-      const double da = (double)llabs(i / side - j / side), db = (double)llabs(i % side - j % side);
-      if (sq) {
-        v = da * da + db * db;
-      } else {  // Manhattan distance to the power k
-        v = 1.0;
-        for (int e = 0; e < k; ++e) v *= da + db;
-      }
+      double d[3];
+      grid_deltas(i, j, side, dims, d);
+      v = grid_metric(d, k, sq);
     } else {
       const double d = (double)(i > j ? i - j : j - i);
       v = 1.0;
@@ -115,23 +133,19 @@ __global__ void dense_epilogue(Real* __restrict__ G, int n, int m, const Real* _
   }
 }
 
-// Constant term on a 2D grid, pointwise: c[i] = scale * sum_j d(i,j)^2 w_j
-// with d the Manhattan or squared Euclidean grid distance (one block per i).
+// Constant term on a 2D or 3D grid, pointwise: c[i] = scale * sum_j d(i,j)^2
+// w_j with d the Manhattan^k or squared Euclidean grid distance (one block
+// per i).
 template <typename Real>
-__global__ void dist2_const_2d(const double* __restrict__ w, int side, int sq, int k, double scale,
-                               Real* __restrict__ out) {
-  const int n = side * side;
+__global__ void dist2_const_grid(const double* __restrict__ w, int side, int dims, int sq, int k, double scale,
+                                 Real* __restrict__ out) {
+  const int n = dims == 3 ? side * side * side : side * side;
   const int i = blockIdx.x;
-  const int a = i / side, b = i % side;
   double acc = 0.0;
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    const double da = (double)abs(a - j / side), db = (double)abs(b - j % side);
-    double d = 1.0;
-    if (sq) {
-      d = da * da + db * db;
-    } else {
-      for (int e = 0; e < k; ++e) d *= da + db;
-    }
+    double dd[3];
+    grid_deltas(i, j, side, dims, dd);
+    const double d = grid_metric(dd, k, sq);
     acc += d * d * w[j];
   }
   __shared__ double sm[32];
@@ -170,7 +184,7 @@ __global__ void col_sums(const Real* __restrict__ T, int n, int m, double* __res
 }
 
 struct DenseCache {
-  int n = 0, k = 0, prec = -1, side = 0, sq = 0, pitch = 0;
+  int n = 0, k = 0, prec = -1, side = 0, dims = 0, sq = 0, pitch = 0;
   double h = 0;
   void* D = nullptr;
 };
@@ -188,8 +202,10 @@ struct DenseState {
   DenseCache X, Y;
 };
 
-static int ensure_dist(DenseCache& c, int n, double h, int k, int side, int sq, int prec, cudaStream_t st) {
-  if (c.D && c.n == n && c.h == h && c.k == k && c.side == side && c.sq == sq && c.prec == prec) return GW_OK;
+static int ensure_dist(DenseCache& c, int n, double h, int k, int side, int dims, int sq, int prec,
+                       cudaStream_t st) {
+  if (c.D && c.n == n && c.h == h && c.k == k && c.side == side && c.dims == dims && c.sq == sq && c.prec == prec)
+    return GW_OK;
   if (c.D) {
     cudaStreamSynchronize(st);
     cudaFree(c.D);
@@ -207,16 +223,17 @@ static int ensure_dist(DenseCache& c, int n, double h, int k, int side, int sq, 
   if (pitch != n) cudaMemsetAsync(c.D, 0, (size_t)pitch * pitch * esz, st);
   const int tf = prec == GW_DENSE_TC_TF32;
   if (bf)
-    build_dist<__nv_bfloat16><<<1024, 256, 0, st>>>((__nv_bfloat16*)c.D, n, hk, k, side, sq, pitch, 0);
+    build_dist<__nv_bfloat16><<<1024, 256, 0, st>>>((__nv_bfloat16*)c.D, n, hk, k, side, dims, sq, pitch, 0);
   else if (prec == GW_DENSE_FP64)
-    build_dist<double><<<1024, 256, 0, st>>>((double*)c.D, n, hk, k, side, sq, pitch, 0);
+    build_dist<double><<<1024, 256, 0, st>>>((double*)c.D, n, hk, k, side, dims, sq, pitch, 0);
   else
-    build_dist<float><<<1024, 256, 0, st>>>((float*)c.D, n, hk, k, side, sq, pitch, tf);
+    build_dist<float><<<1024, 256, 0, st>>>((float*)c.D, n, hk, k, side, dims, sq, pitch, tf);
   c.pitch = pitch;
   c.n = n;
   c.h = h;
   c.k = k;
   c.side = side;
+  c.dims = dims;
   c.sq = sq;
   c.prec = prec;
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
@@ -255,11 +272,12 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
   }
   cublasSetStream(S->handle, st);
   const int n = a.n, m = a.m;
-  const int sq = a.dim == 2 && a.cost == GW_COST_SQEUCLID;
-  int rc = ensure_dist(S->X, n, a.hx, a.k, a.dim == 2 ? a.sx : 0, sq, a.prec, st);
+  const bool grid = a.dim >= 2;
+  const int sq = grid && a.cost == GW_COST_SQEUCLID;
+  int rc = ensure_dist(S->X, n, a.hx, a.k, grid ? a.sx : 0, a.dim, sq, a.prec, st);
   if (rc != GW_OK) return rc;
   const int ky = a.ky > 0 ? a.ky : a.k;
-  rc = ensure_dist(S->Y, m, a.hy, ky, a.dim == 2 ? a.sy : 0, sq, a.prec, st);
+  rc = ensure_dist(S->Y, m, a.hy, ky, grid ? a.sy : 0, a.dim, sq, a.prec, st);
   if (rc != GW_OK) return rc;
   char* ws = (char*)wsv;
   size_t off = 0;
@@ -306,15 +324,15 @@ int dense_grad_launch(void* state, const DenseArgs& a, void* wsv, size_t ws_byte
     wx = r;
     wy = cc;
   }
-  if (a.dim == 2) {
+  if (grid) {
     TraceScope ts(a.tracer, "dense_const", st);
     const double fx = sq ? a.hx * a.hx : std::pow(a.hx, a.k), fy = sq ? a.hy * a.hy : std::pow(a.hy, a.k);
     if (dbl) {
-      dist2_const_2d<double><<<n, 256, 0, st>>>(wx, a.sx, sq, a.k, fx * fx, (double*)cx);
-      dist2_const_2d<double><<<m, 256, 0, st>>>(wy, a.sy, sq, a.k, fy * fy, (double*)cy);
+      dist2_const_grid<double><<<n, 256, 0, st>>>(wx, a.sx, a.dim, sq, a.k, fx * fx, (double*)cx);
+      dist2_const_grid<double><<<m, 256, 0, st>>>(wy, a.sy, a.dim, sq, a.k, fy * fy, (double*)cy);
     } else {
-      dist2_const_2d<float><<<n, 256, 0, st>>>(wx, a.sx, sq, a.k, fx * fx, (float*)cx);
-      dist2_const_2d<float><<<m, 256, 0, st>>>(wy, a.sy, sq, a.k, fy * fy, (float*)cy);
+      dist2_const_grid<float><<<n, 256, 0, st>>>(wx, a.sx, a.dim, sq, a.k, fx * fx, (float*)cx);
+      dist2_const_grid<float><<<m, 256, 0, st>>>(wy, a.sy, a.dim, sq, a.k, fy * fy, (float*)cy);
     }
   } else {
     if (ky == a.k) {

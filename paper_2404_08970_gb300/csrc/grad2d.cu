@@ -36,31 +36,7 @@
 namespace gw {
 namespace {
 
-template <typename Real>
-using AccOf = typename AccT<Real>::type;
-
-__device__ __forceinline__ ff acc_add_d(ff a, double x) { return ff_add(a, ff_from_double(x)); }
-__device__ __forceinline__ double acc_add_d(double a, double x) { return a + x; }
-__device__ __forceinline__ ff acc_mul(ff a, ff b) { return ff_mul(a, b); }
-__device__ __forceinline__ double acc_mul(double a, double b) { return a * b; }
-__device__ __forceinline__ void acc_from(ff* o, double x) { *o = ff_from_double(x); }
-__device__ __forceinline__ void acc_from(double* o, double x) { *o = x; }
-__device__ __forceinline__ void acc_split(ff a, float& hi, float& lo) {
-  hi = a.hi;
-  lo = a.lo;
-}
-__device__ __forceinline__ void acc_split(double a, double& hi, double& lo) {
-  hi = a;
-  lo = 0.0;
-}
-
-// Axis weight A(delta): |delta| or delta^2 (exact in float for |delta| < 4096).
-__device__ __forceinline__ float axis_w(int delta, int sq) {
-  const float a = (float)(delta < 0 ? -delta : delta);
-  return sq ? a * a : a;
-}
-__device__ __forceinline__ ff acc_w(ff x, float w) { return ff_mul(x, w); }
-__device__ __forceinline__ double acc_w(double x, float w) { return x * (double)w; }
+#include "grid_sep.cuh"
 
 // ---------------------------------------------------------------------------
 // g2_rows: per row i of T (length m = sy^2, element (c,d) at c*sy + d)
@@ -132,31 +108,6 @@ __global__ void __launch_bounds__(256, 1)
   }
 }
 
-// Column sums of T over row bands (exact marginals only), then over bands.
-template <typename Real>
-__global__ void g2_colsum(const Real* __restrict__ T, int n, int m, int rows_per, AccOf<Real>* __restrict__ part) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= m) return;
-  const int i0 = blockIdx.y * rows_per, i1 = min(n, i0 + rows_per);
-  Real s = 0, cmp = 0;
-  for (int i = i0; i < i1; ++i) {
-    const Real y = T[(size_t)i * m + p] - cmp;
-    const Real s2 = s + y;
-    cmp = (s2 - s) - y;
-    s = s2;
-  }
-  part[(size_t)blockIdx.y * m + p] = acc_of(s, -cmp);
-}
-
-template <typename Acc>
-__global__ void g2_colsum_fin(const Acc* __restrict__ part, int nb, int m, Acc* __restrict__ out) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= m) return;
-  Acc s = acc_zero((Acc*)nullptr);
-  for (int b = 0; b < nb; ++b) s = acc_add(s, part[(size_t)b * m + p]);
-  out[p] = s;
-}
-
 // M1[a][c] = sum_b Rc[(a,b)][c], M2[a][d] = sum_b Rd[(a,b)][d],
 // M3[b][c] = sum_a Rc[(a,b)][c], M4[b][d] = sum_a Rd[(a,b)][d] (layout
 // [4][sx][sy]); R[a][b] = r_(a,b) and C[c][d] = c_(c,d), from the targets or,
@@ -210,11 +161,6 @@ __global__ void g2_marg(const Acc* __restrict__ Rc, const Acc* __restrict__ Rd, 
 
 // rA = R 1, rB = 1^T R, cA = C 1, cB = 1^T C: one warp per output, lanes
 // over the summed index, then a fixed-order butterfly.
-__device__ __forceinline__ ff acc_shfl_xor(ff a, int o) {
-  return {__shfl_xor_sync(0xffffffffu, a.hi, o), __shfl_xor_sync(0xffffffffu, a.lo, o)};
-}
-__device__ __forceinline__ double acc_shfl_xor(double a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
-
 template <typename Acc>
 __global__ void g2_vec(const Acc* __restrict__ R, const Acc* __restrict__ C, int sx, int sy, Acc* __restrict__ rA,
                        Acc* __restrict__ rB, Acc* __restrict__ cA, Acc* __restrict__ cB) {
@@ -241,64 +187,6 @@ __global__ void g2_vec(const Acc* __restrict__ R, const Acc* __restrict__ C, int
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) t = acc_add(t, acc_shfl_xor(t, o));
   if (lane == 0) dst[j] = t;
-}
-
-// Small transforms by the axis matrix A (entries A(i - l)^pw):
-//   left:  out[b][i][j] = sum_l A(i - l)^pw in[b][l][j]
-//   right: out[b][i][j] = sum_l in[b][i][l] A(l - j)^pw
-struct TxJob {
-  const void* in;
-  void* out;
-  int batch, rows, cols;
-  int right, sq, pw;
-  int start;  // first thread of this job
-};
-constexpr int kMaxTxJobs = 8;
-struct TxJobs {
-  TxJob j[kMaxTxJobs];
-  int n, total;
-};
-
-template <typename Acc>
-__global__ void g2_tx(const __grid_constant__ TxJobs jobs) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= jobs.total) return;
-  int q = 0;
-  while (q + 1 < jobs.n && t >= jobs.j[q + 1].start) ++q;
-  const TxJob J = jobs.j[q];
-  const int e = t - J.start;
-  const int per = J.rows * J.cols;
-  const int b = e / per, i = (e % per) / J.cols, j = e % J.cols;
-  const Acc* in = (const Acc*)J.in + (size_t)b * per;
-  const int len = J.right ? J.cols : J.rows;
-  // Element l of the contracted line and the weight's offset from it.
-  const Acc* x0 = J.right ? in + (size_t)i * J.cols : in + j;
-  const int stride = J.right ? 1 : J.cols;
-  const int ref = J.right ? j : i;
-  constexpr int U = 8;
-  Acc s[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) s[q] = acc_zero((Acc*)nullptr);
-  int l = 0;
-  for (; l + U <= len; l += U) {
-    Acc x[U];
-#pragma unroll
-    for (int q = 0; q < U; ++q) x[q] = x0[(size_t)(l + q) * stride];
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const float w = axis_w(l + q - ref, J.sq);
-      Acc y = acc_w(x[q], w);
-      if (J.pw == 2) y = acc_w(y, w);
-      s[q & 3] = acc_add(s[q & 3], y);
-    }
-  }
-  for (; l < len; ++l) {
-    const float w = axis_w(l - ref, J.sq);
-    Acc y = acc_w(x0[(size_t)l * stride], w);
-    if (J.pw == 2) y = acc_w(y, w);
-    s[0] = acc_add(s[0], y);
-  }
-  ((Acc*)J.out)[e] = acc_add(acc_add(s[0], s[1]), acc_add(s[2], s[3]));
 }
 
 // Epilogue tables, all hi/lo (rounded once from the compensated values):
@@ -455,17 +343,6 @@ G2Layout g2_layout(int sx, int sy, int dtype) {
   return L;
 }
 
-// Blocks of `threads` threads that one SM holds at once for kernel f.
-template <typename F>
-int resident_blocks(F f, int threads) {
-  int b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, threads, 0) != cudaSuccess || b < 1) {
-    cudaGetLastError();
-    b = 1;
-  }
-  return b;
-}
-
 template <typename Real, int NQ>
 int grad2d_typed(const Grad2DArgs& A, void* wsv, size_t ws_bytes) {
   using Acc = AccOf<Real>;
@@ -572,6 +449,7 @@ size_t grad2d_workspace_bytes(int sx, int sy, int dtype, int cost, int k) {
 }
 
 int grad2d_launch(const Grad2DArgs& a, void* ws, size_t ws_bytes) {
+  if (a.dim == 3) return grad3d_launch(a, ws, ws_bytes);
   if (a.cost == GW_COST_POW && a.k >= 2) return grad2d_powk_launch(a, ws, ws_bytes);
   if (a.sx < 1 || a.sy < 1 || a.sx > kMax2DSide || a.sy > kMax2DSide) return GW_ERR_INVALID;
   if (a.cost != GW_COST_POW && a.cost != GW_COST_SQEUCLID) return GW_ERR_INVALID;

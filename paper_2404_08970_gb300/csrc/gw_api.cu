@@ -213,7 +213,7 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 gw_status check_grid(gw_ctx* c, const gw_problem* p) {
   if (!p) return fail(c, GW_ERR_INVALID, "problem descriptor is NULL");
-  if (p->dim != 1 && p->dim != 2) return fail(c, GW_ERR_INVALID, "dim must be 1 or 2 (got %d)", p->dim);
+  if (p->dim < 1 || p->dim > 3) return fail(c, GW_ERR_INVALID, "dim must be 1, 2 or 3 (got %d)", p->dim);
   if (p->nx < 1 || p->ny < 1) return fail(c, GW_ERR_INVALID, "grid sizes must be >= 1 (got %d, %d)", p->nx, p->ny);
   if (!finite_pos(p->hx) || !finite_pos(p->hy)) return fail(c, GW_ERR_INVALID, "grid spacings must be finite and > 0");
   if (p->k < 1) return fail(c, GW_ERR_INVALID, "distance exponent k must be >= 1 (got %d)", p->k);
@@ -225,6 +225,14 @@ gw_status check_grid(gw_ctx* c, const gw_problem* p) {
       return fail(c, GW_ERR_INVALID,
                   "mixed exponents (k, ky) = (%d, %d): supported are (1, 2) and (2, 1) with ny <= 8192 "
                   "(4096 in double)", p->k, p->ky);
+  } else if (p->dim == 3) {
+    if (p->ky != 0 && p->ky != p->k)
+      return fail(c, GW_ERR_INVALID, "3D grids take one distance exponent (ky = 0 or k)");
+    if (!(p->cost == GW_COST_SQEUCLID || (p->cost == GW_COST_POW && p->k == 1)))
+      return fail(c, GW_ERR_INVALID, "3D grids take the Manhattan distance with k = 1 or the squared Euclidean "
+                                     "distance (got cost %d, k = %d)", p->cost, p->k);
+    if (p->nx > gw::kMax3DSide || p->ny > gw::kMax3DSide)
+      return fail(c, GW_ERR_INVALID, "3D grid sides must be <= %d (got %d, %d)", gw::kMax3DSide, p->nx, p->ny);
   } else {
     if (p->ky != 0 && p->ky != p->k)
       return fail(c, GW_ERR_INVALID, "2D grids take one distance exponent (ky = 0 or k)");
@@ -240,9 +248,14 @@ gw_status check_grid(gw_ctx* c, const gw_problem* p) {
   return GW_OK;
 }
 
-// Points of each space: nx, ny in 1D, nx^2, ny^2 on 2D grids.
-size_t points_x(const gw_problem* p) { return p->dim == 2 ? (size_t)p->nx * p->nx : (size_t)p->nx; }
-size_t points_y(const gw_problem* p) { return p->dim == 2 ? (size_t)p->ny * p->ny : (size_t)p->ny; }
+// Points of each space: nx, ny in 1D, nx^dim, ny^dim on 2D and 3D grids.
+size_t grid_points(int side, int dim) {
+  size_t q = 1;
+  for (int d = 0; d < dim; ++d) q *= (size_t)side;
+  return q;
+}
+size_t points_x(const gw_problem* p) { return grid_points(p->nx, p->dim); }
+size_t points_y(const gw_problem* p) { return grid_points(p->ny, p->dim); }
 
 }  // namespace
 
@@ -387,8 +400,9 @@ gw_status grad_device(gw_ctx* c, const gw_problem* p, const double* d_u, const d
   gw_status s;
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
 
-  if (p->dim == 2) {
+  if (p->dim >= 2) {
     gw::Grad2DArgs a{};
+    a.dim = p->dim;
     a.sx = p->nx;
     a.sy = p->ny;
     a.cost = p->cost;
@@ -406,11 +420,11 @@ gw_status grad_device(gw_ctx* c, const gw_problem* p, const double* d_u, const d
     a.status = c->status;
     a.num_sms = c->num_sms;
     a.tracer = c->tr();
-    s = ensure_ws(c, gw::grad2d_workspace_bytes(a.sx, a.sy, a.dtype, a.cost, a.k));
+    s = ensure_ws(c, gw::grid_grad_workspace_bytes(a.dim, a.sx, a.sy, a.dtype, a.cost, a.k));
     if (s != GW_OK) return s;
     char key[384];
-    snprintf(key, sizeof key, "grad2 %d %d %d %d %.17g %.17g %d %p %p %p %p %d %p %zu", a.sx, a.sy, a.cost, a.k, a.hx,
-             a.hy, a.dtype, a.T, a.G, (void*)a.u, (void*)a.v, a.exact, c->ws, c->ws_bytes);
+    snprintf(key, sizeof key, "grad%d %d %d %d %d %.17g %.17g %d %p %p %p %p %d %p %zu", a.dim, a.sx, a.sy, a.cost, a.k,
+             a.hx, a.hy, a.dtype, a.T, a.G, (void*)a.u, (void*)a.v, a.exact, c->ws, c->ws_bytes);
     return run_graph(
         c, key, a.stream,
         [&](cudaStream_t st) {
@@ -418,7 +432,7 @@ gw_status grad_device(gw_ctx* c, const gw_problem* p, const double* d_u, const d
           ac.stream = st;
           return gw::grad2d_launch(ac, c->ws, c->ws_bytes);
         },
-        "gw_grad (2D)");
+        a.dim == 3 ? "gw_grad (3D)" : "gw_grad (2D)");
   }
 
   gw::Grad1DArgs a{};

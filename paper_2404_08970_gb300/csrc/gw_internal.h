@@ -131,8 +131,12 @@ inline bool mixed_k_supported(int k, int ky, int m, int dtype) {
 }
 // Longest row a double-precision Sinkhorn pass holds in shared memory.
 constexpr int kMaxSolveF64Y = 10240;
+// Structured gradient on side^3 grids with an axis-separable cost
+// (grad3d.cu): Manhattan with k = 1, or squared Euclidean.
+constexpr int kMax3DSide = 32;
 struct Grad2DArgs {
-  int sx, sy;           // grid sides; n = sx^2 points of X, m = sy^2 points of Y
+  int sx, sy;           // grid sides; n = sx^dim points of X, m = sy^dim points of Y
+  int dim;              // 2 (side x side grids) or 3 (side^3 grids); 0 reads as 2
   int cost;             // GW_COST_POW (Manhattan^k) or GW_COST_SQEUCLID
   int k;                // exponent of the Manhattan distance (GW_COST_POW)
   double hx, hy;
@@ -152,6 +156,12 @@ struct Grad2DArgs {
 // costs, or Manhattan^k with k >= 2).
 size_t grad2d_workspace_bytes(int sx, int sy, int dtype, int cost, int k);
 int grad2d_launch(const Grad2DArgs& a, void* ws, size_t ws_bytes);
+size_t grad3d_workspace_bytes(int sx, int sy, int dtype);
+int grad3d_launch(const Grad2DArgs& a, void* ws, size_t ws_bytes);
+// Workspace of the grid gradient of a problem with dim 2 or 3.
+inline size_t grid_grad_workspace_bytes(int dim, int sx, int sy, int dtype, int cost, int k) {
+  return dim == 3 ? grad3d_workspace_bytes(sx, sy, dtype) : grad2d_workspace_bytes(sx, sy, dtype, cost, k);
+}
 // Manhattan^k, k = 2, 3 (grad2d_powk.cu): supported grid sides and dtype.
 bool grad2d_powk_supported(int sx, int sy, int k, int dtype);
 size_t grad2d_powk_workspace_bytes(int sx, int sy, int k, int dtype);
@@ -159,7 +169,7 @@ int grad2d_powk_launch(const Grad2DArgs& a, void* ws, size_t ws_bytes);
 
 // Dense comparison gradient through cuBLAS (dense.cu).
 struct DenseArgs {
-  int dim, cost, sx, sy;  // dim 2: sx, sy grid sides, n = sx^2, m = sy^2
+  int dim, cost, sx, sy;  // dim 2, 3: sx, sy grid sides, n = sx^dim, m = sy^dim
   int n, m, k, prec, exact;
   int ky;                 // 1D: exponent of Y's distance (0: same as k)
   double hx, hy;
@@ -187,7 +197,7 @@ size_t dense_workspace_bytes(int n, int m, int prec);
 int dense_grad_launch(void* state, const DenseArgs& a, void* ws, size_t ws_bytes);
 
 // Entropic (fused) GW by mirror descent (sinkhorn.cu).  dim 1: n = nx and
-// m = ny points; dim 2: nx, ny are grid sides (n = nx^2, m = ny^2).
+// m = ny points; dim 2, 3: nx, ny are grid sides (n = nx^dim, m = ny^dim).
 struct SolveArgs {
   int dim, cost;
   int nx, ny;

@@ -51,8 +51,13 @@ struct Request {
   double stats[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
-size_t points_x(const gw_problem& p) { return p.dim == 2 ? (size_t)p.nx * p.nx : (size_t)p.nx; }
-size_t points_y(const gw_problem& p) { return p.dim == 2 ? (size_t)p.ny * p.ny : (size_t)p.ny; }
+size_t grid_points(int side, int dim) {
+  size_t q = 1;
+  for (int d = 0; d < dim; ++d) q *= (size_t)side;
+  return q;
+}
+size_t points_x(const gw_problem& p) { return grid_points(p.nx, p.dim); }
+size_t points_y(const gw_problem& p) { return grid_points(p.ny, p.dim); }
 
 }  // namespace
 
@@ -320,7 +325,7 @@ gw_status gw_submit(gw_server* s, const gw_problem* p, const double* h_u, const 
                     const double* h_psi, void* h_T, uint64_t* ticket) {
   if (!s || !p || !h_u || !h_v || !ticket) return GW_ERR_INVALID;
   const gw_problem& q = *p;
-  if ((q.dim != 1 && q.dim != 2) || q.nx < 1 || q.ny < 1 || !(q.hx > 0) || !(q.hy > 0) || q.k < 1 ||
+  if (q.dim < 1 || q.dim > 3 || q.nx < 1 || q.ny < 1 || !(q.hx > 0) || !(q.hy > 0) || q.k < 1 ||
       (q.dtype != GW_F32 && q.dtype != GW_F64) || !(q.eps > 0) || !(q.tau == 0.0 || q.tau > 0) ||
       (q.warm_start != 0 && q.warm_start != 1) || !(q.rho == 0.0 || q.rho > 0) ||
       (q.rho > 0 && (q.theta != 1.0 || (q.tau != 0.0 && q.tau != q.eps))) || q.n_outer < 0 || q.n_inner < 1 ||
@@ -328,7 +333,10 @@ gw_status gw_submit(gw_server* s, const gw_problem* p, const double* h_u, const 
     return GW_ERR_INVALID;
   if (q.dim == 1 && (q.k > 3 || q.ny > 16384 || !gw::mixed_k_supported(q.k, q.ky, q.ny, q.dtype)))
     return GW_ERR_INVALID;
-  if (q.dim == 2 && q.ky != 0 && q.ky != q.k) return GW_ERR_INVALID;
+  if (q.dim >= 2 && q.ky != 0 && q.ky != q.k) return GW_ERR_INVALID;
+  if (q.dim == 3 && (!(q.cost == GW_COST_SQEUCLID || (q.cost == GW_COST_POW && q.k == 1)) ||
+                     q.nx > gw::kMax3DSide || q.ny > gw::kMax3DSide))
+    return GW_ERR_INVALID;
   if (q.dim == 2 && ((q.cost != GW_COST_POW && q.cost != GW_COST_SQEUCLID) || q.nx > gw::kMax2DSide ||
                      q.ny > gw::kMax2DSide ||
                      (q.cost == GW_COST_POW && q.k > 1 && !gw::grad2d_powk_supported(q.nx, q.ny, q.k, q.dtype))))

@@ -1058,8 +1058,9 @@ int prepare(const SolveArgs& A, void* wsv, size_t ws_bytes, SolveState<Real>* S)
 template <typename Real>
 int gradient(const SolveState<Real>& S, int exact, double out_scale, cudaStream_t st) {
   const SolveArgs& A = *S.A;
-  if (A.dim == 2) {
+  if (A.dim >= 2) {
     Grad2DArgs g2{};
+    g2.dim = A.dim;
     g2.sx = A.nx;
     g2.sy = A.ny;
     g2.cost = A.cost;
@@ -1418,7 +1419,7 @@ size_t solve_workspace_bytes(const SolveArgs& A) {
   add((size_t)n * 8);
   add((size_t)n * 8);
   add(kUgwScal * 8);
-  const size_t g = A.dim == 2 ? grad2d_workspace_bytes(A.nx, A.ny, A.dtype, A.cost, A.k)
+  const size_t g = A.dim >= 2 ? grid_grad_workspace_bytes(A.dim, A.nx, A.ny, A.dtype, A.cost, A.k)
                               : grad1d_workspace_bytes(n, m, A.k, A.dtype, A.num_sms);
   return b + g + 4096;
 }

@@ -56,6 +56,15 @@ def abs_normal_image(side: int, rng: np.random.Generator) -> np.ndarray:
     return w / w.sum()
 
 
+def abs_normal_volume(side: int, rng: np.random.Generator) -> np.ndarray:
+    """Normalised |N(0,1)| voxel intensities of a side^3 volume, row-major."""
+    w = np.abs(rng.standard_normal(side ** 3))
+    while np.any(w == 0.0):
+        z = w == 0.0
+        w[z] = np.abs(rng.standard_normal(int(z.sum())))
+    return w / w.sum()
+
+
 def random_coupling(u: np.ndarray, v: np.ndarray, rng: np.random.Generator,
                     spread: float = 0.2) -> np.ndarray:
     """A random strictly positive n x m coupling whose marginals are u and v.
@@ -87,7 +96,7 @@ def features(count: int, dim: int, rng: np.random.Generator) -> np.ndarray:
 
 # --------------------------------------------------------------------------
 # Named workloads.  Grid spacing h = 1/n for 1D (points x_i = i/n) and
-# h = 1/(side-1) for 2D (the unit square).
+# h = 1/(side-1) for 2D and 3D (the unit square and cube).
 # --------------------------------------------------------------------------
 
 def workload_1d_small(seed: int = 0):
@@ -125,6 +134,19 @@ def workload_2d(side_x: int = 64, side_y: int = 96, cost: str = "sqeuclid",
     u = abs_normal_image(side_x, rng)
     v = abs_normal_image(side_y, rng)
     return dict(dim=2, nx=side_x, ny=side_y, hx=1.0 / (side_x - 1),
+                hy=1.0 / (side_y - 1), k=1, cost=cost, eps=5e-3,
+                n_outer=20, n_inner=100, u=u, v=v)
+
+
+def workload_3d(side_x: int = 16, side_y: int = 21, cost: str = "sqeuclid",
+                seed: int = 0):
+    """3D side_x^3 x side_y^3 workload on the unit cube with |N(0,1)| voxel
+    marginals, eps = 5e-3 (the 2D workload's recipe with a third axis; 16^3
+    vs 21^3 has about the point counts of the 64^2 vs 96^2 images)."""
+    rng = rng_for(seed)
+    u = abs_normal_volume(side_x, rng)
+    v = abs_normal_volume(side_y, rng)
+    return dict(dim=3, nx=side_x, ny=side_y, hx=1.0 / (side_x - 1),
                 hy=1.0 / (side_y - 1), k=1, cost=cost, eps=5e-3,
                 n_outer=20, n_inner=100, u=u, v=v)
 

@@ -40,3 +40,12 @@ def test_serve_workload_generator():
         assert abs(r["u"].sum() - 1) < 1e-12 and r["u"].size == n
         if r["kind"].endswith("fgw"):
             assert r["phi"].shape == (n, 16) and r["psi"].shape == (m, 16) and r["theta"] == 0.5
+
+
+def test_volume_workload_generator():
+    w = I.workload_3d(6, 7, "manhattan", seed=0)
+    assert w["dim"] == 3 and w["u"].shape == (216,) and w["v"].shape == (343,)
+    assert np.all(w["u"] > 0) and abs(w["u"].sum() - 1) < 1e-12 and abs(w["v"].sum() - 1) < 1e-12
+    assert w["hx"] == 1.0 / 5 and w["hy"] == 1.0 / 6
+    again = I.workload_3d(6, 7, "manhattan", seed=0)
+    assert np.array_equal(w["u"], again["u"])
