@@ -97,6 +97,7 @@ struct gw_ctx {
   std::vector<cudaStream_t> bstreams;
   cudaEvent_t fork_ev = nullptr;
   std::vector<cudaEvent_t> join_ev;
+  std::vector<cudaEvent_t> mix_ev;  // fork and join events of the mixed sets
   void* bws = nullptr;
   size_t bws_bytes = 0;
   cudaGraphExec_t batch_exec = nullptr;
@@ -300,6 +301,7 @@ void gw_ctx_destroy(gw_ctx* c) {
   if (c->batch_exec) cudaGraphExecDestroy(c->batch_exec);
   for (auto st : c->bstreams) cudaStreamDestroy(st);
   for (auto ev : c->join_ev) cudaEventDestroy(ev);
+  for (auto ev : c->mix_ev) cudaEventDestroy(ev);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->bws) cudaFree(c->bws);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -744,6 +746,43 @@ gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const do
     total += (gw::solve_workspace_bytes(args[i]) + 4095) / 4096 * 4096;
   }
   if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
+  // Mixed sets: problems of one dtype and schedule whose row configurations
+  // run 512-thread blocks advance in lock step with every Sinkhorn pass one
+  // launch over all of their row bands (each block runs its own problem's
+  // configuration).  The other problems form groups of one row
+  // configuration (one launch per pass per 32 problems).  Sets and groups
+  // run concurrently on worker streams.
+  std::map<std::tuple<int, int, int>, std::vector<int>> mixed;
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
+  for (int i = 0; i < count; ++i) {
+    if (gw::solve_mixable(args[i]))
+      mixed[std::make_tuple(args[i].dtype, args[i].n_outer, args[i].n_inner)].push_back(i);
+    else
+      groups[std::make_tuple(gw::solve_group_key(args[i]), args[i].dtype, args[i].n_outer, args[i].n_inner)]
+          .push_back(i);
+  }
+  std::vector<std::vector<int>> parts;
+  for (auto& g : groups) {
+    auto& v = g.second;
+    std::stable_sort(v.begin(), v.end(), [&](int x, int y) {
+      return (double)args[x].n * args[x].m > (double)args[y].n * args[y].m;
+    });
+    for (size_t b = 0; b < v.size(); b += 32) parts.emplace_back(v.begin() + b, v.begin() + std::min(v.size(), b + 32));
+  }
+  // Each mixed set: a device table after the problems' workspaces, a main
+  // stream and up to kMixWorkers worker streams.
+  constexpr int kMixWorkers = 8;
+  std::vector<std::vector<int>> sets;
+  std::vector<size_t> table_off;
+  for (auto& kv : mixed) {
+    auto& v = kv.second;
+    std::stable_sort(v.begin(), v.end(), [&](int x, int y) {
+      return (double)args[x].n * args[x].m > (double)args[y].n * args[y].m;
+    });
+    sets.push_back(v);
+    table_off.push_back(total);
+    total += (gw::solve_mixed_table_bytes((int)v.size(), args[v[0]].dtype) + 4095) / 4096 * 4096;
+  }
   if (total > c->bws_bytes) {
     if (c->bws) {
       cudaDeviceSynchronize();
@@ -758,23 +797,12 @@ gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const do
     }
     c->bws_bytes = total;
   }
-  // Groups: problems with the same row configuration, dtype and schedule run
-  // in lock step (one launch per Sinkhorn pass for the whole group).  Groups
-  // run concurrently, each on a worker stream; a group larger than 32
-  // problems is split so that its parts also run concurrently.
-  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;
-  for (int i = 0; i < count; ++i)
-    groups[std::make_tuple(gw::solve_group_key(args[i]), args[i].dtype, args[i].n_outer, args[i].n_inner)]
-        .push_back(i);
-  std::vector<std::vector<int>> parts;
-  for (auto& g : groups) {
-    auto& v = g.second;
-    std::stable_sort(v.begin(), v.end(), [&](int x, int y) {
-      return (double)args[x].n * args[x].m > (double)args[y].n * args[y].m;
-    });
-    for (size_t b = 0; b < v.size(); b += 32) parts.emplace_back(v.begin() + b, v.begin() + std::min(v.size(), b + 32));
+  std::vector<int> set_workers(sets.size());
+  int S = (int)std::min<size_t>(parts.size(), 32);
+  for (size_t j = 0; j < sets.size(); ++j) {
+    set_workers[j] = std::min<int>(kMixWorkers, (int)sets[j].size());
+    S += 1 + set_workers[j];
   }
-  const int S = std::min<int>((int)parts.size(), 32);
   while ((int)c->bstreams.size() < S) {
     cudaStream_t st;
     cudaEvent_t ev;
@@ -784,12 +812,56 @@ gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const do
     c->bstreams.push_back(st);
     c->join_ev.push_back(ev);
   }
+  while (c->mix_ev.size() < sets.size() * (1 + kMixWorkers)) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_fail(c, cudaGetLastError(), "gw_solve_batch: mixed-set events");
+    c->mix_ev.push_back(ev);
+  }
   if (!c->fork_ev && cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess)
     return cuda_fail(c, cudaGetLastError(), "gw_solve_batch: fork event");
+  // Arguments, workspaces and device tables of the mixed sets.
+  std::vector<std::vector<const gw::SolveArgs*>> set_args(sets.size());
+  std::vector<std::vector<void*>> set_ws(sets.size());
+  std::vector<std::vector<size_t>> set_wb(sets.size());
+  for (size_t j = 0; j < sets.size(); ++j)
+    for (int i : sets[j]) {
+      set_args[j].push_back(&args[i]);
+      set_ws[j].push_back((char*)c->bws + off[i]);
+      set_wb[j].push_back(gw::solve_workspace_bytes(args[i]));
+    }
+  // The tables are written before the solves are enqueued (or captured); a
+  // previous batch on this context may still read them, so the device is
+  // synchronised first.
+  auto write_tables = [&]() -> int {
+    if (sets.empty()) return GW_OK;
+    if (cudaDeviceSynchronize() != cudaSuccess) return GW_ERR_CUDA;
+    for (size_t j = 0; j < sets.size(); ++j) {
+      const int cnt = (int)sets[j].size();
+      std::vector<char> host(gw::solve_mixed_table_bytes(cnt, args[sets[j][0]].dtype));
+      int rc = gw::solve_mixed_table(set_args[j].data(), set_ws[j].data(), set_wb[j].data(), cnt, host.data());
+      if (rc != GW_OK) return rc;
+      if (cudaMemcpy((char*)c->bws + table_off[j], host.data(), host.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return GW_ERR_CUDA;
+    }
+    return GW_OK;
+  };
   auto enqueue = [&](cudaStream_t origin) -> int {
     if (cudaEventRecord(c->fork_ev, origin) != cudaSuccess) return GW_ERR_CUDA;
     for (int k = 0; k < S; ++k)
       if (cudaStreamWaitEvent(c->bstreams[k], c->fork_ev, 0) != cudaSuccess) return GW_ERR_CUDA;
+    int next = 0;
+    for (size_t j = 0; j < sets.size(); ++j) {
+      const int nw = set_workers[j];
+      cudaStream_t main = c->bstreams[next];
+      const cudaStream_t* workers = c->bstreams.data() + next + 1;
+      next += 1 + nw;
+      const cudaEvent_t* ev = c->mix_ev.data() + j * (1 + kMixWorkers);
+      int rc = gw::solve_mixed_launch(set_args[j].data(), set_ws[j].data(), set_wb[j].data(), (int)sets[j].size(),
+                                      (char*)c->bws + table_off[j], main, workers, nw, ev[0], ev + 1);
+      if (rc != GW_OK) return rc;
+    }
+    const int np = S - next;
     for (size_t g = 0; g < parts.size(); ++g) {
       std::vector<gw::SolveArgs> ga;
       std::vector<const gw::SolveArgs*> gp;
@@ -801,7 +873,8 @@ gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const do
         gb.push_back(gw::solve_workspace_bytes(args[i]));
       }
       for (auto& a : ga) gp.push_back(&a);
-      int rc = gw::solve_group_launch(gp.data(), gws.data(), gb.data(), (int)gp.size(), c->bstreams[g % S]);
+      int rc = gw::solve_group_launch(gp.data(), gws.data(), gb.data(), (int)gp.size(),
+                                      c->bstreams[next + (int)(g % np)]);
       if (rc != GW_OK) return rc;
     }
     for (int k = 0; k < S; ++k) {
@@ -812,7 +885,8 @@ gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const do
   };
   int rc;
   if (c->tracer) {
-    rc = enqueue((cudaStream_t)stream);
+    rc = write_tables();
+    if (rc == GW_OK) rc = enqueue((cudaStream_t)stream);
   } else {
     std::string key;
     char buf[512];
@@ -833,6 +907,8 @@ gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const do
       }
       if (!c->cap && cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess)
         return cuda_fail(c, cudaGetLastError(), "capture stream");
+      rc = write_tables();
+      if (rc != GW_OK) return fail(c, (gw_status)rc, "gw_solve_batch: problem tables: %s", gw::last_failure());
       cudaGraph_t graph = nullptr;
       cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");

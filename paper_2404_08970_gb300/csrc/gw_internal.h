@@ -228,6 +228,19 @@ int solve_group_key(const SolveArgs& a);
 int solve_group_launch(const SolveArgs* const* a, void* const* ws, const size_t* ws_bytes, int count,
                        cudaStream_t stream);
 
+// Mixed batches (sinkhorn.cu): problems of one dtype and schedule whose row
+// configurations all run 512-thread blocks share every Sinkhorn launch.  The
+// host image of the problems' device table (solve_mixed_table_bytes bytes)
+// is written by solve_mixed_table and must be on the device before
+// solve_mixed_launch enqueues the solves: per-problem work on the worker
+// streams, the shared Sinkhorn passes on `main` (fork/join by the events).
+bool solve_mixable(const SolveArgs& A);
+size_t solve_mixed_table_bytes(int count, int dtype);
+int solve_mixed_table(const SolveArgs* const* A, void* const* ws, const size_t* ws_bytes, int count, void* host);
+int solve_mixed_launch(const SolveArgs* const* A, void* const* ws, const size_t* ws_bytes, int count,
+                       const void* dev_table, cudaStream_t main, const cudaStream_t* workers, int nworkers,
+                       cudaEvent_t fork, const cudaEvent_t* join);
+
 // Sinkhorn row configurations (sinkhorn.cu): the built-in choice for m
 // columns, the shape of a configuration id, and every id (count returned, at
 // most cap written).

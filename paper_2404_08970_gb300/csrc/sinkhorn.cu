@@ -25,6 +25,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <type_traits>
 #include <vector>
 
 #include "gw_common.cuh"
@@ -132,11 +134,12 @@ __host__ __device__ __forceinline__ int col_of(int t, int v, int NT) {
   return PER * ((v / PER) * NT + t) + v % PER;
 }
 
-// x[v] = row[col_of(t, v)]: 16-byte loads when the row's start is 16-byte
-// aligned, else scalar loads.  A 16-byte group that starts at or past column
-// m is not read (zeros); the group straddling m reads up to PER - 1 values
-// past the row, inside the slot's slack (finite, see sk_pass).  `row` is
-// derived from the shared array.
+// x[v] = row[col_of(t, v)] by 16-byte loads (two per group when the row's
+// start is not 16-byte aligned).  A 16-byte group that starts at or past
+// column m is not read (zeros); the group straddling m reads up to PER - 1
+// values past the row, and the unaligned form up to one group more, inside
+// the slot's slack (finite, see sk_pass).  `row` is derived from the shared
+// array.
 template <int VPT, int NT, typename Real>
 __device__ __forceinline__ void load_vals(const Real* row, int tid, int m, Real (&x)[VPT]) {
   constexpr int PER = 16 / sizeof(Real);
@@ -151,10 +154,37 @@ __device__ __forceinline__ void load_vals(const Real* row, int tid, int m, Real 
       for (int w = 0; w < PER; ++w) x[j * PER + w] = e[w];
     }
   } else {
+    // The row starts `off` elements into a 16-byte group of the slot: each
+    // 16-byte group of the row spans two aligned slot groups, read whole
+    // (consecutive lanes read consecutive groups, so no bank conflicts) and
+    // recombined with the row-uniform shift.
+    const uint32_t mis = smem_u32(row) & 15u;
+    const float4* base = reinterpret_cast<const float4*>(reinterpret_cast<const char*>(row) - mis);
+    const int off = (int)(mis / sizeof(Real));
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) {
-      const int p = col_of<Real>(tid, v, NT);
-      x[v] = p < m + PER ? row[p] : (Real)0;
+    for (int j = 0; j < VPT / PER; ++j) {
+      const int q = j * NT + tid;
+      Real* o = x + j * PER;
+      if (PER * q < m) {
+        const float4 a4 = base[q], b4 = base[q + 1];
+        const Real* A = reinterpret_cast<const Real*>(&a4);
+        const Real* B = reinterpret_cast<const Real*>(&b4);
+        if constexpr (PER == 4) {
+          if (off == 1) {
+            o[0] = A[1]; o[1] = A[2]; o[2] = A[3]; o[3] = B[0];
+          } else if (off == 2) {
+            o[0] = A[2]; o[1] = A[3]; o[2] = B[0]; o[3] = B[1];
+          } else {
+            o[0] = A[3]; o[1] = B[0]; o[2] = B[1]; o[3] = B[2];
+          }
+        } else {
+          o[0] = A[1];
+          o[1] = B[0];
+        }
+      } else {
+#pragma unroll
+        for (int w = 0; w < PER; ++w) o[w] = (Real)0;
+      }
     }
   }
 }
@@ -282,14 +312,14 @@ __device__ __forceinline__ Real row_redo(const Real* row, int gt, int g, int m, 
 // added in shared memory.  A row sum out of range is redone from the ring
 // with a max shift (group-uniform branch).
 // ---------------------------------------------------------------------------
-template <int NW, int VPT, int NG, typename Real, int MAXP>
-__global__ void __launch_bounds__(32 * NW * NG, 1)
-    sk_pass(const __grid_constant__ SkBatch<Real, MAXP> P, unsigned* status) {
+// The pass over band `a` of problem `pr` by one block of 32 NW NG threads
+// (smem_dyn: the block's dynamic shared memory).
+template <int NW, int VPT, int NG, typename Real>
+__device__ __forceinline__ void pass_band(const SkProb<Real>& pr, int a, unsigned* status,
+                                          unsigned char* smem_dyn) {
   constexpr int GT = 32 * NW;  // threads of a row group
   constexpr int NT = GT * NG;
   constexpr int COVER = GT * VPT;
-  const int pi = batch_problem(P);
-  const SkProb<Real>& pr = P.p[pi];
   const int S = pr.geo.stages, slot_bytes = pr.geo.slot_bytes;
   const Real* __restrict__ Pi = pr.Pi;
   Real* __restrict__ F = pr.F;
@@ -297,7 +327,6 @@ __global__ void __launch_bounds__(32 * NW * NG, 1)
   const int n = pr.n, m = pr.m, R = pr.R;
   const Real c = pr.c;
 
-  extern __shared__ __align__(16) unsigned char smem_dyn[];
   unsigned char* sm = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
   unsigned char* ring = sm;
   const size_t ring_bytes = (size_t)NG * S * slot_bytes > (size_t)NG * COVER * sizeof(Real)
@@ -311,7 +340,7 @@ __global__ void __launch_bounds__(32 * NW * NG, 1)
   uint64_t* full = reinterpret_cast<uint64_t*>(braw + ((8u - (smem_u32(braw) & 7u)) & 7u));
 
   const int tid = threadIdx.x, g = tid / GT, gt = tid % GT, lane = tid & 31, wig = gt >> 5;
-  const int a = (int)blockIdx.x - P.block0[pi], s = a * R, Ra = min(R, n - s);
+  const int s = a * R, Ra = min(R, n - s);
   unsigned char* gring = ring + (size_t)g * S * slot_bytes;
   uint64_t* gfull = full + g * S;
   // Row k of group g is band row g + k NG, in slot k mod S.
@@ -326,14 +355,19 @@ __global__ void __launch_bounds__(32 * NW * NG, 1)
   };
   // Past the row's end a slot holds up to 24 bytes of what follows the row in
   // Pi (finite), or the zeros written here: finite values that the -inf of the
-  // padded columns' G turns into exact zeros, with no per-element masks.
-  const size_t row_bytes = (size_t)m * sizeof(Real);
-  for (int q = 0; q < NG * S; ++q)
-    for (size_t b = row_bytes + 4 * (size_t)tid; b + 4 <= (size_t)slot_bytes; b += 4 * (size_t)NT)
-      *reinterpret_cast<unsigned*>(ring + (size_t)q * slot_bytes + b) = 0u;
+  // padded columns' G turns into exact zeros, with no per-element masks.  A
+  // thread reads at most 2 * 16 bytes past the row's end (alignment offset
+  // plus the 16-byte group straddling column m), so 48 bytes per slot are
+  // cleared, by all threads at once, as are the slots' barriers initialised.
+  const int row_bytes = m * (int)sizeof(Real);
+  const int zw = min((slot_bytes - row_bytes) / 4, 12);
+  for (int e = tid; e < NG * S * zw; e += NT) {
+    const int q = e / zw;
+    *reinterpret_cast<unsigned*>(ring + (size_t)q * slot_bytes + row_bytes + 4 * (e - q * zw)) = 0u;
+  }
   fence_proxy_async_smem();
-  if (tid == 0) {
-    for (int i = 0; i < NG * S; ++i) mbar_init(&full[i], 1);
+  if (tid < NG * S) {
+    mbar_init(&full[tid], 1);
     fence_mbar_init();
   }
   for (int t = tid; t < Ra; t += NT) {
@@ -426,15 +460,21 @@ __global__ void __launch_bounds__(32 * NW * NG, 1)
   }
 }
 
+template <int NW, int VPT, int NG, typename Real, int MAXP>
+__global__ void __launch_bounds__(32 * NW * NG, 1)
+    sk_pass(const __grid_constant__ SkBatch<Real, MAXP> P, unsigned* status) {
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  const int pi = batch_problem(P);
+  pass_band<NW, VPT, NG, Real>(P.p[pi], (int)blockIdx.x - P.block0[pi], status, smem_dyn);
+}
+
 // Per column: S_p = sum_b part_bp (FP32 compensated sums over 8 band groups,
 // combined in FP64) and G_p += log2 v_p - log2 S_p.  A block covers 32
 // columns.  If any of them has S_p out of range, the block recomputes its 32
 // columns from Pi and the new F with a running max (8 warps over the rows,
 // one lane per column).
-template <typename Real, int MAXP>
-__global__ void __launch_bounds__(256) sk_cols(const __grid_constant__ SkBatch<Real, MAXP> P) {
-  const int pi = batch_problem(P);
-  const SkProb<Real>& pr = P.p[pi];
+template <typename Real>
+__device__ __forceinline__ void cols_block(const SkProb<Real>& pr, int cb) {
   const Real* __restrict__ part = pr.part;
   const Real* __restrict__ lv = pr.lv;
   Real* __restrict__ G = pr.G;
@@ -445,7 +485,7 @@ __global__ void __launch_bounds__(256) sk_cols(const __grid_constant__ SkBatch<R
   __shared__ double sS[8][32];
   __shared__ Real sM[8][32];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
-  const int p = ((int)blockIdx.x - P.block0[pi]) * 32 + lane;
+  const int p = cb * 32 + lane;
   const int per = (B + 7) / 8;
   const int b0 = min(B, grp * per), b1 = min(B, b0 + per);
   Real S = 0, C = 0;
@@ -517,6 +557,81 @@ __global__ void __launch_bounds__(256) sk_cols(const __grid_constant__ SkBatch<R
     const double gn = (double)Gp + (double)lv[p] - ((double)Mt + log2(St2));
     G[p] = (Real)(kap == 1.0 ? gn : kap * gn);
   }
+}
+
+template <typename Real, int MAXP>
+__global__ void __launch_bounds__(256) sk_cols(const __grid_constant__ SkBatch<Real, MAXP> P) {
+  const int pi = batch_problem(P);
+  cols_block<Real>(P.p[pi], (int)blockIdx.x - P.block0[pi]);
+}
+
+// ---------------------------------------------------------------------------
+// Batched Sinkhorn passes over many problems of different row lengths in one
+// launch (gw_solve_batch).  The problems' row-pass configurations all use
+// 512-thread blocks; a block finds its problem in a device-resident table
+// (binary search over the problems' first blocks) and runs that problem's
+// configuration on the band.  Blocks are scheduled onto the SMs as they free
+// up, so the small problems' bands fill the SMs beside the large ones'.
+// ---------------------------------------------------------------------------
+// Problems of one mixed launch: their states in device memory, their
+// configurations and first blocks in the (constant-cached) parameter block.
+constexpr int kMixMax = 256;
+template <typename Real>
+struct SkMixTable {
+  const SkProb<Real>* probs;    // [count], device memory
+  int count;
+  int cfg[kMixMax];             // row configuration ids
+  int block0[kMixMax + 1];      // first row-pass block of each problem
+  int cblock0[kMixMax + 1];     // first column-update block of each problem
+};
+
+__device__ __forceinline__ int find_owner(const int* first, int count, int b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+constexpr int kMixThreads = 512;
+
+template <typename Real>
+__global__ void __launch_bounds__(kMixThreads, 1) sk_pass_mix(const __grid_constant__ SkMixTable<Real> T,
+                                                              unsigned* status) {
+  extern __shared__ __align__(16) unsigned char smem_dyn[];
+  const int pi = find_owner(T.block0, T.count, (int)blockIdx.x);
+  const SkProb<Real> pr = T.probs[pi];
+  const int a = (int)blockIdx.x - T.block0[pi];
+  if constexpr (sizeof(Real) == 4) {
+    switch (T.cfg[pi]) {
+      case 0: pass_band<1, 16, 16, float>(pr, a, status, smem_dyn); break;
+      case 1: pass_band<2, 16, 8, float>(pr, a, status, smem_dyn); break;
+      case 2: pass_band<4, 16, 4, float>(pr, a, status, smem_dyn); break;
+      case 3: pass_band<8, 16, 2, float>(pr, a, status, smem_dyn); break;
+      case 4: pass_band<16, 16, 1, float>(pr, a, status, smem_dyn); break;
+      case 20: pass_band<2, 8, 8, float>(pr, a, status, smem_dyn); break;
+      case 21: pass_band<4, 8, 4, float>(pr, a, status, smem_dyn); break;
+      case 22: pass_band<8, 8, 2, float>(pr, a, status, smem_dyn); break;
+      default: pass_band<16, 8, 1, float>(pr, a, status, smem_dyn); break;  // 23
+    }
+  } else {
+    switch (T.cfg[pi]) {
+      case 10: pass_band<1, 8, 16, double>(pr, a, status, smem_dyn); break;
+      case 11: pass_band<4, 8, 4, double>(pr, a, status, smem_dyn); break;
+      case 12: pass_band<16, 8, 1, double>(pr, a, status, smem_dyn); break;
+      case 30: pass_band<2, 4, 8, double>(pr, a, status, smem_dyn); break;
+      default: pass_band<8, 4, 2, double>(pr, a, status, smem_dyn); break;  // 31
+    }
+  }
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256) sk_cols_mix(const __grid_constant__ SkMixTable<Real> T) {
+  const int pi = find_owner(T.cblock0, T.count, (int)blockIdx.x);
+  const SkProb<Real> pr = T.probs[pi];
+  cols_block<Real>(pr, (int)blockIdx.x - T.cblock0[pi]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1453,6 +1568,184 @@ int solve_launch(const SolveArgs& A, void* ws, size_t ws_bytes) {
 }
 
 int solve_group_key(const SolveArgs& A) { return row_config(A.m, A.dtype); }
+
+// ---------------------------------------------------------------------------
+// Mixed batches: problems of one schedule whose row configurations run
+// 512-thread blocks share every Sinkhorn launch (sk_pass_mix, sk_cols_mix).
+// ---------------------------------------------------------------------------
+bool solve_mixable(const SolveArgs& A) {
+  int dt = 0, nw = 0, vpt = 0, ng = 0;
+  if (!sk_config_shape(row_config(A.m, A.dtype), &dt, &nw, &vpt, &ng)) return false;
+  return 32 * nw * ng == kMixThreads;
+}
+
+namespace {
+template <typename Real>
+size_t mix_table_bytes(int count) {
+  return ((size_t)count * sizeof(SkProb<Real>) + 255) / 256 * 256;
+}
+
+template <typename Real>
+struct PrepareRun {
+  const SolveArgs& A;
+  void* ws;
+  size_t bytes;
+  SolveState<Real>* S;
+  template <int NW, int VPT, int NG, typename R>
+  int run() {
+    if constexpr (std::is_same<R, Real>::value) return prepare<NW, VPT, NG, Real>(A, ws, bytes, S);
+    return GW_ERR_INVALID;
+  }
+};
+
+template <typename Real>
+struct PlanRun {
+  SolveState<Real>* const* S;
+  int count;
+  cudaStream_t st;
+  unsigned* status;
+  Tracer* tracer;
+  template <int NW, int VPT, int NG, typename R>
+  int run() {
+    if constexpr (std::is_same<R, Real>::value) return launch_rows<NW, VPT, NG, Real, 32>(S, count, true, st, status, tracer);
+    return GW_ERR_INVALID;
+  }
+};
+
+// States of all problems (each prepared with its own row configuration),
+// their configuration ids, and the host image of the device table.
+template <typename Real>
+int mixed_prepare(const SolveArgs* const* A, void* const* ws, const size_t* ws_bytes, int count,
+                  std::vector<SolveState<Real>>& S, std::vector<int>& cfg) {
+  S.assign(count, SolveState<Real>{});
+  cfg.assign(count, 0);
+  for (int i = 0; i < count; ++i) {
+    cfg[i] = row_config(A[i]->m, A[i]->dtype);
+    PrepareRun<Real> r{*A[i], ws[i], ws_bytes[i], &S[i]};
+    const int rc = with_config(cfg[i], r);
+    if (rc != GW_OK) return rc;
+  }
+  return GW_OK;
+}
+
+template <typename Real>
+int mixed_table_typed(const SolveArgs* const* A, void* const* ws, const size_t* ws_bytes, int count, void* host) {
+  std::vector<SolveState<Real>> S;
+  std::vector<int> cfg;
+  int rc = mixed_prepare<Real>(A, ws, ws_bytes, count, S, cfg);
+  if (rc != GW_OK) return rc;
+  char* h = (char*)host;
+  memset(h, 0, mix_table_bytes<Real>(count));
+  SkProb<Real>* probs = (SkProb<Real>*)h;
+  for (int i = 0; i < count; ++i) probs[i] = S[i].sk;
+  return GW_OK;
+}
+
+template <typename Real>
+int mixed_launch_typed(const SolveArgs* const* A, void* const* ws, const size_t* ws_bytes, int count,
+                       const void* dev, cudaStream_t main, const cudaStream_t* workers, int nworkers,
+                       cudaEvent_t fork, const cudaEvent_t* join) {
+  std::vector<SolveState<Real>> S;
+  std::vector<int> cfg;
+  int rc = mixed_prepare<Real>(A, ws, ws_bytes, count, S, cfg);
+  if (rc != GW_OK) return rc;
+  // Parameter blocks of at most kMixMax problems each.
+  std::vector<SkMixTable<Real>> tabs;
+  std::vector<int> tblocks, tcblocks;
+  size_t smem = 0;
+  for (int base = 0; base < count; base += kMixMax) {
+    SkMixTable<Real> T;
+    memset(&T, 0, sizeof(T));
+    T.probs = (const SkProb<Real>*)dev + base;
+    T.count = std::min(kMixMax, count - base);
+    int blocks = 0, cblocks = 0;
+    for (int q = 0; q < T.count; ++q) {
+      const SolveState<Real>& st = S[base + q];
+      T.cfg[q] = cfg[base + q];
+      T.block0[q] = blocks;
+      T.cblock0[q] = cblocks;
+      blocks += st.sk.B;
+      cblocks += (st.sk.m + 31) / 32;
+      smem = std::max(smem, st.smem_pass);
+    }
+    T.block0[T.count] = blocks;
+    T.cblock0[T.count] = cblocks;
+    tabs.push_back(T);
+    tblocks.push_back(blocks);
+    tcblocks.push_back(cblocks);
+  }
+  if (!allow_dynamic_smem((const void*)sk_pass_mix<Real>, smem)) return GW_ERR_CUDA;
+  // Problems with the same configuration share their plan launches.
+  std::map<int, std::vector<SolveState<Real>*>> by_cfg;
+  for (int i = 0; i < count; ++i) by_cfg[cfg[i]].push_back(&S[i]);
+  unsigned* status = A[0]->status;
+  Tracer* tracer = A[0]->tracer;
+  const int nw = std::max(1, nworkers);
+  auto fork_out = [&]() -> int {
+    if (cudaEventRecord(fork, main) != cudaSuccess) return GW_ERR_CUDA;
+    for (int k = 0; k < nw; ++k)
+      if (cudaStreamWaitEvent(workers[k], fork, 0) != cudaSuccess) return GW_ERR_CUDA;
+    return GW_OK;
+  };
+  auto join_in = [&]() -> int {
+    for (int k = 0; k < nw; ++k) {
+      if (cudaEventRecord(join[k], workers[k]) != cudaSuccess) return GW_ERR_CUDA;
+      if (cudaStreamWaitEvent(main, join[k], 0) != cudaSuccess) return GW_ERR_CUDA;
+    }
+    return GW_OK;
+  };
+  // Per-problem work (setup, each step's cost, the step's end) runs on the
+  // worker streams, problem i on worker i mod nw; the Sinkhorn passes of all
+  // problems run on `main`, one launch each.
+  if ((rc = fork_out()) != GW_OK) return rc;
+  for (int i = 0; i < count; ++i) step_setup(S[i], workers[i % nw]);
+  const int n_outer = A[0]->n_outer, n_inner = A[0]->n_inner;
+  for (int l = 0; l < n_outer; ++l) {
+    for (int i = 0; i < count; ++i)
+      if ((rc = step_cost(S[i], workers[i % nw], l)) != GW_OK) return rc;
+    if ((rc = join_in()) != GW_OK) return rc;
+    for (int it = 0; it < n_inner; ++it) {
+      for (size_t t = 0; t < tabs.size(); ++t) {
+        TraceScope ts(tracer, "sk_pass", main);
+        sk_pass_mix<Real><<<tblocks[t], kMixThreads, smem, main>>>(tabs[t], status);
+      }
+      for (size_t t = 0; t < tabs.size(); ++t) {
+        TraceScope ts(tracer, "sk_cols", main);
+        sk_cols_mix<Real><<<tcblocks[t], 256, 0, main>>>(tabs[t]);
+      }
+    }
+    for (auto& kv : by_cfg) {
+      PlanRun<Real> r{kv.second.data(), (int)kv.second.size(), main, status, tracer};
+      if ((rc = with_config(kv.first, r)) != GW_OK) return rc;
+    }
+    if ((rc = fork_out()) != GW_OK) return rc;
+    for (int i = 0; i < count; ++i) step_after_plan(S[i], workers[i % nw]);
+  }
+  for (int i = 0; i < count; ++i)
+    if ((rc = step_finish(S[i], workers[i % nw])) != GW_OK) return rc;
+  if ((rc = join_in()) != GW_OK) return rc;
+  return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+}
+}  // namespace
+
+size_t solve_mixed_table_bytes(int count, int dtype) {
+  return dtype == GW_F32 ? mix_table_bytes<float>(count) : mix_table_bytes<double>(count);
+}
+
+int solve_mixed_table(const SolveArgs* const* A, void* const* ws, const size_t* ws_bytes, int count, void* host) {
+  if (count <= 0) return GW_OK;
+  if (A[0]->dtype == GW_F32) return mixed_table_typed<float>(A, ws, ws_bytes, count, host);
+  return mixed_table_typed<double>(A, ws, ws_bytes, count, host);
+}
+
+int solve_mixed_launch(const SolveArgs* const* A, void* const* ws, const size_t* ws_bytes, int count,
+                       const void* dev_table, cudaStream_t main, const cudaStream_t* workers, int nworkers,
+                       cudaEvent_t fork, const cudaEvent_t* join) {
+  if (count <= 0) return GW_OK;
+  if (A[0]->dtype == GW_F32)
+    return mixed_launch_typed<float>(A, ws, ws_bytes, count, dev_table, main, workers, nworkers, fork, join);
+  return mixed_launch_typed<double>(A, ws, ws_bytes, count, dev_table, main, workers, nworkers, fork, join);
+}
 
 int solve_group_launch(const SolveArgs* const* A, void* const* ws, const size_t* ws_bytes, int count,
                        cudaStream_t stream) {

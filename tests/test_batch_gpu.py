@@ -119,3 +119,30 @@ def test_batch_rejects_bad_problem():
     assert "[1]" in str(e.value)
     c.gw_solve_batch([], [], [], [])
 
+
+
+def test_batch_mixed_and_grouped_problems():
+    """Problems whose row configuration runs 512-thread blocks share every
+    Sinkhorn launch (one launch per pass over all of them, each block running
+    its own problem's configuration); longer rows (here 9000 columns) run in
+    their own group beside them.  Every result equals the single solve."""
+    import torch
+    from paper_2404_08970_gb300 import _lib as L
+    rng = np.random.default_rng(8)
+    shapes = [(40, 9000, 1), (300, 257, 2), (129, 3001, 1), (700, 75, 1), (64, 8192, 2), (33, 4097, 1)]
+    ws = [dict(nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=k, eps=5e-2, n_outer=2, n_inner=20,
+               u=I.dirichlet(n, 1.0, rng), v=I.dirichlet(m, 1.0, rng)) for (n, m, k) in shapes]
+    c = U.ctx()
+    probs = [_prob(L, w, "f32") for w in ws]
+    u, v, T, st, phi, psi = _dev(ws, "f32")
+    c.gw_solve_batch(probs, u, v, T, st)
+    c.gw_ctx_check()
+    for i, w in enumerate(ws):
+        T1 = torch.empty_like(T[i])
+        s1 = torch.zeros(8, dtype=torch.float64, device="cuda")
+        c.gw_solve(probs[i], u[i], v[i], T1, None, None, s1)
+        c.gw_ctx_check()
+        a, b = T[i].double().cpu().numpy(), T1.double().cpu().numpy()
+        assert np.linalg.norm(a - b) <= 1e-3 * np.linalg.norm(b), i
+        assert abs(float(st[i][0]) - float(s1[0])) <= 1e-5 * abs(float(s1[0])), i
+        assert float(st[i][5]) < 1e-5, i
