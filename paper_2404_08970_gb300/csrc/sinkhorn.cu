@@ -358,25 +358,26 @@ __device__ __forceinline__ void pass_band(const SkProb<Real>& pr, int a, unsigne
   // padded columns' G turns into exact zeros, with no per-element masks.  A
   // thread reads at most 2 * 16 bytes past the row's end (alignment offset
   // plus the 16-byte group straddling column m), so 48 bytes per slot are
-  // cleared, by all threads at once, as are the slots' barriers initialised.
+  // cleared.  Each group's first thread clears its group's slots, sets up
+  // their barriers and issues the first copies at once, so that their latency
+  // overlaps the loads of the band's potentials below.
   const int row_bytes = m * (int)sizeof(Real);
   const int zw = min((slot_bytes - row_bytes) / 4, 12);
-  for (int e = tid; e < NG * S * zw; e += NT) {
-    const int q = e / zw;
-    *reinterpret_cast<unsigned*>(ring + (size_t)q * slot_bytes + row_bytes + 4 * (e - q * zw)) = 0u;
-  }
-  fence_proxy_async_smem();
-  if (tid < NG * S) {
-    mbar_init(&full[tid], 1);
+  if (gt == 0) {
+    for (int q = 0; q < S; ++q) {
+      unsigned* z = reinterpret_cast<unsigned*>(gring + (size_t)q * slot_bytes + row_bytes);
+      for (int w = 0; w < zw; ++w) z[w] = 0u;
+      mbar_init(&gfull[q], 1);
+    }
     fence_mbar_init();
+    fence_proxy_async_smem();
+    for (int k = 0; k < S && g + k * NG < Ra; ++k) issue(k);
   }
   for (int t = tid; t < Ra; t += NT) {
     Fold[t] = F[s + t];
     LU[t] = pr.lu[s + t];
   }
   __syncthreads();
-  if (gt == 0)
-    for (int k = 0; k < S && g + k * NG < Ra; ++k) issue(k);
   Real Gv[VPT], acc[VPT];
 #pragma unroll
   for (int v = 0; v < VPT; ++v) {
