@@ -345,6 +345,12 @@ size_t grad1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms) {
   return k1_layout(n, m, k, dtype == GW_F32 ? 4 : 8, num_sms).end;
 }
 
+bool grad1d_regen_supported(int n, int m, int k, int ky, int dtype, int force_generic) {
+  const int kk = ky > 0 ? ky : k;
+  return dtype == GW_F32 && !force_generic && n >= 1 && m % 32 == 0 && m >= 32 && m <= 8192 && k >= 1 &&
+         k <= 2 && kk >= 1 && kk <= 2;
+}
+
 int grad1d_launch(const Grad1DArgs& a, void* ws, size_t ws_bytes) {
   if (a.ky != 0 && a.ky != a.k) return grad1d_launch_mixed(a, ws, ws_bytes);
   switch (a.k) {

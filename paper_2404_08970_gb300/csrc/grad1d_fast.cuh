@@ -56,14 +56,15 @@ struct FastSmem {
 };
 
 // KX: exponent of the column transform (X); K: of the row transform (Y).
-template <int KX, int K, int NW, int VPT, typename Real>
+// REGEN: the ring holds rows of Pi and T is formed from them (rF, rG, rc).
+template <int KX, int K, int NW, int VPT, typename Real, bool REGEN = false>
 __global__ void __launch_bounds__(32 * (NW + 1), 1)
     k1c_fast_rows(const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmG,
                   int use_tma_store, const Real* __restrict__ T, Real* __restrict__ G, int n,
                   int m, int R, const Real* __restrict__ q, const Real* __restrict__ cxh,
                   const Real* __restrict__ cxl, const Real* __restrict__ cyh, const Real* __restrict__ cyl, Real scale,
                   int use_tma, int stages, int slot_bytes, int vec_bytes, int box_cols, int ncopies,
-                  unsigned* status) {
+                  const Real* __restrict__ rF, const Real* __restrict__ rG, Real rc, unsigned* status) {
   using A = typename AccT<Real>::type;
   constexpr int NT = 32 * NW;        // compute threads
   constexpr int ALL = NT + 32;       // + scan warp
@@ -195,6 +196,14 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
     for (int e = 0; e <= KX; ++e) cst[v][e] = (p < m) ? q[((size_t)a * (KX + 1) + e) * m + p] : (Real)0;
   }
   constexpr int PER = 16 / sizeof(Real);
+  // REGEN: the ring holds rows of Pi and T = 2^(F_i + G_p - c Pi) is formed
+  // from them, with the columns' potentials G_p kept in registers (-inf for
+  // the padding columns, whose T stays 0).
+  Real gp[REGEN ? VPT : 1];
+  if constexpr (REGEN) {
+#pragma unroll
+    for (int v = 0; v < VPT; ++v) gp[v] = c0 + v < m ? rG[c0 + v] : (Real)-INFINITY;
+  }
   Real ex_prev[K + 1];
   // In-chunk forward states of the pending row (odd K, float).
   Real fl_prev[VPT];
@@ -239,6 +248,15 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
 #pragma unroll
       for (int j = 0; j < VPT / PER; ++j)
         xv[j] = *reinterpret_cast<const float4*>(xr + swz128((uint32_t)((c0 + j * PER) * sizeof(Real))));
+      if constexpr (REGEN) {
+        const Real fi = rF[i];
+#pragma unroll
+        for (int j = 0; j < VPT / PER; ++j) {
+          Real* x = reinterpret_cast<Real*>(&xv[j]);
+#pragma unroll
+          for (int w = 0; w < PER; ++w) x[w] = ex2(fma(-rc, x[w], gp[j * PER + w] + fi));
+        }
+      }
 #pragma unroll
       for (int j = 0; j < VPT / PER; ++j) {
         const Real* x = reinterpret_cast<const Real*>(&xv[j]);

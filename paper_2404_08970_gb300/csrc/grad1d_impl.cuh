@@ -278,7 +278,8 @@ constexpr int kA_VPT = 8;
 template <int K>
 __global__ void __launch_bounds__(1024, 1)
     k1a_band_moments_tma(const __grid_constant__ CUtensorMap tmT, int n, int m, int R, int slot_bytes,
-                         int box_cols, int ncopies, float* __restrict__ mu, unsigned* status) {
+                         int box_cols, int ncopies, float* __restrict__ mu, const float* __restrict__ rF,
+                         const float* __restrict__ rG, float rc, unsigned* status) {
   extern __shared__ __align__(16) unsigned char smem_dyn[];
   unsigned char* ring = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
   uint64_t* bars = reinterpret_cast<uint64_t*>(ring + (size_t)kA_STAGES * slot_bytes);
@@ -301,20 +302,28 @@ __global__ void __launch_bounds__(1024, 1)
   }
   __syncthreads();
   float m0[kA_VPT], c0k[kA_VPT], mr[K][kA_VPT];
+  // With rF set the ring holds rows of Pi: the plan's columns' potentials.
+  float gp[kA_VPT];
+  const bool active = c0 < m;
 #pragma unroll
   for (int v = 0; v < kA_VPT; ++v) {
     m0[v] = 0.f;
     c0k[v] = 0.f;
+    gp[v] = (rF && active) ? rG[c0 + v] : 0.f;
 #pragma unroll
     for (int r = 0; r < K; ++r) mr[r][v] = 0.f;
   }
-  const bool active = c0 < m;
   for (int j = 0; j < Ra; ++j) {
     const int slot = j % kA_STAGES;
     mbar_wait_bounded(&bars[slot], (unsigned)((j / kA_STAGES) & 1), status);
     if (active) {
       float x[kA_VPT];
       lds_swz<float, kA_VPT>(ring + (size_t)slot * slot_bytes, c0, x);
+      if (rF) {
+        const float fi = rF[s + Ra - 1 - j];
+#pragma unroll
+        for (int v = 0; v < kA_VPT; ++v) x[v] = ex2(fmaf(-rc, x[v], gp[v] + fi));
+      }
       const float tr = (float)(j + 1);  // R_a - t for row t = R_a - 1 - j
 #pragma unroll
       for (int v = 0; v < kA_VPT; ++v) {
@@ -848,8 +857,8 @@ int launch_k1c(const Grad1DArgs& g, const K1Layout& L, char* ws, int use_tma, cu
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }
 
-template <int KX, int K, int NW, int VPT, typename Real>
-int launch_k1c_fast(const Grad1DArgs& g, const K1Layout& L, char* ws, cudaStream_t st) {
+template <int KX, int K, int NW, int VPT, typename Real, bool REGEN>
+int launch_k1c_fast_as(const Grad1DArgs& g, const K1Layout& L, char* ws, cudaStream_t st) {
   CUtensorMap tm, tmg;
   memset(&tm, 0, sizeof tm);
   memset(&tmg, 0, sizeof tmg);
@@ -870,18 +879,33 @@ int launch_k1c_fast(const Grad1DArgs& g, const K1Layout& L, char* ws, cudaStream
   const int fl_bytes = (int)FastSmem<K, NW, VPT, Real>::fl_bytes;
   if (use_tma) stages = std::max(2, std::min(4, (200 * 1024 - 3 * vec_bytes - fl_bytes) / slot_bytes));
   const size_t smem = FastSmem<K, NW, VPT, Real>::bytes(slot_bytes, vec_bytes, stages);
-  auto kern = k1c_fast_rows<KX, K, NW, VPT, Real>;
+  auto kern = k1c_fast_rows<KX, K, NW, VPT, Real, REGEN>;
   TraceScope ts(g.tracer, "k1c_fast_rows", st);
   if (!allow_dynamic_smem((const void*)kern, smem))
     return GW_ERR_CUDA;
   const Real scale = (Real)(2.0 * g.out_scale * std::pow(g.hx, KX) * std::pow(g.hy, K));
   const Real* cx = (const Real*)(ws + L.cx_off);
   const Real* cy = (const Real*)(ws + L.cy_off);
+  const Real* rF = nullptr;
+  const Real* rG = nullptr;
+  if constexpr (REGEN) {
+    rF = g.regen_F;
+    rG = g.regen_G;
+  }
   kern<<<L.bands.B, 32 * (NW + 1), smem, st>>>(tm, tmg, use_tma_store, (const Real*)g.T, (Real*)g.G, g.n, g.m,
                                                 L.bands.R,
                                                 (const Real*)(ws + L.q_off), cx, cx + g.n, cy, cy + g.m, scale,
-                                                use_tma, stages, slot_bytes, vec_bytes, box_cols, 1, g.status);
+                                                use_tma, stages, slot_bytes, vec_bytes, box_cols, 1, rF, rG,
+                                                (Real)g.regen_c, g.status);
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
+}
+
+template <int KX, int K, int NW, int VPT, typename Real>
+int launch_k1c_fast(const Grad1DArgs& g, const K1Layout& L, char* ws, cudaStream_t st) {
+  if constexpr (sizeof(Real) == 4) {
+    if (g.regen_F) return launch_k1c_fast_as<KX, K, NW, VPT, Real, true>(g, L, ws, st);
+  }
+  return launch_k1c_fast_as<KX, K, NW, VPT, Real, false>(g, L, ws, st);
 }
 
 template <int K, typename Real, int VEC, int CPT>
@@ -952,11 +976,16 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
           if (allow_dynamic_smem((const void*)kern, smem)) {
             const int nt = std::max(32, (m / kA_VPT + 31) / 32 * 32);
             kern<<<B, nt, smem, st>>>(tm, n, m, R, slot_bytes, box_cols, (m / 32) / box_cols, (float*)mu,
-                                      g.status);
+                                      g.regen_F, g.regen_G, g.regen_c, g.status);
             done = true;
           }
         }
       }
+    }
+    if (!done && g.regen_F) {
+      note_failure("forming T from Pi needs the TMA-fed band-moment pass (float, target marginals, m a multiple "
+                   "of 32 up to 8192)");
+      return GW_ERR_INVALID;
     }
     if (done) {
     } else if constexpr (sizeof(Real) == 4) {
@@ -1026,6 +1055,10 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
         if (m <= 4096) return launch_k1c_fast<KX, KY, 16, 8, Real>(g, L, ws, st);
       }
     }
+  }
+  if (g.regen_F) {
+    note_failure("forming T from Pi needs the warp-specialised row kernel (float, k <= 2, m <= 8192)");
+    return GW_ERR_INVALID;
   }
   if constexpr (KX != KY) {
     note_failure("mixed distance exponents need rows of at most 8192 columns (4096 in double)");

@@ -112,6 +112,18 @@ __device__ __forceinline__ double acc_neg_of(double a) { return -a; }
 __device__ __forceinline__ float acc_round(ff a) { return ff_to_float(a); }
 __device__ __forceinline__ double acc_round(double a) { return a; }
 
+// exp2 on the special-function unit (relative error about 2 ulp, subnormal
+// results flushed to zero, which only drops terms below 2^-126 of a sum of
+// terms bounded by 1).  The plan T = 2^(F_i + G_p - c Pi_ip) is formed with
+// it wherever T is made from the potentials (the plan pass and the gradient
+// kernels that read the plan from Pi), so every form gives the same values.
+__device__ __forceinline__ float ex2(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double ex2(double x) { return exp2(x); }
+
 // Binomial coefficient C(r, s) for small r (compile-time friendly).
 __host__ __device__ constexpr int binom(int r, int s) {
   if (s < 0 || s > r) return 0;

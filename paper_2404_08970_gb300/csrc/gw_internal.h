@@ -68,6 +68,14 @@ struct Grad1DArgs {
   const double* v;
   int exact;            // 1: constant term from T's own marginals
   double out_scale;     // G := out_scale * (c_x + c_y - 2 D_X T D_Y)
+  // With regen_F set (float, target marginals), T is not read: `T` points to
+  // the cost Pi of the previous mirror-descent step and the kernels form the
+  // plan T_ip = 2^(regen_F[i] + regen_G[p] - regen_c Pi_ip) as they load it
+  // (the expression of the plan pass).  G may then be Pi itself: each row is
+  // read before it is written.
+  const float* regen_F;
+  const float* regen_G;
+  float regen_c;
   cudaStream_t stream;
   unsigned* status;     // device status word
   int num_sms;
@@ -102,6 +110,9 @@ bool encode_rows_tmap_box(void* tmap, const void* base, int n, int m, int elem_b
 size_t grad1d_workspace_bytes(int n, int m, int k, int dtype, int num_sms);
 // Launches the structured 1D gradient.  Returns GW_OK or an error.
 int grad1d_launch(const Grad1DArgs& a, void* ws, size_t ws_bytes);
+// Whether the 1D gradient can form T from (Pi, F, G) as it loads it (the
+// TMA-fed band-moment pass and the warp-specialised row kernel run).
+bool grad1d_regen_supported(int n, int m, int k, int ky, int dtype, int force_generic);
 
 // Per-exponent entry points (one translation unit each).
 int grad1d_launch_k1(const Grad1DArgs& a, void* ws, size_t ws_bytes);

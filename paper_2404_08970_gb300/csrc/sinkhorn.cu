@@ -34,15 +34,6 @@
 
 namespace gw {
 
-// exp2 on the special-function unit (relative error about 2 ulp, subnormal
-// results flushed to zero, which only drops terms below 2^-126 of a sum of
-// terms bounded by 1).
-__device__ __forceinline__ float ex2(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ double ex2(double x) { return exp2(x); }
 __device__ __forceinline__ float lg2(float x) { return log2f(x); }
 __device__ __forceinline__ double lg2(double x) { return log2(x); }
 
@@ -1172,7 +1163,7 @@ int prepare(const SolveArgs& A, void* wsv, size_t ws_bytes, SolveState<Real>* S)
 // Pi = out_scale * G(T) with target marginals (out_scale = 2 theta), or,
 // for the value, G(T) with T's own marginals.
 template <typename Real>
-int gradient(const SolveState<Real>& S, int exact, double out_scale, cudaStream_t st) {
+int gradient(const SolveState<Real>& S, int exact, double out_scale, cudaStream_t st, bool regen = false) {
   const SolveArgs& A = *S.A;
   if (A.dim >= 2) {
     Grad2DArgs g2{};
@@ -1215,6 +1206,16 @@ int gradient(const SolveState<Real>& S, int exact, double out_scale, cudaStream_
   ga.num_sms = A.num_sms;
   ga.tracer = A.tracer;
   ga.force_generic = A.force_generic;
+  if constexpr (sizeof(Real) == 4) {
+    if (regen) {
+      // The plan of the previous step is formed from Pi and the potentials
+      // as the gradient loads it; the new cost overwrites Pi row by row.
+      ga.T = S.sk.Pi;
+      ga.regen_F = S.sk.F;
+      ga.regen_G = S.sk.G;
+      ga.regen_c = S.sk.c;
+    }
+  }
   return grad1d_launch(ga, S.gws, S.gws_bytes);
 }
 
@@ -1253,6 +1254,15 @@ void ugw_scalars(const SolveState<Real>& S, cudaStream_t st) {
 
 // Pi for mirror-descent step l, then f = g = 0 (or, warm-started after the
 // first step, the previous step's potentials stay).
+// Single solves of 1D float problems whose gradient can read the plan from
+// Pi (balanced, tau = eps, at least two steps) never materialise the plan
+// between mirror-descent steps: it is formed from the previous step's Pi and
+// potentials inside the next gradient, and written only after the last step.
+bool plan_on_the_fly(const SolveArgs& A) {
+  return !A.batch && A.dim == 1 && A.dtype == GW_F32 && !(A.rho > 0.0) && A.tau == A.eps && A.n_outer >= 2 &&
+         grad1d_regen_supported(A.n, A.m, A.k, A.ky, A.dtype, A.force_generic);
+}
+
 template <typename Real>
 int step_cost(const SolveState<Real>& S, cudaStream_t st, int l) {
   const SolveArgs& A = *S.A;
@@ -1270,7 +1280,7 @@ int step_cost(const SolveState<Real>& S, cudaStream_t st, int l) {
     fill_val<Real><<<(A.m + 255) / 256, 256, 0, st>>>(S.sk.G, A.m, (Real)0);
     return GW_OK;
   }
-  int rc = gradient(S, 0, 2.0 * A.theta, st);
+  int rc = gradient(S, 0, 2.0 * A.theta, st, l > 0 && plan_on_the_fly(A));
   if (rc != GW_OK) return rc;
   if (fused<Real>(A)) {
     TraceScope ts(A.tracer, "add_feature_cost", st);
@@ -1388,6 +1398,7 @@ int solve_typed(const SolveArgs& A, void* ws, size_t ws_bytes) {
       rc = launch_rows<NW, VPT, NG, Real, 1>(list, 1, false, st, A.status, A.tracer);
       if (rc != GW_OK) return rc;
     }
+    if (l + 1 < A.n_outer && plan_on_the_fly(A)) continue;  // the next gradient forms the plan
     rc = launch_rows<NW, VPT, NG, Real, 1>(list, 1, true, st, A.status, A.tracer);
     if (rc != GW_OK) return rc;
     step_after_plan(S, st);

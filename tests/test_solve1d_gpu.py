@@ -203,3 +203,35 @@ def test_solve_invalid_arguments():
         with pytest.raises(L.GWError) as e:
             c.gw_solve(p, u, u, T)
         assert e.value.status == L.GW_ERR_INVALID
+
+
+@pytest.mark.parametrize("k,ky,theta", [(1, 0, 1.0), (2, 0, 1.0), (1, 2, 1.0), (2, 0, 0.5)])
+def test_plan_formed_on_the_fly(k, ky, theta):
+    """Float 1D solves whose gradient reads the previous step's plan straight
+    from Pi and the potentials (rows a multiple of 32 columns, balanced,
+    tau = eps): the plan is written once, after the last step (one plan
+    launch per solve), and the result matches the FP64 oracle."""
+    import torch
+    from paper_2404_08970_gb300 import _lib as L
+    rng = I.rng_for(41 + k + ky)
+    n, m = 300, 1024
+    w = dict(nx=n, ny=m, hx=1.0 / n, hy=1.0 / m, k=k, ky=ky, eps=5e-2, n_outer=5, n_inner=40,
+             u=I.dirichlet(n, 1.0, rng), v=I.dirichlet(m, 1.0, rng))
+    phi = psi = None
+    if theta < 1.0:
+        frng = np.random.default_rng(3)
+        phi, psi = I.features(n, 16, frng) * 0.1, I.features(m, 16, frng) * 0.1
+    c = U.ctx()
+    c.gw_ctx_profile(True)
+    c.gw_ctx_profile_report(reset=True)
+    try:
+        T, f, g, st = gpu_solve(w, "f32", theta, phi, psi)
+        rep = c.gw_ctx_profile_report(reset=True)
+    finally:
+        c.gw_ctx_profile(False)
+    assert rep["sk_plan"]["launches"] == 1, rep
+    assert rep["k1c_fast_rows"]["launches"] == w["n_outer"] + 1, rep  # 5 steps and the value
+    Ts, fs, gs, ss = oracle_solve(w, theta, phi, psi)
+    assert abs(st[0] - ss["obj"]) <= 1e-5 * abs(ss["obj"]), (st[0], ss["obj"])
+    assert fro(T, Ts) < 1e-3, fro(T, Ts)
+    assert st[5] < 1e-5
