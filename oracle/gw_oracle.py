@@ -26,7 +26,10 @@ direct, each function citing the part of the paper it follows:
 * entropic unbalanced GW (Remark "Entropic algorithm for UGW"): its
   objective, the step cost (1/2) grad E plus the scalar g, log-domain
   unbalanced Sinkhorn with KL-relaxed marginals, and the alternate
-  minimisation with mass rescaling.
+  minimisation with mass rescaling,
+* the fixed-support GW barycenter (named in the conclusion): entropic GW
+  solves against each input and the square-loss update of the barycenter's
+  distance matrix.
 
 Parity pins for every function live in tests/test_oracle_*.py.
 """
@@ -271,6 +274,38 @@ def fgw_value(DX, DY, T, theta: float, CC) -> float:
     """(1 - theta) <CC, T> + theta E(T)  (Remark "FGW")."""
     lin = 0.0 if CC is None else float(np.sum(CC * T))
     return (1.0 - theta) * lin + theta * value(DX, DY, T)
+
+
+# ---------------------------------------------------------------------------
+# Fixed-support GW barycenter (named in the conclusion as a GW variant the
+# fast gradient accelerates; the iteration is the cited barycenter method's
+# block coordinate descent with the square loss)
+# ---------------------------------------------------------------------------
+
+
+def barycenter_update(Ts, Cs, lambdas, p: np.ndarray) -> np.ndarray:
+    """The distance matrix of the barycenter for fixed couplings T_s (each
+    with first marginal p): the minimiser over C of
+      sum_s lambda_s sum_{i,j,k,l} (C_ij - C_s,kl)^2 T_s,ik T_s,jl,
+    which is C = sum_s lambda_s T_s C_s T_s^T / ((sum_s lambda_s) p p^T)."""
+    B = np.zeros((p.size, p.size))
+    for lam, T, C in zip(lambdas, Ts, Cs):
+        B = B + lam * (T @ C @ T.T)
+    return B / (float(np.sum(lambdas)) * np.outer(p, p))
+
+
+def barycenter(Cs, ps, lambdas, p: np.ndarray, C0: np.ndarray, eps: float, n_iter: int, n_outer: int,
+               n_inner: int):
+    """Fixed-support GW barycenter: n_iter rounds of (i) an entropic GW solve
+    between the barycenter (C, p) and each input (C_s, p_s) by mirror descent
+    (n_outer steps of n_inner Sinkhorn iterations, T^0 = p p_s^T each round)
+    and (ii) the update of C for those couplings.  Returns (C, [T_s])."""
+    C = np.array(C0, dtype=np.float64)
+    Ts = []
+    for _ in range(n_iter):
+        Ts = [mirror_descent(C, Cs_s, p, ps_s, eps, n_outer, n_inner)[0] for Cs_s, ps_s in zip(Cs, ps)]
+        C = barycenter_update(Ts, Cs, lambdas, p)
+    return C, Ts
 
 
 # ---------------------------------------------------------------------------

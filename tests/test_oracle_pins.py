@@ -774,3 +774,84 @@ def test_3d_gradient_matches_brute_force():
     T = rng.uniform(0.1, 1.0, size=(sx ** 3, sy ** 3))
     DX, DY = O.grid_dist_3d(sx, 0.7, "sqeuclid"), O.grid_dist_3d(sy, 0.4, "sqeuclid")
     assert relerr(O.grad_exact(DX, DY, T), O.grad_brute(DX, DY, T)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Fixed-support GW barycenter
+# ---------------------------------------------------------------------------
+
+def _bary_objective(C, Cs, Ts, lambdas):
+    """sum_s lambda_s sum_{i,j,k,l} (C_ij - C_s,kl)^2 T_s,ik T_s,jl, summed term by term."""
+    tot = 0.0
+    for lam, Csk, T in zip(lambdas, Cs, Ts):
+        d = C[:, :, None, None] - Csk[None, None, :, :]          # (i, j, k, l)
+        w = T[:, None, :, None] * T[None, :, None, :]           # T_ik T_jl
+        tot += lam * float(np.sum(d * d * w))
+    return tot
+
+
+def _bary_case(seed=0):
+    rng = np.random.default_rng(seed)
+    p = rng.dirichlet(np.ones(4))
+    Cs = [O.grid_dist_1d(5, 0.3, 1), O.grid_dist_1d(3, 0.5, 2)]
+    ps = [rng.dirichlet(np.ones(5)), rng.dirichlet(np.ones(3))]
+    Ts = [I.random_coupling(p, q, rng, spread=0.8) for q in ps]
+    return p, Cs, Ts, [0.25, 0.5]
+
+
+def test_barycenter_update_minimises_the_objective():
+    """The update's C is the stationary point (and, the objective being a
+    convex quadratic in C, the minimiser) of the brute-force objective for
+    fixed couplings: every central difference vanishes, every perturbation
+    increases it.  Planted mistakes (weights not normalised, transposed
+    couplings) are not stationary."""
+    p, Cs, Ts, lam = _bary_case()
+    C = O.barycenter_update(Ts, Cs, lam, p)
+    f0 = _bary_objective(C, Cs, Ts, lam)
+    h = 1e-4
+    for i in range(4):
+        for j in range(4):
+            E = np.zeros((4, 4))
+            E[i, j] = h
+            dfd = (_bary_objective(C + E, Cs, Ts, lam) - _bary_objective(C - E, Cs, Ts, lam)) / (2 * h)
+            assert abs(dfd) < 1e-9, (i, j, dfd)
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        assert _bary_objective(C + 1e-3 * rng.standard_normal((4, 4)), Cs, Ts, lam) > f0
+    B = sum(l * (T @ Ck @ T.T) for l, T, Ck in zip(lam, Ts, Cs))
+    unnormalised = B / np.outer(p, p)
+    one_sided = B / (float(np.sum(lam)) * p[:, None])
+    for bad in (unnormalised, one_sided):
+        worst = 0.0
+        for i in range(4):
+            for j in range(4):
+                E = np.zeros((4, 4))
+                E[i, j] = h
+                d = (_bary_objective(bad + E, Cs, Ts, lam) - _bary_objective(bad - E, Cs, Ts, lam)) / (2 * h)
+                worst = max(worst, abs(d))
+        assert worst > 1e-6
+
+
+def test_barycenter_update_identity_coupling_returns_the_input():
+    """With the identity coupling T = diag(p) of a space with itself the
+    update gives that space's distance matrix back exactly."""
+    p = np.array([0.1, 0.2, 0.3, 0.4])
+    C1 = O.grid_dist_1d(4, 0.25, 2)
+    assert np.allclose(O.barycenter_update([np.diag(p)], [C1], [1.0], p), C1, rtol=0, atol=1e-15)
+
+
+def test_barycenter_is_symmetric_and_uses_the_solver():
+    """The barycenter of symmetric inputs stays symmetric, and its couplings
+    are the mirror-descent solves against the final round's barycenter input."""
+    rng = np.random.default_rng(5)
+    Cs = [O.grid_dist_1d(6, 0.2, 1), O.grid_dist_1d(8, 1 / 8, 2)]
+    ps = [rng.dirichlet(np.ones(6)), rng.dirichlet(np.ones(8))]
+    p = np.full(5, 0.2)
+    C0 = rng.uniform(0, 1, (5, 5))
+    C0 = (C0 + C0.T) / 2
+    C1, _ = O.barycenter(Cs, ps, [0.3, 0.7], p, C0, 0.05, 1, 3, 30)
+    C2, Ts = O.barycenter(Cs, ps, [0.3, 0.7], p, C0, 0.05, 2, 3, 30)
+    assert np.max(np.abs(C2 - C2.T)) < 1e-15
+    T_direct = O.mirror_descent(C1, Cs[0], p, ps[0], 0.05, 3, 30)[0]
+    assert relerr(Ts[0], T_direct) < 1e-14
+    assert relerr(O.barycenter_update(Ts, Cs, [0.3, 0.7], p), C2) < 1e-14
