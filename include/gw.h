@@ -307,12 +307,15 @@ gw_status gw_solve(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const
  *                       doubles (layout as for gw_solve).
  *   The pointer arrays themselves are host memory, read during the call.
  *
- * Problems with the same row configuration (set by ny), dtype and schedule
- * form groups of up to 32 that advance in lock step: each Sinkhorn pass is
- * one launch over all row bands of the group's problems (bands of at least 32
- * rows), the gradients run per problem.  Groups run concurrently on up to 32
- * worker streams of the context, forked from and joined back into `stream`;
- * each problem gets its own region of a batch workspace owned by the context.
+ * Problems of one dtype and schedule whose rows fit the 512-thread row
+ * configurations (up to 8192 columns in float, 4096 in double) advance in
+ * lock step and share every Sinkhorn launch: each pass is one launch over all
+ * of their row bands (bands of at least 32 rows), each block running its own
+ * problem's row configuration; the gradients and statistics run per problem
+ * on worker streams.  Longer rows form groups of one row configuration (up
+ * to 32 problems per launch) beside them.  The worker streams belong to the
+ * context and are forked from and joined back into `stream`; each problem
+ * gets its own region of a batch workspace owned by the context.
  * The whole batch is captured once into one CUDA graph and relaunched while
  * the arguments are unchanged.  Results agree with gw_solve on each problem
  * alone up to rounding (the batch's longer row bands group the partial sums
@@ -323,6 +326,57 @@ gw_status gw_solve(gw_ctx* ctx, const gw_problem* prob, const double* d_u, const
 gw_status gw_solve_batch(gw_ctx* ctx, int count, const gw_problem* probs, const double* const* d_u,
                          const double* const* d_v, const double* const* d_phi, const double* const* d_psi,
                          void* const* d_T, double* const* d_stats, void* stream);
+
+/* Fixed-support GW barycenter problem (gw_barycenter). */
+typedef struct gw_barycenter_problem {
+  int count;    /* input spaces, 1 .. 64 */
+  int N;        /* barycenter points, 1 .. 4096 */
+  int k;        /* distance exponent of the input grids, 1 or 2 */
+  int dtype;    /* GW_F32 or GW_F64: plans, C and the solves' arithmetic */
+  double eps;   /* entropic regularisation of every GW solve (> 0) */
+  int n_iter;   /* barycenter rounds (>= 1) */
+  int n_outer;  /* mirror-descent steps per GW solve (>= 1) */
+  int n_inner;  /* Sinkhorn iterations per step (>= 1) */
+} gw_barycenter_problem;
+
+/*
+ * gw_barycenter - fixed-support GW barycenter of spaces on 1D grids (the
+ * conclusion names the barycenter among the GW variants that the fast
+ * gradient accelerates; the iteration is the cited barycenter method's
+ * block coordinate descent with the square loss).
+ *
+ * Input s is the grid of n[s] points i h[s] with distances h[s]^k |i - j|^k
+ * and marginal d_ps[s]; the barycenter has N points with weights d_p and a
+ * dense distance matrix C.  Each of prob->n_iter rounds solves entropic GW
+ * between (C, p) and every input by mirror descent (as gw_solve: T^0 = p
+ * p_s^T, cost 2 G with G = (C o C) p 1^T + 1 ((D_s o D_s) p_s)^T - 2 C T D_s,
+ * prob->n_outer steps of prob->n_inner Sinkhorn iterations at eps) and then
+ * sets
+ *     C = sum_s lambda[s] T_s D_s T_s^T / ((sum_s lambda[s]) p p^T).
+ * T D_s is the paper's O(N n) transform along the rows of T (double
+ * arithmetic); C (T D_s) and (T_s D_s) T_s^T are dense products accumulated
+ * in double.
+ *
+ *   n, h, lambda  host arrays of prob->count entries: grid sizes (1 .. 16384,
+ *                 10240 with GW_F64), spacings (finite, > 0), weights
+ *                 (finite, >= 0, positive sum).
+ *   d_ps          host array of prob->count device pointers to the inputs'
+ *                 marginals (double, n[s] each).
+ *   d_p           barycenter weights (device, double, N, positive).
+ *   d_C           device N x N row-major array of prob->dtype: the initial
+ *                 distance matrix on entry, the barycenter's on return.
+ *   d_stats       NULL, or 8 * count device doubles: for each input the
+ *                 statistics of its last round's solve (layout as gw_solve's
+ *                 stats, against the C of that round).
+ *
+ * The whole computation is captured once into a CUDA graph keyed by the
+ * arguments and relaunched while they are unchanged.  Errors: GW_ERR_INVALID
+ * for a bad descriptor, size or pointer; GW_ERR_OOM if the workspace cannot
+ * be allocated.
+ */
+gw_status gw_barycenter(gw_ctx* ctx, const gw_barycenter_problem* prob, const int* n, const double* h,
+                        const double* lambda, const double* const* d_ps, const double* d_p, void* d_C,
+                        double* d_stats, void* stream);
 
 /*
  * Serving: independent (fused) GW solves arriving over time (a deployment

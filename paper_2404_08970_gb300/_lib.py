@@ -66,6 +66,19 @@ class gw_problem(ctypes.Structure):
     ]
 
 
+class gw_barycenter_problem(ctypes.Structure):
+    _fields_ = [
+        ("count", ctypes.c_int),
+        ("N", ctypes.c_int),
+        ("k", ctypes.c_int),
+        ("dtype", ctypes.c_int),
+        ("eps", ctypes.c_double),
+        ("n_iter", ctypes.c_int),
+        ("n_outer", ctypes.c_int),
+        ("n_inner", ctypes.c_int),
+    ]
+
+
 class GWError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -101,6 +114,7 @@ def load() -> ctypes.CDLL:
         "gw_grad_noalloc": (S, [prob, P, P, P, P, I, P]),
         "gw_grad_host": (S, [P, prob, P, P, P, P, I, P]),
         "gw_solve_batch": (S, [P, I, prob, P, P, P, P, P, P, P]),
+        "gw_barycenter": (S, [P, ctypes.POINTER(gw_barycenter_problem), P, P, P, P, P, P, P, P]),
         "gw_server_create": (S, [ctypes.POINTER(P), I, ctypes.c_size_t, I]),
         "gw_server_destroy": (None, [P]),
         "gw_submit": (S, [P, prob, P, P, P, P, P, ctypes.POINTER(ctypes.c_uint64)]),
@@ -285,6 +299,21 @@ class Context:
         st = self.lib.gw_solve_batch(self.h, cnt, arr, *[ctypes.cast(k, ctypes.c_void_p) if k is not None else None
                                                          for k in keep], _stream(stream))
         return self._check(st, "gw_solve_batch")
+
+    def gw_barycenter(self, prob: gw_barycenter_problem, n, h, lambdas, ps, p, C, stats=None, stream=None) -> int:
+        """n, h, lambdas: sequences of prob.count host values; ps: device
+        tensors (the inputs' marginals); p: device tensor (N); C: device
+        N x N tensor (in: initial distances, out: the barycenter's)."""
+        cnt = len(n)
+        n_arr = (ctypes.c_int * cnt)(*[int(x) for x in n])
+        h_arr = (ctypes.c_double * cnt)(*[float(x) for x in h])
+        l_arr = (ctypes.c_double * cnt)(*[float(x) for x in lambdas])
+        p_arr = (ctypes.c_void_p * cnt)(*[_ptr(x) for x in ps])
+        st = self.lib.gw_barycenter(self.h, ctypes.byref(prob), ctypes.cast(n_arr, ctypes.c_void_p),
+                                    ctypes.cast(h_arr, ctypes.c_void_p), ctypes.cast(l_arr, ctypes.c_void_p),
+                                    ctypes.cast(p_arr, ctypes.c_void_p), _ptr(p), _ptr(C), _ptr(stats),
+                                    _stream(stream))
+        return self._check(st, "gw_barycenter")
 
     def gw_grad_dense(self, prob: gw_problem, u, v, T, G, marginals=GW_MARG_TARGET, precision=GW_DENSE_BF16,
                       stream=None) -> int:

@@ -721,6 +721,77 @@ gw_status gw_solve(gw_ctx* c, const gw_problem* p, const double* d_u, const doub
       "gw_solve");
 }
 
+gw_status gw_barycenter(gw_ctx* c, const gw_barycenter_problem* p, const int* n, const double* h,
+                        const double* lambda, const double* const* d_ps, const double* d_p, void* d_C,
+                        double* d_stats, void* stream) {
+  if (!c) return GW_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(c->mu);
+  if (!p) return fail(c, GW_ERR_INVALID, "gw_barycenter: problem descriptor is NULL");
+  if (p->count < 1 || p->count > 64) return fail(c, GW_ERR_INVALID, "gw_barycenter: count must be in [1, 64]");
+  if (p->N < 1 || p->N > 4096) return fail(c, GW_ERR_INVALID, "gw_barycenter: N must be in [1, 4096]");
+  if (p->k != 1 && p->k != 2) return fail(c, GW_ERR_INVALID, "gw_barycenter: k must be 1 or 2");
+  if (p->dtype != GW_F32 && p->dtype != GW_F64)
+    return fail(c, GW_ERR_INVALID, "gw_barycenter: dtype must be GW_F32 or GW_F64");
+  if (!finite_pos(p->eps) || p->n_iter < 1 || p->n_outer < 1 || p->n_inner < 1)
+    return fail(c, GW_ERR_INVALID, "gw_barycenter: need eps > 0 and n_iter, n_outer, n_inner >= 1");
+  if (!n || !h || !lambda || !d_ps || !d_p || !d_C)
+    return fail(c, GW_ERR_INVALID, "gw_barycenter: n, h, lambda, d_ps, d_p and d_C must not be NULL");
+  double wsum = 0.0;
+  const int nmax = p->dtype == GW_F64 ? gw::kMaxSolveF64Y : 16384;
+  for (int s = 0; s < p->count; ++s) {
+    if (n[s] < 1 || n[s] > nmax) return fail(c, GW_ERR_INVALID, "gw_barycenter: n[%d] must be in [1, %d]", s, nmax);
+    if (!finite_pos(h[s])) return fail(c, GW_ERR_INVALID, "gw_barycenter: h[%d] must be finite and > 0", s);
+    if (!std::isfinite(lambda[s]) || lambda[s] < 0.0)
+      return fail(c, GW_ERR_INVALID, "gw_barycenter: lambda[%d] must be finite and >= 0", s);
+    if (!d_ps[s]) return fail(c, GW_ERR_INVALID, "gw_barycenter: d_ps[%d] is NULL", s);
+    wsum += lambda[s];
+  }
+  if (!(wsum > 0.0)) return fail(c, GW_ERR_INVALID, "gw_barycenter: the weights must have a positive sum");
+  if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, GW_ERR_CUDA, "cudaSetDevice failed");
+  const std::vector<int> nv(n, n + p->count);
+  const std::vector<double> hv(h, h + p->count), lv(lambda, lambda + p->count);
+  const std::vector<const double*> pv(d_ps, d_ps + p->count);
+  gw::BarycenterArgs a{};
+  a.count = p->count;
+  a.N = p->N;
+  a.k = p->k;
+  a.dtype = p->dtype;
+  a.n = nv.data();
+  a.h = hv.data();
+  a.lambda = lv.data();
+  a.ps = pv.data();
+  a.p = d_p;
+  a.C = d_C;
+  a.values = d_stats;
+  a.eps = p->eps;
+  a.n_iter = p->n_iter;
+  a.n_outer = p->n_outer;
+  a.n_inner = p->n_inner;
+  a.stream = (cudaStream_t)stream;
+  a.status = c->status;
+  a.num_sms = c->num_sms;
+  a.tracer = c->tr();
+  gw_status s = ensure_ws(c, gw::barycenter_workspace_bytes(a));
+  if (s != GW_OK) return s;
+  std::string key = "bary ";
+  char buf[256];
+  snprintf(buf, sizeof buf, "%d %d %d %d %.17g %d %d %d %p %p %p %p %zu|", a.count, a.N, a.k, a.dtype, a.eps, a.n_iter,
+           a.n_outer, a.n_inner, (void*)d_p, d_C, (void*)d_stats, c->ws, c->ws_bytes);
+  key += buf;
+  for (int q = 0; q < a.count; ++q) {
+    snprintf(buf, sizeof buf, "%d %.17g %.17g %p|", nv[q], hv[q], lv[q], (void*)pv[q]);
+    key += buf;
+  }
+  return run_graph(
+      c, key, a.stream,
+      [&](cudaStream_t st) {
+        gw::BarycenterArgs ac = a;
+        ac.stream = st;
+        return gw::barycenter_launch(ac, c->ws, c->ws_bytes);
+      },
+      "gw_barycenter");
+}
+
 gw_status gw_solve_batch(gw_ctx* c, int count, const gw_problem* probs, const double* const* d_u,
                          const double* const* d_v, const double* const* d_phi, const double* const* d_psi,
                          void* const* d_T, double* const* d_stats, void* stream) {

@@ -228,6 +228,47 @@ struct SolveArgs {
   Tracer* tracer;
   int force_generic;
   int batch;  // 1: part of a batch (row bands of at least 32 rows)
+  // Barycenter solves: X is a dense N x N distance matrix (Real, row-major)
+  // instead of a grid; Y is the 1D grid of m points (hy, k).
+  const void* dense_x;
+};
+
+// Gradient with a dense X side (barycenter.cu): G = out_scale ((C o C) u 1^T +
+// 1 ((D o D) v)^T - 2 C T D) with C dense N x N and D the 1D grid distance
+// of n points (hy, k = 1 or 2); T and G are N x n in dtype.
+struct DenseXGradArgs {
+  int N, n, k, dtype, exact;
+  double hy, out_scale;
+  const void* C;
+  const void* T;
+  void* G;
+  const double *u, *v;
+  cudaStream_t stream;
+  Tracer* tracer;
+};
+size_t dense_x_workspace_bytes(int N, int n, int dtype);
+int dense_x_grad_launch(const DenseXGradArgs& a, void* ws, size_t ws_bytes);
+
+// Fixed-support GW barycenter of `count` 1D grid spaces (n[s] points, spacing
+// h[s], exponent k, marginals ps[s]) with weights lambda, on N points with
+// weights p; C (N x N, dtype) is the initial distance matrix and receives
+// the result; values (8 doubles per input, nullable) the statistics of the
+// last round's solves.
+struct BarycenterArgs {
+  int count, N, k, dtype;
+  const int* n;
+  const double* h;
+  const double* lambda;
+  const double* const* ps;
+  const double* p;
+  void* C;
+  double* values;
+  double eps;
+  int n_iter, n_outer, n_inner;
+  cudaStream_t stream;
+  unsigned* status;
+  int num_sms;
+  Tracer* tracer;
 };
 
 size_t solve_workspace_bytes(const SolveArgs& a);
@@ -251,6 +292,10 @@ int solve_mixed_table(const SolveArgs* const* A, void* const* ws, const size_t* 
 int solve_mixed_launch(const SolveArgs* const* A, void* const* ws, const size_t* ws_bytes, int count,
                        const void* dev_table, cudaStream_t main, const cudaStream_t* workers, int nworkers,
                        cudaEvent_t fork, const cudaEvent_t* join);
+
+size_t barycenter_workspace_bytes(const BarycenterArgs& a);
+int barycenter_launch(const BarycenterArgs& a, void* ws, size_t ws_bytes);
+SolveArgs barycenter_solve_args(const BarycenterArgs& a, int s, const void* C, void* T, double* stats);
 
 // Sinkhorn row configurations (sinkhorn.cu): the built-in choice for m
 // columns, the shape of a configuration id, and every id (count returned, at

@@ -1165,6 +1165,24 @@ int prepare(const SolveArgs& A, void* wsv, size_t ws_bytes, SolveState<Real>* S)
 template <typename Real>
 int gradient(const SolveState<Real>& S, int exact, double out_scale, cudaStream_t st, bool regen = false) {
   const SolveArgs& A = *S.A;
+  if (A.dense_x) {
+    DenseXGradArgs d{};
+    d.N = A.n;
+    d.n = A.m;
+    d.k = A.k;
+    d.dtype = A.dtype;
+    d.exact = exact;
+    d.hy = A.hy;
+    d.out_scale = out_scale;
+    d.C = A.dense_x;
+    d.T = A.T;
+    d.G = (void*)S.sk.Pi;
+    d.u = A.u;
+    d.v = A.v;
+    d.stream = st;
+    d.tracer = A.tracer;
+    return dense_x_grad_launch(d, S.gws, S.gws_bytes);
+  }
   if (A.dim >= 2) {
     Grad2DArgs g2{};
     g2.dim = A.dim;
@@ -1259,7 +1277,8 @@ void ugw_scalars(const SolveState<Real>& S, cudaStream_t st) {
 // between mirror-descent steps: it is formed from the previous step's Pi and
 // potentials inside the next gradient, and written only after the last step.
 bool plan_on_the_fly(const SolveArgs& A) {
-  return !A.batch && A.dim == 1 && A.dtype == GW_F32 && !(A.rho > 0.0) && A.tau == A.eps && A.n_outer >= 2 &&
+  return !A.batch && !A.dense_x && A.dim == 1 && A.dtype == GW_F32 && !(A.rho > 0.0) && A.tau == A.eps &&
+         A.n_outer >= 2 &&
          grad1d_regen_supported(A.n, A.m, A.k, A.ky, A.dtype, A.force_generic);
 }
 
@@ -1546,8 +1565,9 @@ size_t solve_workspace_bytes(const SolveArgs& A) {
   add((size_t)n * 8);
   add((size_t)n * 8);
   add(kUgwScal * 8);
-  const size_t g = A.dim >= 2 ? grid_grad_workspace_bytes(A.dim, A.nx, A.ny, A.dtype, A.cost, A.k)
-                              : grad1d_workspace_bytes(n, m, A.k, A.dtype, A.num_sms);
+  const size_t g = A.dense_x ? dense_x_workspace_bytes(n, m, A.dtype)
+                  : A.dim >= 2 ? grid_grad_workspace_bytes(A.dim, A.nx, A.ny, A.dtype, A.cost, A.k)
+                               : grad1d_workspace_bytes(n, m, A.k, A.dtype, A.num_sms);
   return b + g + 4096;
 }
 

@@ -30,20 +30,24 @@ def test_null_context_is_rejected_without_touching_the_device(lib):
     assert lib.gw_last_error(None) == b"no context"
 
 
-def test_problem_struct_layout_matches_header(tmp_path):
-    """Offsets of gw_problem as the C compiler lays it out == the ctypes mirror."""
+@pytest.mark.parametrize("cname,pytype", [("gw_problem", "gw_problem"),
+                                           ("gw_barycenter_problem", "gw_barycenter_problem")])
+def test_problem_struct_layout_matches_header(tmp_path, cname, pytype):
+    """Offsets of the descriptor structs as the C compiler lays them out ==
+    the ctypes mirrors."""
     import shutil
     import subprocess
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    fields = [f for f, _ in L.gw_problem._fields_]
+    py = getattr(L, pytype)
+    fields = [f for f, _ in py._fields_]
     src = tmp_path / "layout.c"
-    body = "".join(f'  printf("%zu\\n", offsetof(gw_problem, {f}));\n' for f in fields)
+    body = "".join(f'  printf("%zu\\n", offsetof({cname}, {f}));\n' for f in fields)
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "gw.h"\nint main(void){\n'
-                   + body + '  printf("%zu\\n", sizeof(gw_problem));\n  return 0;\n}\n')
+                   + body + f'  printf("%zu\\n", sizeof({cname}));\n  return 0;\n}}\n')
     exe = tmp_path / "layout"
     subprocess.run([cc, "-I", os.path.join(L.ROOT, "include"), str(src), "-o", str(exe)], check=True)
     out = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
-    want = [getattr(L.gw_problem, f).offset for f in fields] + [ctypes.sizeof(L.gw_problem)]
+    want = [getattr(py, f).offset for f in fields] + [ctypes.sizeof(py)]
     assert out == want
