@@ -296,6 +296,62 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Float rows with the c_y table staged in shared memory (hi and lo side by
+// side, one 8-byte shared load per element): loading the table from L2 for
+// every element bounded g2_epi (long-scoreboard stalls).  The table is read
+// with plain shared-memory loads only; everything else as g2_epi.
+template <int NQ>
+__global__ void __launch_bounds__(512, 2)
+    g2_epi_cs(float* __restrict__ G, int n, int sy, const float* __restrict__ Cy, const float* __restrict__ UV) {
+  extern __shared__ __align__(16) float2 g2_cys[];
+  const int lane = threadIdx.x & 31;
+  const int w0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int m = sy * sy;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) g2_cys[p] = make_float2(Cy[p], Cy[m + p]);
+  __syncthreads();
+  Quad<float> nxt[NQ];
+  auto fetch = [&](int i) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int d = lane + 32 * q;
+      nxt[q] = (i < n && d < sy) ? load_quad(UV + ((size_t)i * sy + d) * 4) : Quad<float>{0, 0, 0, 0};
+    }
+  };
+  fetch(w0);
+  for (int i = w0; i < n; i += nw) {
+    Quad<float> cur[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) cur[q] = nxt[q];
+    fetch(i + nw);
+    float* grow = G + (size_t)i * m;
+#pragma unroll
+    for (int qc = 0; qc < NQ; ++qc) {
+      const int cmax = min(32, sy - 32 * qc);
+#pragma unroll 4
+      for (int l = 0; l < cmax; ++l) {
+        const int c = 32 * qc + l;
+        const float uh = __shfl_sync(0xffffffffu, cur[qc].uh, l);
+        const float ul = __shfl_sync(0xffffffffu, cur[qc].ul, l);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int d = lane + 32 * q;
+          if (d < sy) {
+            const int p = c * sy + d;
+            const float2 cv = g2_cys[p];
+            float g = (uh + cur[q].vh) + cv.x;
+            g += (ul + cur[q].vl) + cv.y;
+            __stcs(grow + p, g);
+          }
+        }
+      }
+    }
+  }
+}
+
+// Largest c_y table staged in shared memory: two blocks of g2_epi_cs per SM.
+constexpr size_t kEpiSmemMax = 100 * 1024;
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -422,8 +478,22 @@ int grad2d_typed(const Grad2DArgs& A, void* wsv, size_t ws_bytes) {
   }
   {
     TraceScope ts(A.tracer, "g2_epi", st);
-    const int blocks = std::max(1, std::min((n + 7) / 8, resident_blocks(g2_epi<Real, NQ>, 256) * A.num_sms));
-    g2_epi<Real, NQ><<<blocks, 256, 0, st>>>((Real*)A.G, n, sy, (const Real*)(ws + L.Cy), (const Real*)(ws + L.UV));
+    const size_t cs_bytes = (size_t)m * sizeof(float2);
+    bool staged = false;
+    if constexpr (sizeof(Real) == 4) {
+      if (cs_bytes <= kEpiSmemMax && allow_dynamic_smem((const void*)g2_epi_cs<NQ>, cs_bytes)) {
+        const int blocks =
+            std::max(1, std::min((n + 15) / 16, resident_blocks(g2_epi_cs<NQ>, 512, cs_bytes) * A.num_sms));
+        g2_epi_cs<NQ><<<blocks, 512, cs_bytes, st>>>((float*)A.G, n, sy, (const float*)(ws + L.Cy),
+                                                     (const float*)(ws + L.UV));
+        staged = true;
+      }
+    }
+    if (!staged) {
+      const int blocks = std::max(1, std::min((n + 7) / 8, resident_blocks(g2_epi<Real, NQ>, 256) * A.num_sms));
+      g2_epi<Real, NQ><<<blocks, 256, 0, st>>>((Real*)A.G, n, sy, (const Real*)(ws + L.Cy),
+                                               (const Real*)(ws + L.UV));
+    }
   }
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }

@@ -366,6 +366,60 @@ __global__ void __launch_bounds__(256, g3_min_blocks<Real, NQ>(4))
   }
 }
 
+// Float rows with the c_y table staged in shared memory (hi and lo side by
+// side, one 8-byte shared load per element): loading the table from L2 for
+// every element bounded g3_epi (long-scoreboard stalls).  Plain shared loads
+// only; everything else as g3_epi.
+template <int NQ>
+__global__ void __launch_bounds__(512, 2)
+    g3_epi_cs(float* __restrict__ G, int n, int sy, const float* __restrict__ Cy, const float* __restrict__ U) {
+  extern __shared__ __align__(16) float2 g3_cys[];
+  const int lane = threadIdx.x & 31;
+  const int w0 = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int q2 = sy * sy;
+  const int m = q2 * sy;
+  for (int p = threadIdx.x; p < m; p += blockDim.x) g3_cys[p] = make_float2(Cy[p], Cy[m + p]);
+  __syncthreads();
+  for (int i = w0; i < n; i += nw) {
+    const float* ur = U + (size_t)i * sy * 6;
+    const float u0h = lane < sy ? ur[lane * 6] : 0.f;
+    const float u0l = lane < sy ? ur[lane * 6 + 1] : 0.f;
+    float uh[NQ], ul[NQ];
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+      const int q = lane + 32 * j;
+      if (q < q2) {
+        const int y1 = q / sy, y2 = q % sy;
+        const ff sum = ff_add(acc_of(ur[y1 * 6 + 2], ur[y1 * 6 + 3]), acc_of(ur[y2 * 6 + 4], ur[y2 * 6 + 5]));
+        uh[j] = sum.hi;
+        ul[j] = sum.lo;
+      } else {
+        uh[j] = ul[j] = 0.f;
+      }
+    }
+    float* grow = G + (size_t)i * m;
+    for (int y0 = 0; y0 < sy; ++y0) {
+      const float ah = __shfl_sync(0xffffffffu, u0h, y0);
+      const float al = __shfl_sync(0xffffffffu, u0l, y0);
+#pragma unroll
+      for (int j = 0; j < NQ; ++j) {
+        const int q = lane + 32 * j;
+        if (q < q2) {
+          const int p = y0 * q2 + q;
+          const float2 cv = g3_cys[p];
+          float g = (ah + uh[j]) + cv.x;
+          g += (al + ul[j]) + cv.y;
+          __stcs(grow + p, g);
+        }
+      }
+    }
+  }
+}
+
+// Largest c_y table staged in shared memory: two blocks of g3_epi_cs per SM.
+constexpr size_t kEpi3SmemMax = 100 * 1024;
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -497,8 +551,22 @@ int grad3d_typed(const Grad2DArgs& A, void* wsv, size_t ws_bytes) {
   }
   {
     TraceScope ts(A.tracer, "g3_epi", st);
-    const int blocks = std::max(1, std::min((n + 7) / 8, resident_blocks(g3_epi<Real, NQ>, 256) * A.num_sms));
-    g3_epi<Real, NQ><<<blocks, 256, 0, st>>>((Real*)A.G, n, sy, (const Real*)(ws + L.Cy), (const Real*)(ws + L.U));
+    const size_t cs_bytes = (size_t)m * sizeof(float2);
+    bool staged = false;
+    if constexpr (sizeof(Real) == 4) {
+      if (cs_bytes <= kEpi3SmemMax && allow_dynamic_smem((const void*)g3_epi_cs<NQ>, cs_bytes)) {
+        const int blocks =
+            std::max(1, std::min((n + 15) / 16, resident_blocks(g3_epi_cs<NQ>, 512, cs_bytes) * A.num_sms));
+        g3_epi_cs<NQ><<<blocks, 512, cs_bytes, st>>>((float*)A.G, n, sy, (const float*)(ws + L.Cy),
+                                                     (const float*)(ws + L.U));
+        staged = true;
+      }
+    }
+    if (!staged) {
+      const int blocks = std::max(1, std::min((n + 7) / 8, resident_blocks(g3_epi<Real, NQ>, 256) * A.num_sms));
+      g3_epi<Real, NQ><<<blocks, 256, 0, st>>>((Real*)A.G, n, sy, (const Real*)(ws + L.Cy),
+                                               (const Real*)(ws + L.U));
+    }
   }
   return cudaPeekAtLastError() == cudaSuccess ? GW_OK : GW_ERR_CUDA;
 }
