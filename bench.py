@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-solve", dest="solve", action="store_false")
     ap.add_argument("--no-2d", dest="grid2d", action="store_false")
     ap.add_argument("--no-3d", dest="grid3d", action="store_false")
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
     ap.add_argument("--no-batch", dest="batch", action="store_false")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--no-serve", dest="serve", action="store_false")
@@ -414,6 +415,86 @@ def bench_3d(ctx, L, dev, stream, barrier, steps, with_solve):
         ctx.gw_ctx_check(stream)
         out["solve"] = {"schedule": "eps=5e-3, 20 x 100", "solves_per_s": 1e3 / sms, "ms": sms,
                         "gw_value": float(stats[1].item()), "col_marginal_err": float(stats[5].item())}
+    return out
+
+
+def bench_variants(ctx, L, dev, stream, barrier):
+    """The method's variants on 1D grids, one timed call each after a warm-up
+    call: entropic unbalanced GW (rho = 1) and mirror descent with tau = 2 eps
+    and warm-started Sinkhorn at n = m = 4096 (eps = 1e-2, 20 x 100), mixed
+    exponents (k_X, k_Y) = (1, 2) in the gradient at 8192^2, and the
+    fixed-support barycenter of three grids (N = 1024; 1024, 2048 and 4096
+    points; 3 rounds of 5 x 50)."""
+    import numpy as np
+    import torch
+    from paper_2404_08970_gb300 import inputs as I
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=1):
+        fn()
+        barrier()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    n = 4096
+    w = I.workload_1d_grad(n, 1, "uniform", seed=0)
+    du = torch.from_numpy(w["u"]).to(dev)
+    dv = torch.from_numpy(w["v"]).to(dev)
+    T = torch.empty(n, n, dtype=torch.float32, device=dev)
+    stats = torch.zeros(8, dtype=torch.float64, device=dev)
+    passes_bytes = 4.0 * n * n * 20 * 100
+    for name, kw in (("ugw_solve", dict(rho=1.0)), ("tau_warm_solve", dict(tau=2e-2, warm_start=1))):
+        prob = L.problem(dim=1, nx=n, ny=n, hx=1.0 / n, hy=1.0 / n, k=1, eps=1e-2, n_outer=20, n_inner=100,
+                         dtype=L.GW_F32, **kw)
+        try:
+            ms = timed(lambda: ctx.gw_solve(prob, du, dv, T, None, None, stats, stream=stream))
+            ctx.gw_ctx_check(stream)
+            out[name] = {"workload": f"1D n = m = {n}, k = 1, uniform marginals, eps = 1e-2, 20 x 100, fp32, {kw}",
+                         "ms": ms, "solves_per_s": 1e3 / ms, "pi_stream_gbs": passes_bytes / (ms / 1e3) / 1e9,
+                         "value": float(stats[1].item())}
+        except Exception as ex:
+            out[name] = {"error": str(ex)[:200]}
+    nm = 8192
+    wm = I.workload_1d_grad(nm, 1, "uniform", seed=1)
+    dT = torch.from_numpy(wm["T"].astype(np.float32)).to(dev)
+    dG = torch.empty_like(dT)
+    dum = torch.from_numpy(wm["u"]).to(dev)
+    dvm = torch.from_numpy(wm["v"]).to(dev)
+    probm = L.problem(dim=1, nx=nm, ny=nm, hx=1.0 / nm, hy=1.0 / nm, k=1, ky=2, dtype=L.GW_F32)
+    try:
+        ms = timed(lambda: ctx.gw_grad(probm, dum, dvm, dT, dG, L.GW_MARG_TARGET, stream), 20)
+        out["mixed_k_gradient"] = {"workload": "1D n = m = 8192, (k_X, k_Y) = (1, 2), fp32", "ms": ms,
+                                   "grad_evals_per_s": 1e3 / ms, "gbs_8B": 8.0 * nm * nm / (ms / 1e3) / 1e9}
+    except Exception as ex:
+        out["mixed_k_gradient"] = {"error": str(ex)[:200]}
+    del dT, dG
+    N, ns = 1024, [1024, 2048, 4096]
+    rng = I.rng_for(2)
+    ps = [torch.from_numpy(I.dirichlet(q, 1.0, rng)).to(dev) for q in ns]
+    dp = torch.from_numpy(I.uniform_weights(N)).to(dev)
+    C0 = np.abs(np.arange(N)[:, None] - np.arange(N)[None, :]) / N
+    dC = torch.from_numpy(C0).to(dev, torch.float32)
+    bst = torch.zeros(8 * len(ns), dtype=torch.float64, device=dev)
+    bprob = L.gw_barycenter_problem(len(ns), N, 1, L.GW_F32, 1e-2, 3, 5, 50)
+
+    def bary():
+        dC.copy_(torch.from_numpy(C0).to(dev, torch.float32))
+        ctx.gw_barycenter(bprob, ns, [1.0 / q for q in ns], [1.0, 1.0, 1.0], ps, dp, dC, bst, stream)
+
+    try:
+        ms = timed(bary)
+        ctx.gw_ctx_check(stream)
+        out["barycenter"] = {"workload": "N = 1024 barycenter of 1D grids of 1024, 2048, 4096 points, k = 1, "
+                                         "eps = 1e-2, 3 rounds x 5 x 50, fp32", "ms": ms,
+                             "rounds_per_s": 3e3 / ms}
+    except Exception as ex:
+        out["barycenter"] = {"error": str(ex)[:200]}
     return out
 
 
@@ -802,6 +883,7 @@ def run_ours(args):
 
     grid2d = bench_2d(ctx, L, dev, stream, barrier, min(args.steps, 20), args.solve) if args.grid2d else None
     grid3d = bench_3d(ctx, L, dev, stream, barrier, min(args.steps, 20), args.solve) if args.grid3d else None
+    variants = bench_variants(ctx, L, dev, stream, barrier) if args.variants else None
     batch = bench_batch(ctx, L, dev, stream, barrier, args.batch_count) if args.batch else None
     serve = bench_serve(L, local, args.serve_count, args.serve_slots) if args.serve else None
 
@@ -833,7 +915,7 @@ def run_ours(args):
                 "clocks": clk, "gpu_launches": launches, "kernels": prof, "dense": dense,
                 "structured_f64": structured_f64,
                 "errors_vs_fp64": errs, "solve": solve,
-                "grid2d": grid2d, "grid3d": grid3d, "batch": batch, "serve": serve}
+                "grid2d": grid2d, "grid3d": grid3d, "variants": variants, "batch": batch, "serve": serve}
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -333,7 +333,8 @@ size_t barycenter_workspace_bytes(const BarycenterArgs& a) {
   size_t b = ((size_t)a.N * a.N * 8 + 255) / 256 * 256;
   int nmax = 1;
   for (int s = 0; s < a.count; ++s) {
-    SolveArgs sa = barycenter_solve_args(a, s, nullptr, nullptr, nullptr);
+    // Sized for the solves' dense-X gradient (a.C marks the dense side).
+    SolveArgs sa = barycenter_solve_args(a, s, a.C, nullptr, nullptr);
     b += (solve_workspace_bytes(sa) + 255) / 256 * 256;
     b += ((size_t)a.N * a.n[s] * rb + 255) / 256 * 256;
     nmax = std::max(nmax, a.n[s]);
@@ -390,7 +391,7 @@ int barycenter_typed(const BarycenterArgs& a, void* wsv, size_t ws_bytes) {
   std::vector<size_t> swb(a.count);
   int nmax = 1;
   for (int s = 0; s < a.count; ++s) {
-    SolveArgs sa = barycenter_solve_args(a, s, nullptr, nullptr, nullptr);
+    SolveArgs sa = barycenter_solve_args(a, s, a.C, nullptr, nullptr);
     swb[s] = solve_workspace_bytes(sa);
     sws[s] = take(swb[s]);
     Ts[s] = take((size_t)a.N * a.n[s] * sizeof(Real));

@@ -28,6 +28,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "gw_common.cuh"
@@ -945,16 +946,17 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
   Real* rowpart = (Real*)(ws + L.rowpart_off);
 
   // With target marginals the constant terms do not depend on T: given a
-  // side stream, they run there concurrently with k1a and k1b.
+  // side stream, they run there concurrently with k1b.
   const int dt = sizeof(Real) == 4 ? GW_F32 : GW_F64;
   const bool overlap = !g.exact && g.side && g.ev_fork && g.ev_join;
-  if (overlap) {
+  auto fork_consts = [&]() -> int {
     if (cudaEventRecord(g.ev_fork, st) != cudaSuccess || cudaStreamWaitEvent(g.side, g.ev_fork, 0) != cudaSuccess)
       return GW_ERR_CUDA;
     int rc = const_terms<KX, KY>(g, g.u, g.v, ws, L, dt, g.side);
     if (rc != GW_OK) return rc;
     if (cudaEventRecord(g.ev_join, g.side) != cudaSuccess) return GW_ERR_CUDA;
-  }
+    return GW_OK;
+  };
 
   // k1a: VEC columns per vector load, CPT column groups per thread.
   const bool vec_ok = (m % 4 == 0) && ((((uintptr_t)g.T) & 15) == 0);
@@ -1013,6 +1015,13 @@ int grad1d_launch_typed(const Grad1DArgs& g, void* wsv, size_t ws_bytes) {
     }
   }
   if (cudaPeekAtLastError() != cudaSuccess) return GW_ERR_CUDA;
+  // Forked after k1a, which streams T on every SM: the constant terms then
+  // share the GPU with k1b's second wave of blocks instead (172 against 174 us
+  // per 8192^2 gradient when forked before k1a).
+  if (overlap) {
+    int rc = fork_consts();
+    if (rc != GW_OK) return rc;
+  }
   const int nchunks = (m + 32 * vec_used - 1) / (32 * vec_used);
 
   // k1b

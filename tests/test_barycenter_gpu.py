@@ -49,7 +49,8 @@ def oracle_barycenter(N, ns, k, hs, ps, p, lam, C0, eps, n_iter, n_outer, n_inne
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("N,ns,k", [(12, (15, 20, 9), 1), (20, (33, 64), 2), (7, (100,), 1), (65, (70, 31), 2)])
+@pytest.mark.parametrize("N,ns,k", [(12, (15, 20, 9), 1), (20, (33, 64), 2), (7, (100,), 1), (65, (70, 31), 2),
+                                    (300, (700,), 1)])
 def test_barycenter_matches_oracle(N, ns, k, dtype):
     hs, ps, p, lam, C0 = _case(N, ns, k, seed=N + sum(ns))
     args = (N, ns, k, hs, ps, p, lam, C0, 5e-2, 3, 4, 40)
