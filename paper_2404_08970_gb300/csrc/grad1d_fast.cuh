@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
                   int use_tma, int stages, int slot_bytes, int vec_bytes, int box_cols, int ncopies,
                   const Real* __restrict__ rF, const Real* __restrict__ rG, Real rc, unsigned* status) {
   using A = typename AccT<Real>::type;
+  constexpr int kL2Ahead = 4;
   constexpr int NT = 32 * NW;        // compute threads
   constexpr int ALL = NT + 32;       // + scan warp
   constexpr int SEG = 32 * VPT;      // columns per compute warp
@@ -122,14 +123,22 @@ __global__ void __launch_bounds__(32 * (NW + 1), 1)
       for (int c = 0; c < ncopies; ++c)
         tma_load_3d(ring + (size_t)slot * slot_bytes + (size_t)c * box_cols * 128, &tmT, 0, c * box_cols, row, &bars[slot]);
     };
+    // Rows kL2Ahead beyond the ring are pulled into L2 early, so that more
+    // bytes per SM are in flight than the ring's slots hold.
+    const unsigned row_bytes = (unsigned)(m * sizeof(Real));
+    auto prefetch = [&](int t) {
+      if (t < Ra) bulk_prefetch_l2(T + (size_t)(s + t) * m, row_bytes);
+    };
     if (use_tma && lane == 0) {
       for (int st = 0; st < stages - 1 && st < Ra; ++st) issue(s + st, st);
+      for (int q = 0; q < kL2Ahead; ++q) prefetch(stages - 1 + q);
     }
     for (int t = 0; t < Ra; ++t) {
       named_sync(1 + (t & 1), ALL);  // totals(t) posted
       if (use_tma && lane == 0) {
         const int nt = t + stages - 1;
         if (nt < Ra) issue(s + nt, nt % stages);
+        prefetch(nt + kL2Ahead);
       }
       const Real* wt = wtot + (t & 1) * NW * 2 * (K + 1);
       A W[K + 1], V[K + 1];
