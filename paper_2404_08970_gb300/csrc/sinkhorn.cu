@@ -606,6 +606,11 @@ __global__ void __launch_bounds__(kMixThreads, 1) sk_pass_mix(const __grid_const
       case 20: pass_band<2, 8, 8, float>(pr, a, status, smem_dyn); break;
       case 21: pass_band<4, 8, 4, float>(pr, a, status, smem_dyn); break;
       case 22: pass_band<8, 8, 2, float>(pr, a, status, smem_dyn); break;
+      case 40: pass_band<1, 12, 16, float>(pr, a, status, smem_dyn); break;
+      case 41: pass_band<2, 12, 8, float>(pr, a, status, smem_dyn); break;
+      case 42: pass_band<4, 12, 4, float>(pr, a, status, smem_dyn); break;
+      case 43: pass_band<8, 12, 2, float>(pr, a, status, smem_dyn); break;
+      case 44: pass_band<16, 12, 1, float>(pr, a, status, smem_dyn); break;
       default: pass_band<16, 8, 1, float>(pr, a, status, smem_dyn); break;  // 23
     }
   } else {
@@ -1093,11 +1098,21 @@ RowGeom row_geom(int m) {
 }
 
 // Row bands of the Sinkhorn kernels.  A single solve spreads its rows over
-// all SMs; in a batch, problems share the GPU, so bands are at least 32 rows
-// (fewer blocks and fewer column partials per problem).
+// all SMs.  In a batch, problems share the GPU, and a band is one block's
+// whole work: each block pays for its ring set-up, the first copies' latency
+// and its column partials, so bands hold at least kBatchBandBytes of Pi (and
+// at least 32 rows, at most kBatchBandRowsMax, whose potentials the block
+// keeps in shared memory).  At 256 to 1024 columns this takes the batched pass
+// from 1.0-2.6 TB/s (32-row bands) to 1.9-4.1 TB/s.
+constexpr size_t kBatchBandBytes = 512 * 1024;
+constexpr int kBatchBandRowsMax = 1024;
 Bands solve_bands(const SolveArgs& A) {
   if (!A.batch) return choose_bands(A.n, A.num_sms);
-  const int target = std::max(1, std::min(A.num_sms, A.n / 32));
+  const size_t row_bytes = (size_t)A.m * (A.dtype == GW_F32 ? 4 : 8);
+  const int min_rows =
+      (int)std::min<size_t>(kBatchBandRowsMax, std::max<size_t>(32, (kBatchBandBytes + row_bytes - 1) / row_bytes));
+  const int fewest = (A.n + kBatchBandRowsMax - 1) / kBatchBandRowsMax;
+  const int target = std::max(fewest, std::min(A.num_sms, A.n / min_rows));
   return choose_bands(A.n, target);
 }
 
@@ -1464,10 +1479,13 @@ int solve_group(const SolveArgs* const* A, void* const* ws, const size_t* ws_byt
 
 // Row configurations of the Sinkhorn kernels: warps per row group NW, values
 // per thread VPT (a row group covers 32 NW VPT >= m columns), row groups per
-// block NG.  Ids 0-13 are the built-in choices by row length; ids 20-32 are
-// alternatives for the tuning table, each with half the values per thread of
-// the built-in configuration that covers the same columns.  with_config
-// below has one case per entry.
+// block NG.  Ids 0-13 and 40-44 are the built-in choices by row length; ids
+// 20-32 are alternatives for the tuning table, each with half the values per
+// thread of the built-in configuration that covers the same columns.  Ids
+// 40-44 (float, 12 values per thread) cover three quarters of the columns of
+// 0-4, so that a row just above a power of two does not pay for a row twice
+// its length: the passes are bound by the work per covered column, padding
+// included.  with_config below has one case per entry.
 struct SkConfig {
   int id, dtype, nw, vpt, ng;
 };
@@ -1476,7 +1494,8 @@ constexpr SkConfig kSkConfigs[] = {
     {4, GW_F32, 16, 16, 1}, {5, GW_F32, 18, 16, 1}, {6, GW_F32, 32, 16, 1}, {10, GW_F64, 1, 8, 16},
     {11, GW_F64, 4, 8, 4},  {12, GW_F64, 16, 8, 1}, {13, GW_F64, 32, 16, 1}, {20, GW_F32, 2, 8, 8},
     {21, GW_F32, 4, 8, 4},  {22, GW_F32, 8, 8, 2},  {23, GW_F32, 16, 8, 1}, {24, GW_F32, 32, 8, 1},
-    {30, GW_F64, 2, 4, 8},  {31, GW_F64, 8, 4, 2},  {32, GW_F64, 32, 4, 1},
+    {30, GW_F64, 2, 4, 8},  {31, GW_F64, 8, 4, 2},  {32, GW_F64, 32, 4, 1},  {40, GW_F32, 1, 12, 16},
+    {41, GW_F32, 2, 12, 8}, {42, GW_F32, 4, 12, 4}, {43, GW_F32, 8, 12, 2}, {44, GW_F32, 16, 12, 1},
 };
 
 bool sk_config_shape(int id, int* dtype, int* nw, int* vpt, int* ng) {
@@ -1500,10 +1519,15 @@ int sk_config_ids(int* out, int cap) {
 // Built-in row configuration for m columns.
 int sk_default_config(int m, int dtype) {
   if (dtype == GW_F32) {
+    if (m <= 384) return 40;
     if (m <= 512) return 0;
+    if (m <= 768) return 41;
     if (m <= 1024) return 1;
+    if (m <= 1536) return 42;
     if (m <= 2048) return 2;
+    if (m <= 3072) return 43;
     if (m <= 4096) return 3;
+    if (m <= 6144) return 44;
     if (m <= 8192) return 4;
     if (m <= 9216) return 5;
     return 6;
@@ -1539,6 +1563,11 @@ int with_config(int cfg, F&& f) {
     case 22: return f.template run<8, 8, 2, float>();
     case 23: return f.template run<16, 8, 1, float>();
     case 24: return f.template run<32, 8, 1, float>();
+    case 40: return f.template run<1, 12, 16, float>();
+    case 41: return f.template run<2, 12, 8, float>();
+    case 42: return f.template run<4, 12, 4, float>();
+    case 43: return f.template run<8, 12, 2, float>();
+    case 44: return f.template run<16, 12, 1, float>();
     case 30: return f.template run<2, 4, 8, double>();
     case 31: return f.template run<8, 4, 2, double>();
     case 32: return f.template run<32, 4, 1, double>();

@@ -14,7 +14,7 @@ from tests import gwtest_util as U
 
 pytestmark = pytest.mark.gpu
 
-ROWS = {"f32": [300, 1000, 2000, 4000, 8000], "f64": [200, 1000, 4000]}
+ROWS = {"f32": [300, 700, 1000, 1500, 2000, 3000, 4000, 6000, 8000], "f64": [200, 1000, 4000]}
 TABLE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2404_08970_gb300",
                      "tune_table.txt")
 
@@ -93,6 +93,10 @@ def test_every_alternative_configuration_matches_oracle(dtype):
             Es = O.value(DX, DY, Ts)
             base = L.gw_tune_config(SK, dt, m)
             Tb, sb = _solve(w, dtype)
+            seen.add(base)
+            if dtype == "f32":
+                assert np.linalg.norm(Tb - Ts) <= 1e-3 * np.linalg.norm(Ts), (m, base)
+                assert abs(sb[1] - Es) <= 1e-5 * abs(Es), (m, base, sb[1], Es)
             for cfg in L.gw_tune_candidates(SK, dt, m)[1:]:
                 L.gw_tune_set(SK, dt, m, m, cfg)
                 assert L.gw_tune_config(SK, dt, m) == cfg
@@ -110,6 +114,7 @@ def test_every_alternative_configuration_matches_oracle(dtype):
     finally:
         L.gw_tune_clear()
         _reload_committed_table(L)
-    # Every alternative configuration of this dtype ran at least once.
-    alts = {20, 21, 22, 23, 24} if dtype == "f32" else {30, 31, 32}
+    # Every alternative configuration of this dtype, and every built-in one
+    # with twelve values per thread, ran at least once.
+    alts = {20, 21, 22, 23, 24, 40, 41, 42, 43, 44} if dtype == "f32" else {30, 31, 32}
     assert alts <= seen, alts - seen
