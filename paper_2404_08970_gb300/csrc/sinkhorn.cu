@@ -222,11 +222,17 @@ __device__ __forceinline__ double scale_of(double lu, double S) { return exp2(lu
 // Shared memory of sk_pass (128-byte aligned base):
 //   ring [NG][stages][slot_bytes] (reused at the end for the groups' column
 //   sums, [NG][cover] Real) | red [NG][2][NW] Real | sfb [NG][NW] Real |
-//   Fold, LU [R] Real | full [NG][stages] mbarriers
+//   Fold, LU [R] Real | full [NG][stages] mbarriers | (VPT >= kGvSmemVpt) the
+//   columns' potentials G [cover] Real, 16-byte aligned.
+// With 32 values per thread the column potentials do not fit in the register
+// budget of a 512-thread block (128 per thread) beside the row values and the
+// column sums; they are read from shared memory with the row's 16-byte loads.
+constexpr int kGvSmemVpt = 32;
 template <int NW, int VPT, int NG, typename Real>
 size_t pass_smem_bytes(const RowGeom& g, int R) {
   const size_t ring = std::max((size_t)NG * g.stages * g.slot_bytes, (size_t)NG * 32 * NW * VPT * sizeof(Real));
-  return 128 + ring + sizeof(Real) * (3 * NG * NW + 2 * (size_t)R) + 16 + 8 * (size_t)NG * g.stages;
+  const size_t gvs = VPT >= kGvSmemVpt ? 16 + (size_t)32 * NW * VPT * sizeof(Real) : 0;
+  return 128 + ring + sizeof(Real) * (3 * NG * NW + 2 * (size_t)R) + 16 + 8 * (size_t)NG * g.stages + gvs;
 }
 // Shared memory of sk_plan: ring | full [stages] mbarriers.
 inline size_t plan_smem_bytes(const RowGeom& g) { return 128 + (size_t)g.stages * g.slot_bytes + 8 * g.stages + 16; }
@@ -248,8 +254,8 @@ __device__ __forceinline__ void group_sync(int g) {
 // Returns the new potential and adds the row's plan entries to acc.  The
 // row is read again from the ring, so nothing of the row pass stays live
 // across the group barrier.
-template <int NW, int VPT, typename Real>
-__device__ __forceinline__ Real row_redo(const Real* row, int gt, int g, int m, Real c, const Real (&Gv)[VPT],
+template <int NW, int VPT, typename Real, typename GvAt>
+__device__ __forceinline__ Real row_redo(const Real* row, int gt, int g, int m, Real c, GvAt Gv,
                                          Real Fo, Real lut, Real kappa, Real (&acc)[VPT], Real* sfb) {
   const int lane = gt & 31, wig = gt >> 5;
   Real x[VPT];
@@ -258,7 +264,7 @@ __device__ __forceinline__ Real row_redo(const Real* row, int gt, int g, int m, 
   Real lm = -INFINITY;
 #pragma unroll
   for (int v = 0; v < VPT; ++v) {
-    e[v] = fma(-c, x[v], Gv[v] + Fo);
+    e[v] = fma(-c, x[v], Gv(v) + Fo);
     lm = fmax(lm, e[v]);
   }
   lm = warp_max(lm);
@@ -329,6 +335,9 @@ __device__ __forceinline__ void pass_band(const SkProb<Real>& pr, int a, unsigne
   Real* LU = Fold + R;
   unsigned char* braw = reinterpret_cast<unsigned char*>(LU + R);
   uint64_t* full = reinterpret_cast<uint64_t*>(braw + ((8u - (smem_u32(braw) & 7u)) & 7u));
+  constexpr bool GVS = VPT >= kGvSmemVpt;
+  unsigned char* graw = reinterpret_cast<unsigned char*>(full + NG * S);
+  Real* gvs = reinterpret_cast<Real*>(graw + ((16u - (smem_u32(graw) & 15u)) & 15u));
 
   const int tid = threadIdx.x, g = tid / GT, gt = tid % GT, lane = tid & 31, wig = gt >> 5;
   const int s = a * R, Ra = min(R, n - s);
@@ -368,14 +377,23 @@ __device__ __forceinline__ void pass_band(const SkProb<Real>& pr, int a, unsigne
     Fold[t] = F[s + t];
     LU[t] = pr.lu[s + t];
   }
+  if constexpr (GVS) {
+    for (int p = tid; p < COVER; p += NT) gvs[p] = p < m ? pr.G[p] : (Real)-INFINITY;
+  }
   __syncthreads();
-  Real Gv[VPT], acc[VPT];
+  Real Gv[GVS ? 1 : VPT], acc[VPT];
 #pragma unroll
   for (int v = 0; v < VPT; ++v) {
-    const int p = col_of<Real>(gt, v, GT);
-    Gv[v] = p < m ? pr.G[p] : (Real)-INFINITY;
+    if constexpr (!GVS) {
+      const int p = col_of<Real>(gt, v, GT);
+      Gv[v] = p < m ? pr.G[p] : (Real)-INFINITY;
+    }
     acc[v] = 0;
   }
+  auto gv_at = [&](int v) -> Real {
+    if constexpr (GVS) return gvs[col_of<Real>(gt, v, GT)];
+    else return Gv[v];
+  };
   Real* gred = red + g * 2 * NW;
   Real* gsfb = sfb + g * NW;
   for (int k = 0;; ++k) {
@@ -387,8 +405,19 @@ __device__ __forceinline__ void pass_band(const SkProb<Real>& pr, int a, unsigne
     Real x[VPT], w[VPT];
     load_vals<VPT, GT>(row, gt, m, x);
     const Real Fo = Fold[t];
+    if constexpr (GVS) {
+      constexpr int PER = 16 / sizeof(Real);
 #pragma unroll
-    for (int v = 0; v < VPT; ++v) w[v] = ex2(fma(-c, x[v], Gv[v] + Fo));
+      for (int j = 0; j < VPT / PER; ++j) {
+        const float4 q = reinterpret_cast<const float4*>(gvs)[j * GT + gt];
+        const Real* e = reinterpret_cast<const Real*>(&q);
+#pragma unroll
+        for (int u = 0; u < PER; ++u) w[j * PER + u] = ex2(fma(-c, x[j * PER + u], e[u] + Fo));
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < VPT; ++v) w[v] = ex2(fma(-c, x[v], Gv[v] + Fo));
+    }
     Real St = warp_sum(tree_sum<VPT>(w));
     if constexpr (NW > 1) {
       Real* rb = gred + (k & 1) * NW;
@@ -419,7 +448,7 @@ __device__ __forceinline__ void pass_band(const SkProb<Real>& pr, int a, unsigne
         if (gt == 0) F[s + t] = Fn;
       }
     } else {
-      const Real Fn = row_redo<NW, VPT, Real>(row, gt, g, m, c, Gv, Fo, lut, pr.kappa, acc, gsfb);
+      const Real Fn = row_redo<NW, VPT, Real>(row, gt, g, m, c, gv_at, Fo, lut, pr.kappa, acc, gsfb);
       if (gt == 0) {
         F[s + t] = Fn;
         if (more) {
@@ -615,6 +644,10 @@ __global__ void __launch_bounds__(kMixThreads, 1) sk_pass_mix(const __grid_const
       case 46: pass_band<4, 24, 4, float>(pr, a, status, smem_dyn); break;
       case 47: pass_band<8, 24, 2, float>(pr, a, status, smem_dyn); break;
       case 48: pass_band<1, 24, 16, float>(pr, a, status, smem_dyn); break;
+      case 50: pass_band<1, 32, 16, float>(pr, a, status, smem_dyn); break;
+      case 51: pass_band<2, 32, 8, float>(pr, a, status, smem_dyn); break;
+      case 52: pass_band<4, 32, 4, float>(pr, a, status, smem_dyn); break;
+      case 53: pass_band<8, 32, 2, float>(pr, a, status, smem_dyn); break;
       default: pass_band<16, 8, 1, float>(pr, a, status, smem_dyn); break;  // 23
     }
   } else {
@@ -1483,15 +1516,17 @@ int solve_group(const SolveArgs* const* A, void* const* ws, const size_t* ws_byt
 
 // Row configurations of the Sinkhorn kernels: warps per row group NW, values
 // per thread VPT (a row group covers 32 NW VPT >= m columns), row groups per
-// block NG.  Ids 0-13, 40 and 45-48 are the built-in choices by row length;
-// ids 20-32 and 41-44 are alternatives for the tuning table.  Float covers
-// come in steps of 1.5 and 4/3 (384, 512, 768, 1024, 1536, ...), so that a row
-// just above a power of two does not pay for a row twice its length.  The
-// three-quarter covers take 24 values per thread and half the warps per row
-// of the 12-value ones (41-44): a row group's fixed work per row (its
-// reductions, barrier and scale) is then shared by twice the columns, and a
-// block streams twice the rows at once; in batched passes that is 1.35-1.45x
-// the throughput of 41-44.  with_config below has one case per entry.
+// block NG.  Built-in choices by row length: float 40, 0, 48, 50, 45, 51, 46,
+// 52, 47, 53, 55, 54 (covers 384, 512, 768, 1024, ..., 12288, 16384: steps of
+// 4/3 and 3/2, so that a row just above a power of two does not pay for a row
+// twice its length), double 10-13; the other ids are alternatives for the
+// tuning table.  The built-in float covers from 768 columns take 24 or 32
+// values per thread and as few warps per row as that allows: a row group's
+// fixed work per row (its reductions, barrier and scale) is shared by more
+// columns, and a block streams more rows at once.  Against 12 and 16 values
+// per thread with twice the warps per row, batched passes run 1.35-1.45x and
+// 1.1-1.2x as fast, the 8192-column single solve 1.14x.  with_config below
+// has one case per entry.
 struct SkConfig {
   int id, dtype, nw, vpt, ng;
 };
@@ -1503,6 +1538,8 @@ constexpr SkConfig kSkConfigs[] = {
     {30, GW_F64, 2, 4, 8},  {31, GW_F64, 8, 4, 2},  {32, GW_F64, 32, 4, 1},  {40, GW_F32, 1, 12, 16},
     {41, GW_F32, 2, 12, 8}, {42, GW_F32, 4, 12, 4}, {43, GW_F32, 8, 12, 2}, {44, GW_F32, 16, 12, 1},
     {45, GW_F32, 2, 24, 8}, {46, GW_F32, 4, 24, 4}, {47, GW_F32, 8, 24, 2}, {48, GW_F32, 1, 24, 16},
+    {50, GW_F32, 1, 32, 16}, {51, GW_F32, 2, 32, 8}, {52, GW_F32, 4, 32, 4}, {53, GW_F32, 8, 32, 2},
+    {54, GW_F32, 16, 32, 1}, {55, GW_F32, 16, 24, 1},
 };
 
 bool sk_config_shape(int id, int* dtype, int* nw, int* vpt, int* ng) {
@@ -1529,15 +1566,15 @@ int sk_default_config(int m, int dtype) {
     if (m <= 384) return 40;
     if (m <= 512) return 0;
     if (m <= 768) return 48;
-    if (m <= 1024) return 1;
+    if (m <= 1024) return 50;
     if (m <= 1536) return 45;
-    if (m <= 2048) return 2;
+    if (m <= 2048) return 51;
     if (m <= 3072) return 46;
-    if (m <= 4096) return 3;
+    if (m <= 4096) return 52;
     if (m <= 6144) return 47;
-    if (m <= 8192) return 4;
-    if (m <= 9216) return 5;
-    return 6;
+    if (m <= 8192) return 53;
+    if (m <= 12288) return 55;
+    return 54;
   }
   if (m <= 256) return 10;
   if (m <= 1024) return 11;
@@ -1579,6 +1616,12 @@ int with_config(int cfg, F&& f) {
     case 46: return f.template run<4, 24, 4, float>();
     case 47: return f.template run<8, 24, 2, float>();
     case 48: return f.template run<1, 24, 16, float>();
+    case 50: return f.template run<1, 32, 16, float>();
+    case 51: return f.template run<2, 32, 8, float>();
+    case 52: return f.template run<4, 32, 4, float>();
+    case 53: return f.template run<8, 32, 2, float>();
+    case 54: return f.template run<16, 32, 1, float>();
+    case 55: return f.template run<16, 24, 1, float>();
     case 30: return f.template run<2, 4, 8, double>();
     case 31: return f.template run<8, 4, 2, double>();
     case 32: return f.template run<32, 4, 1, double>();
@@ -1645,10 +1688,13 @@ int solve_group_key(const SolveArgs& A) { return row_config(A.m, A.dtype); }
 // Mixed batches: problems of one schedule whose row configurations run
 // 512-thread blocks share every Sinkhorn launch (sk_pass_mix, sk_cols_mix).
 // ---------------------------------------------------------------------------
+// Rows above 8192 columns run in groups of their own configuration: their
+// variants in the shared kernel would push its register allocation into
+// spills for every problem.
 bool solve_mixable(const SolveArgs& A) {
   int dt = 0, nw = 0, vpt = 0, ng = 0;
   if (!sk_config_shape(row_config(A.m, A.dtype), &dt, &nw, &vpt, &ng)) return false;
-  return 32 * nw * ng == kMixThreads;
+  return 32 * nw * ng == kMixThreads && 32 * nw * vpt <= 8192;
 }
 
 namespace {

@@ -25,7 +25,7 @@ from . import _lib as L
 # Built-in row-length ranges (the boundaries of the built-in choice).
 RANGES = {
     L.GW_F32: [(1, 384), (385, 512), (513, 768), (769, 1024), (1025, 1536), (1537, 2048), (2049, 3072),
-               (3073, 4096), (4097, 6144), (6145, 8192), (8193, 9216), (9217, 16384)],
+               (3073, 4096), (4097, 6144), (6145, 8192), (8193, 12288), (12289, 16384)],
     L.GW_F64: [(1, 256), (257, 1024), (1025, 4096), (4097, 10240)],
 }
 TOL = {L.GW_F32: 1e-4, L.GW_F64: 1e-10}

@@ -14,7 +14,7 @@ from tests import gwtest_util as U
 
 pytestmark = pytest.mark.gpu
 
-ROWS = {"f32": [300, 700, 1000, 1500, 2000, 3000, 4000, 6000, 8000], "f64": [200, 1000, 4000]}
+ROWS = {"f32": [300, 700, 1000, 1500, 2000, 3000, 4000, 6000, 8000, 10000], "f64": [200, 1000, 4000]}
 TABLE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2404_08970_gb300",
                      "tune_table.txt")
 
@@ -114,7 +114,8 @@ def test_every_alternative_configuration_matches_oracle(dtype):
     finally:
         L.gw_tune_clear()
         _reload_committed_table(L)
-    # Every alternative configuration of this dtype, and every built-in one
-    # with twelve or 24 values per thread, ran at least once.
-    alts = set(range(20, 25)) | set(range(40, 49)) if dtype == "f32" else {30, 31, 32}
+    # Every configuration of this dtype up to 16384 columns ran at least once
+    # (as the built-in choice or as an alternative).
+    alts = set(range(0, 7)) | set(range(20, 25)) | set(range(40, 49)) | set(range(50, 56)) if dtype == "f32" \
+        else {30, 31, 32}
     assert alts <= seen, alts - seen
