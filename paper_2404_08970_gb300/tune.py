@@ -29,6 +29,12 @@ RANGES = {
     L.GW_F64: [(1, 256), (257, 1024), (1025, 4096), (4097, 10240)],
 }
 TOL = {L.GW_F32: 1e-4, L.GW_F64: 1e-10}
+# Rows of the synthetic problems: a single solve then spreads bands of about 54
+# rows over the GPU's SMs, close to the bands of large single solves and of
+# batched problems (at least 512 KB each).  With 2048 rows (14-row bands) the
+# per-band start-up decides, and configurations that stream fewer rows at once
+# win there but lose in batched passes.
+ROWS = 8192
 
 
 def halves(lo: int, hi: int):
@@ -38,7 +44,7 @@ def halves(lo: int, hi: int):
     return [(lo, mid), (mid + 1, hi)]
 
 
-def sweep(n: int = 2048, reps: int = 3, log=print):
+def sweep(n: int = ROWS, reps: int = 3, log=print):
     import numpy as np
     import torch
 
@@ -116,7 +122,7 @@ def write_table(path: str, entries, notes, n: int, reps: int, device_name: str) 
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=os.path.join(os.path.dirname(L.LIB_PATH), "tune_table.txt"))
-    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--n", type=int, default=ROWS)
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
     import torch
