@@ -777,9 +777,10 @@ __global__ void __launch_bounds__(32 * NW, 1) sk_plan(const __grid_constant__ Sk
 template <typename Real>
 __global__ void fill_product(const double* __restrict__ u, const double* __restrict__ v, int n, int m,
                              Real* __restrict__ T) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const size_t N = (size_t)n * m;
-  for (size_t k = idx; k < N; k += (size_t)gridDim.x * blockDim.x) T[k] = (Real)(u[k / m] * v[k % m]);
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m) return;
+  const double vp = v[p];
+  for (int i = blockIdx.y; i < n; i += gridDim.y) T[(size_t)i * m + p] = (Real)(u[i] * vp);
 }
 
 template <typename Real>
@@ -956,6 +957,9 @@ __global__ void finish_stats(const double* __restrict__ dotE, int nE, const doub
 //   scal[9] sqrt(m_prev / m) (the rescale after each step's plan)
 // ---------------------------------------------------------------------------
 constexpr int kUgwScal = 16;
+// Row-parallel elementwise kernels: columns on the grid's x, rows strided over
+// at most kRowGridY blocks in y.
+constexpr int kRowGridY = 2048;
 
 // Per row: a_i = sum_p T_ip, e_i = sum_p T_ip ln T_ip (0 ln 0 = 0), in double.
 template <typename Real>
@@ -966,9 +970,16 @@ __global__ void ugw_rowstats(const Real* __restrict__ T, int n, int m, double* _
   const Real* row = T + (size_t)i * m;
   double s = 0.0, t = 0.0;
   for (int p = threadIdx.x & 31; p < m; p += 32) {
-    const double x = (double)row[p];
+    const Real xr = row[p];
+    const double x = (double)xr;
     s += x;
-    if (x > 0.0) t += x * log(x);
+    // Float plans take x ln x in float (1 ulp logf; the FP64 log costs tens
+    // of FP64 operations per element on this GPU); double plans in double.
+    if constexpr (sizeof(Real) == 4) {
+      if (xr > 0.0f) t += (double)(xr * logf(xr));
+    } else {
+      if (x > 0.0) t += x * log(x);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -1084,10 +1095,12 @@ __global__ void ugw_cost_kernel(Real* __restrict__ Pi, int n, int m, const Real*
                                 const Real* __restrict__ lv, const double* __restrict__ scal, double eps) {
   const Real g = (Real)scal[0], inv_m = (Real)(1.0 / scal[1]);
   const Real el = (Real)(eps * 0.6931471805599453);
-  const size_t N = (size_t)n * m;
-  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (size_t)gridDim.x * blockDim.x) {
-    const size_t i = k / m, p = k % m;
-    Pi[k] = fma(Pi[k] + g, inv_m, -el * (lu[i] + lv[p]));
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= m) return;
+  const Real lvp = lv[p];
+  for (int i = blockIdx.y; i < n; i += gridDim.y) {
+    const size_t k = (size_t)i * m + p;
+    Pi[k] = fma(Pi[k] + g, inv_m, -el * (lu[i] + lvp));
   }
 }
 
@@ -1303,7 +1316,8 @@ void step_setup(const SolveState<Real>& S, cudaStream_t st) {
   cudaMemsetAsync((char*)S.sk.Pi + (size_t)A.n * A.m * sizeof(Real), 0, 16, st);
   log2_scaled<Real><<<(A.n + 255) / 256, 256, 0, st>>>(A.u, A.n, (Real*)S.sk.lu);
   log2_scaled<Real><<<(A.m + 255) / 256, 256, 0, st>>>(A.v, A.m, (Real*)S.sk.lv);
-  fill_product<Real><<<4 * A.num_sms, 256, 0, st>>>(A.u, A.v, A.n, A.m, (Real*)A.T);
+  fill_product<Real><<<dim3((A.m + 255) / 256, std::min(A.n, kRowGridY)), 256, 0, st>>>(A.u, A.v, A.n, A.m,
+                                                                                    (Real*)A.T);
   if (A.rho > 0.0) {
     // Unbalanced GW starts at u v^T / sqrt(m(u) m(v)).
     ugw_start_scale<<<1, 256, 0, st>>>(A.u, A.n, A.v, A.m, S.ugw_scal);
@@ -1318,7 +1332,7 @@ void ugw_scalars(const SolveState<Real>& S, cudaStream_t st) {
   ugw_rowstats<Real><<<(A.n + 7) / 8, 256, 0, st>>>((const Real*)A.T, A.n, A.m, S.ugw_a, S.ugw_e);
   ugw_colsums<Real><<<dim3((A.m + 255) / 256, S.sk.B), 256, 0, st>>>((const Real*)A.T, A.n, A.m, S.sk.R,
                                                                       S.sk.colpart);
-  ugw_finish<<<1, 256, 0, st>>>(S.ugw_a, S.ugw_e, S.sk.colpart, S.sk.B, A.n, A.m, A.u, A.v, A.rho, A.eps,
+  ugw_finish<<<1, 1024, 0, st>>>(S.ugw_a, S.ugw_e, S.sk.colpart, S.sk.B, A.n, A.m, A.u, A.v, A.rho, A.eps,
                                 S.ugw_scal);
 }
 
@@ -1344,7 +1358,8 @@ int step_cost(const SolveState<Real>& S, cudaStream_t st, int l) {
     ugw_scalars(S, st);
     int rc = gradient(S, 1, 1.0, st);
     if (rc != GW_OK) return rc;
-    ugw_cost_kernel<Real><<<4 * A.num_sms, 256, 0, st>>>((Real*)S.sk.Pi, A.n, A.m, S.sk.lu, S.sk.lv, S.ugw_scal,
+    ugw_cost_kernel<Real><<<dim3((A.m + 255) / 256, std::min(A.n, kRowGridY)), 256, 0, st>>>(
+        (Real*)S.sk.Pi, A.n, A.m, S.sk.lu, S.sk.lv, S.ugw_scal,
                                                          A.eps);
     if (A.warm_start && l > 0) return GW_OK;
     fill_val<Real><<<(A.n + 255) / 256, 256, 0, st>>>(S.sk.F, A.n, (Real)0);
@@ -1377,7 +1392,7 @@ void step_after_plan(const SolveState<Real>& S, cudaStream_t st) {
   const SolveArgs& A = *S.A;
   if (!(A.rho > 0.0)) return;
   TraceScope ts(A.tracer, "ugw_rescale", st);
-  ugw_rescale_factor<<<1, 256, 0, st>>>(S.sk.colpart, S.sk.B, A.m, S.ugw_scal);
+  ugw_rescale_factor<<<1, 1024, 0, st>>>(S.sk.colpart, S.sk.B, A.m, S.ugw_scal);
   scale_by<Real><<<4 * A.num_sms, 256, 0, st>>>((Real*)A.T, (size_t)A.n * A.m, S.ugw_scal + 9);
 }
 
