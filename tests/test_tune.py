@@ -140,3 +140,24 @@ def test_sweep_ranges_and_table_round_trip(tmp_path):
     assert L.gw_tune_config(SK, F32, 600) == 21
     assert L.gw_tune_config(SK, F32, 900) == 1
     assert L.gw_tune_config(SK, F64, 100) == 30
+
+
+def test_committed_table_loads_and_is_consistent():
+    """The committed table (read at context creation) loads, has one entry per
+    half range of the sweep, and each entry names a candidate of its longest
+    row (so it covers every row of its range)."""
+    import os
+    from paper_2404_08970_gb300 import tune
+    path = os.path.join(os.path.dirname(os.path.abspath(L.__file__)), "tune_table.txt")
+    rows = []
+    for line in open(path):
+        body = line.split("#")[0].split()
+        if body:
+            rows.append(tuple(int(x) for x in body))
+    want = [(SK, dt, a, b) for dt, ranges in tune.RANGES.items() for lo, hi in ranges for a, b in tune.halves(lo, hi)]
+    assert sorted(r[:4] for r in rows) == sorted(want)
+    L.gw_tune_load(path)
+    for kernel, dt, lo, hi, cfg in rows:
+        assert L.gw_tune_config(kernel, dt, lo) == cfg and L.gw_tune_config(kernel, dt, hi) == cfg
+        assert cfg in L.gw_tune_candidates(kernel, dt, hi), (lo, hi, cfg)
+        assert cover(cfg) >= hi
