@@ -106,7 +106,11 @@ typedef struct gw_ctx gw_ctx;
 
 /* Creates a context on CUDA device `device` (made current for the calls of
  * this context).  *ctx receives the handle.  GW_ERR_CUDA if the device is
- * unusable. */
+ * unusable.  With the environment variable GW_FORCE_GENERIC set to a value
+ * other than "0" at creation, the context's 1D gradients use the generic row
+ * kernel (one thread block per band, no warp specialisation) even where the
+ * warp-specialised one applies: same results within rounding, for testing
+ * that kernel on shapes the fast one would take. */
 gw_status gw_ctx_create(gw_ctx** ctx, int device);
 
 /* Frees the context and its device workspace (synchronises the device). */
