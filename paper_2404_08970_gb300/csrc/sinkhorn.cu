@@ -1152,8 +1152,9 @@ RowGeom row_geom(int m) {
 // whole work: each block pays for its ring set-up, the first copies' latency
 // and its column partials, so bands hold at least kBatchBandBytes of Pi (and
 // at least 32 rows, at most kBatchBandRowsMax, whose potentials the block
-// keeps in shared memory).  At 256 to 1024 columns this takes the batched pass
-// from 1.0-2.6 TB/s (32-row bands) to 1.9-4.1 TB/s.
+// keeps in shared memory).  Against 32-row bands this takes batched passes
+// over rows of 256 columns from 1.0 to 2.5 TB/s and of 1024 columns from 2.6
+// to 4.2 TB/s (n = 4096); 1 MB and 2 MB bands were slower on mixed batches.
 constexpr size_t kBatchBandBytes = 512 * 1024;
 constexpr int kBatchBandRowsMax = 1024;
 Bands solve_bands(const SolveArgs& A) {
