@@ -28,12 +28,20 @@ def _rank(rank, world, port, times, out):
 
 def test_two_ranks_max_time_and_job_rate():
     world = 2
-    port = _free_port()
     times = [120.0, 150.0]
-    with mp.Manager() as man:
-        out = man.dict()
-        mp.spawn(_rank, args=(world, port, times, out), nprocs=world, join=True)
-        res = dict(out)
+    # The free port is released before the ranks bind it, so another process
+    # can take it in between: the rendezvous is retried on a fresh port.
+    for attempt in range(3):
+        port = _free_port()
+        try:
+            with mp.Manager() as man:
+                out = man.dict()
+                mp.spawn(_rank, args=(world, port, times, out), nprocs=world, join=True)
+                res = dict(out)
+            break
+        except Exception:
+            if attempt == 2:
+                raise
     for r in range(world):
         ms_max, rate = res[r]
         assert ms_max == 150.0
